@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""IPM benchmark: cell-steps/s of Algorithm 1 (IPM time step) on the 1-D Euler Sod workload
+(2000 cells, 3 uncertain dims, total degree 5 -> N = 56 moments x 3 variables, 6^3 = 216 Gauss nodes).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+One step = one call of ipm_step: the Newton solve of the dual problem in every cell, the CFL time
+step, the kinetic-flux moment update (one captured CUDA graph). Prints one JSON line (rank 0).
+--impl reference times the CPU oracle on the host cores instead (each step a bounded sample).
+With torchrun (N > 1) every rank runs an independent replica of the workload on its own GPU
+(the method needs no data exchange between replicas), value = all cells updated / max time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IPM cell-steps/s (mixed+batched vs FP64 GPU at equal error); p50/p99 latency"
+UNIT = "cell-steps/s"
+FP64_PEAK_TFLOPS = 1.25      # nominal dense FP64 of a GB300 (probe: 1.19 measured with FMA chains)
+L2_FLUSH_BYTES = 512 << 20   # > 4x the 126 MiB L2
+WINDOW = dict(nx=200, x_lo=0.45, x_hi=0.55)   # same dx as the 2000-cell mesh, around the interface
+
+
+def workload():
+    from paper_1912_09238_gb300 import workloads
+    return workloads.SOD_1D
+
+
+def workload_desc(w, precision):
+    return {
+        "workload": (f"{w['name']}: 1-D Euler Sod tube IPM, {w['nx']} cells on [0,1], gamma 1.4, 3 uniform "
+                     f"uncertain dims (rho_L, p_L, interface), total degree {w['M']} Legendre (N=56 x 3 vars), "
+                     f"tensor Gauss {w['nq']}^3=216 nodes, Euler entropy (App. B), global LF kinetic flux, "
+                     f"CFL {w['cfl']}, Newton tol {w['newton_tol']}; Algorithm 1 time steps from t=0"),
+        "precision": precision,
+        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write on the same stream, excluded from step times)",
+        "inputs": "initial data projected on the device; state resident in HBM",
+    }
+
+
+# ------------------------------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.strip().split(",") for r in open(self.f.name).read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def newton_flops(N, m, Q, cells, iters):
+    """Algorithmic FP64 flops of one Newton launch: every cell evaluates the gradient (reconstruction +
+    projection) once more than it updates; every update adds the Hessian (unique entries, B*N(N+1)/2
+    Q-term dot products), the Cholesky factorisation, two triangular solves and the direction at the
+    nodes. Closures and line-search trials are not counted."""
+    B = m * (m + 1) // 2
+    NM = N * m
+    grad_eval = 4.0 * Q * N * m
+    per_update = B * Q * N * (N + 1) + NM ** 3 / 3.0 + 2.0 * NM ** 2 + 2.0 * Q * N * m
+    return (cells + iters) * grad_eval + iters * per_update
+
+
+# ------------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from tests._cases import gpu_context
+
+    w = workload()
+    precision = args.precision
+    ctx = gpu_context(w, precision=precision)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream.cuda_stream)
+    d = ctx.dims
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        ctx.step(sync=False)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    step_ms, newton_ms, iters = [], [], []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        ctx.step(sync=False)
+        ev[k][1].record(stream)
+        nm, _, _ = ctx.step_timing()               # waits for this step; outside the event pair
+        s = ctx.sync_stats()
+        newton_ms.append(nm)
+        iters.append(s.newton_iters)
+        if s.failed_cells:
+            raise RuntimeError(f"dual solve failed in {s.failed_cells} cells: {s.as_dict()}")
+    barrier()
+    cl = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    cells = d.n_interior
+    value = ws * cells * args.steps / total_s
+
+    # roofline of the dominant kernel (the Newton solve), FP64-ALU bound
+    flops = [newton_flops(d.N, d.m, d.Q, cells, it) for it in iters]
+    achieved = (sum(flops) / len(flops)) / (statistics.mean(newton_ms) / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_newton (fused dual solve: reconstruction, closure, gradient, "
+                "Hessian, Cholesky, solves, Armijo)", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "nominal GB300 dense FP64 (recipe); an FMA-chain probe measured 1.19 TFLOP/s",
+                "traffic": None, "newton_ms_mean": round(statistics.mean(newton_ms), 4),
+                "newton_share_of_step": round(sum(newton_ms) / sum(step_ms), 4),
+                "algorithmic_flops_per_launch": round(sum(flops) / len(flops)),
+                "newton_iters_per_step": round(statistics.mean(iters), 1)}
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    shape = ctx.shape
+    hu = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    hl = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    hu[...] = ctx.get_moments()
+    hl[...] = ctx.get_duals()
+    e2e_steps = args.steps
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_moments(hu)
+        ctx.set_duals(hl)
+        ctx.step(sync=False)
+        hu[...] = ctx.get_moments()
+        hl[...] = ctx.get_duals()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nbytes = int(np.prod(shape)) * 8
+    e2e = {"value": ws * cells * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
+           "d2h_bytes_per_step": 2 * nbytes, "api": "ipm_set_moments + ipm_set_duals + ipm_step + "
+           "ipm_get_moments + ipm_get_duals (host buffers, pinned)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+            "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == "fp64" else "f64+bf16", "data": "synthetic",
+            "config": workload_desc(w, precision), "roofline": roofline, "e2e": e2e,
+            "gpu_launches": 3 * args.steps, "clocks": cl}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
+def oracle_step_sample(kind, n_steps):
+    """Time the CPU oracle (single thread) on a bounded sample of the Sod workload.
+
+    kind == "first_step": Algorithm 1 step 1 of the full 2000-cell workload from its initial data.
+    kind == "window": n_steps consecutive Algorithm-1 steps on the 200 cells around the interface
+    (same dx), from the initial data. Returns the seconds of each step."""
+    from paper_1912_09238_gb300 import workloads
+    from tests._cases import oracle_problem
+    from oracle import scheme1d as s1
+    w = workload() if kind == "first_step" else workloads.variant(workload(), **WINDOW)
+    prob = oracle_problem(w)
+    st = s1.initial_state(prob)
+    secs = []
+    for _ in range(1 if kind == "first_step" else n_steps):
+        t0 = time.perf_counter()
+        st = s1.ipm_step(prob, st)
+        secs.append(time.perf_counter() - t0)
+        assert (st.newton_status == 0).all()
+    return {"cells": w["nx"], "seconds": secs}
+
+
+def _oracle_subprocess(kind, n_steps=1):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", kind,
+                        "--steps", str(n_steps)], env=env, capture_output=True, text=True, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline():
+    res = _oracle_subprocess("first_step")
+    secs = res["seconds"][0]
+    return {"value": res["cells"] / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle (numpy FP64, one thread) Algorithm-1 step 1 of the full {res['cells']}-cell Sod "
+                      f"workload from its initial data: {secs:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    res = _oracle_subprocess("window", args.warmup + args.steps)
+    times = res["seconds"][args.warmup:]
+    cells = res["cells"]
+    value = cells * len(times) / sum(times)
+    w = workload()
+    sample = (f"oracle (numpy FP64, one thread) Algorithm-1 steps {args.warmup + 1}..{args.warmup + args.steps} "
+              f"on the {cells} cells of the Sod workload around the interface (x in [0.45,0.55], same dx), "
+              f"from the initial data")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_desc(w, "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", choices=["first_step", "window"], default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_sample:
+        print(json.dumps(oracle_step_sample(args.oracle_sample, args.steps)), flush=True)
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

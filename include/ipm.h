@@ -1,0 +1,230 @@
+/*
+ * ipm.h -- C ABI of the GB300 Intrusive Polynomial Moment (IPM) library.
+ *
+ * The library runs the hot path of the IPM method for hyperbolic conservation laws with
+ * uncertain initial data (Kusch, Wolters, Frank, "Intrusive acceleration strategies for
+ * Uncertainty Quantification for hyperbolic systems of conservation laws", arXiv:1912.09238):
+ *
+ *   - the per-cell dual problem lambda_hat(u_hat) = argmin L(lambda; u_hat)         (Sec. 2, Eq. dualProblem;
+ *     Sec. 3.1, Eq. L), solved by the Newton map d (Eq. dualIterationFunction) with an Armijo
+ *     line search, stopped by Eq. tauCrit;
+ *   - the kinetic-flux moment update c (Eq. momentIterationFunction, quadrature form
+ *     Eq. momentUpQuadrature) with a Lax-Friedrichs flux (App. A);
+ *   - Algorithm 1 (IPM time step) and Algorithm 2 (One-Shot IPM pseudo-time step).
+ *
+ * Conventions shared by every call
+ *   Moments and duals cross the ABI as float64 arrays laid out [cell][moment][variable]
+ *   (row-major), i.e. element (c, i, a) sits at c*N*m + i*m + a. "cell" runs over ALL cells
+ *   including the ghost layer: 1-D meshes have nx+2 cells (ghost 0, interior 1..nx, ghost
+ *   nx+1). "moment" i follows the graded total-degree order of the multi-indices: ascending
+ *   total degree, and within one degree descending lexicographic order of (i_1..i_p)
+ *   (Sec. 2, Eq. numberBasisFcts gives their number N = C(M+p, p)). "variable" a runs over the m
+ *   conserved quantities (Burgers: u; 1-D Euler: rho, rho v, E; 2-D Euler: rho, rho v1,
+ *   rho v2, E).
+ *
+ *   Ownership: ipm_init allocates all device state and keeps it resident until ipm_destroy.
+ *   Host pointers passed in are only read (or written) during the call. Device-pointer calls
+ *   (suffix _device) borrow the caller's buffer for the duration of the call and order their
+ *   work on the context's stream.
+ *
+ *   Errors: every call returns an ipm_status; nothing throws or exits across the ABI. The
+ *   message of the last failure is returned by ipm_last_error(ctx) (ctx may be NULL for a
+ *   failure inside ipm_init). Per-cell solver failures do not fail the call: they are counted
+ *   in ipm_stats, and the first failing cell and its status are reported there.
+ *
+ *   Threading: a context is not thread-safe; use one context per host thread. All GPU work of a
+ *   context is ordered on its stream (ipm_set_stream).
+ */
+#ifndef IPM_H
+#define IPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IPM_OK = 0,
+  IPM_EINVAL = 1,       /* bad argument or unsupported combination */
+  IPM_ENOMEM = 2,       /* device or host allocation failed */
+  IPM_ENOCONV = 3,      /* Newton iteration cap reached (per-cell status) */
+  IPM_ENOTSPD = 4,      /* Hessian not positive definite in the Cholesky factorisation (per-cell) */
+  IPM_EINFEASIBLE = 5,  /* dual state outside the domain of u_s, e.g. Lambda_E >= 0 (per-cell) */
+  IPM_ELINESEARCH = 6,  /* Armijo backtracking exhausted its halvings (per-cell) */
+  IPM_ENONFINITE = 7,   /* NaN/Inf gradient (per-cell) */
+  IPM_EAGAIN = 8,       /* serving: result not ready yet */
+  IPM_ECUDA = 9,        /* a CUDA runtime call failed; see ipm_last_error */
+  IPM_ETIMEOUT = 10     /* a bounded wait ran out */
+} ipm_status;
+
+typedef enum { IPM_BURGERS_1D = 0, IPM_EULER_1D = 1, IPM_EULER_2D = 2 } ipm_problem_kind;
+
+/* Boundary handling of the ghost layer (Algorithm 1 keeps ghost cells j = 0, nx+1). */
+typedef enum {
+  IPM_BC_OUTFLOW = 0,    /* ghost copies its interior neighbour (moments and duals) */
+  IPM_BC_PERIODIC = 1,   /* ghost copies the opposite interior cell */
+  IPM_BC_DIRICHLET = 2   /* ghost keeps its initial state; its duals are converged once at init */
+} ipm_bc;
+
+typedef enum {
+  IPM_IC_RIEMANN = 0     /* one jump at x0(xi); left/right states and x0 affine in xi */
+} ipm_ic_kind;
+
+typedef enum {
+  IPM_ENTROPY_QUADRATIC = 0,        /* s(u) = |u|^2/2: IPM = stochastic Galerkin (Sec. 1, Sec. 3.1) */
+  IPM_ENTROPY_BOUNDED_BARRIER = 1,  /* s(u) = (u-u_-)ln(u-u_-) + (u_+-u)ln(u_+-u), scalar problems */
+  IPM_ENTROPY_EULER = 2             /* s(u) = -rho ln(rho^-gamma (E - |m|^2/(2 rho)))  (App. B) */
+} ipm_entropy_kind;
+
+typedef enum {
+  IPM_PREC_FP64 = 0,   /* every operation in float64 */
+  IPM_PREC_MIXED = 1   /* Hessian contraction on the tensor cores (BF16 split products, FP32
+                          accumulate); gradient, Cholesky, Newton step and update in float64 */
+} ipm_precision;
+
+/* Problem description. Primitive states are (u) for Burgers and (rho, v_1[, v_2], p) for Euler;
+ * every parameter X of the initial data is X + sum_d dX[d] * xi_d with xi_d ~ U[-1, 1]. */
+typedef struct {
+  int kind;                 /* ipm_problem_kind */
+  int nx, ny;               /* interior cells (ny = 1 for 1-D problems) */
+  double x_lo, x_hi;        /* 1-D domain */
+  int bc_left, bc_right;    /* ipm_bc of the two 1-D ends */
+  double cfl;               /* dt = cfl * dx / max speed over all cells and nodes */
+  double t_end;             /* final time of ipm_run and clip of the last step; 0 = no clip */
+  double gamma;             /* heat capacity ratio (Euler) */
+  int ic_kind;              /* ipm_ic_kind */
+  double ic_x0, ic_dx0[3];
+  double ic_left[4], ic_dleft[4][3];
+  double ic_right[4], ic_dright[4][3];
+} ipm_problem;
+
+typedef struct {
+  int p;                    /* number of uncertain dimensions, 1..3 */
+  int total_degree;         /* M: moments N = C(M+p, p) */
+} ipm_basis;
+
+typedef struct {
+  int n_per_dim;            /* tensor Gauss-Legendre rule with n_per_dim^p nodes */
+} ipm_quadrature;
+
+typedef struct {
+  int kind;                 /* ipm_entropy_kind */
+  double u_minus, u_plus;   /* bounded barrier bounds */
+} ipm_entropy;
+
+typedef struct {
+  int precision;            /* ipm_precision */
+  double newton_tol;        /* tau of Eq. tauCrit (absolute; sum over moments of 2-norms) */
+  int max_newton;           /* Newton iteration cap per cell and solve */
+  double armijo_c;          /* sufficient-decrease constant */
+  int max_halvings;         /* Armijo backtracking cap */
+  double slack_rel;         /* rounding allowance of the Armijo test, relative to the terms of L */
+} ipm_options;
+
+/* Sizes of a context's arrays. */
+typedef struct {
+  int N;                    /* moments per variable */
+  int m;                    /* conserved variables */
+  int Q;                    /* quadrature nodes */
+  int p;                    /* uncertain dimensions */
+  int n_cells;              /* all cells including ghosts */
+  int n_interior;           /* interior cells */
+} ipm_dims;
+
+/* Counters of the last solve or step. */
+typedef struct {
+  int64_t newton_iters;     /* Newton updates summed over cells */
+  int32_t max_iters;        /* largest per-cell count */
+  int32_t failed_cells;     /* cells whose per-cell status is not IPM_OK */
+  int32_t first_failed_cell;/* lowest failing cell index, -1 if none */
+  int32_t first_status;     /* its ipm_status */
+  double dt;                /* time step taken (ipm_step / ipm_oneshot_step) */
+  double t;                 /* time after the call */
+  double residual;          /* steady residual of the last step (Eq. residualSteady, first variable) */
+  int64_t steps;            /* steps taken since ipm_init */
+} ipm_stats;
+
+typedef struct ipm_ctx ipm_ctx;
+
+/* Fill *opt with the defaults: FP64, tau = 1e-10, 100 iterations, c = 1e-4, 30 halvings,
+ * slack 1e-12. */
+void ipm_default_options(ipm_options* opt);
+
+/* Create a context on the current CUDA device: build the basis and quadrature tables, allocate
+ * the resident state, project the initial data (Algorithm 1, first loop) and set the initial
+ * duals to the projection of the nodal entropy variables; Dirichlet ghosts are solved to
+ * convergence. Returns IPM_EINVAL for unsupported sizes (N*m above the per-CTA limit of the
+ * chosen precision), IPM_ENOMEM / IPM_ECUDA on device failures. */
+ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad,
+                    const ipm_entropy* entropy, const ipm_options* options, ipm_ctx** out);
+
+/* Release all device state of ctx. NULL is accepted. */
+void ipm_destroy(ipm_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failing ipm_init when ctx is NULL). */
+const char* ipm_last_error(const ipm_ctx* ctx);
+
+ipm_status ipm_get_dims(const ipm_ctx* ctx, ipm_dims* out);
+
+/* Order all later work of ctx on the given cudaStream_t (NULL restores the context's own stream). */
+ipm_status ipm_set_stream(ipm_ctx* ctx, void* cuda_stream);
+
+/* Copy moments / duals in or out; count must equal n_cells*N*m doubles. Synchronous. */
+ipm_status ipm_set_moments(ipm_ctx* ctx, const double* host, size_t count);
+ipm_status ipm_get_moments(ipm_ctx* ctx, double* host, size_t count);
+ipm_status ipm_set_duals(ipm_ctx* ctx, const double* host, size_t count);
+ipm_status ipm_get_duals(ipm_ctx* ctx, double* host, size_t count);
+/* Nodal states u_s(lambda_j^T phi(xi_k)) at the current duals, laid out [cell][variable][node]
+ * (count = n_cells*m*Q). Valid after ipm_dual_solve / ipm_step / ipm_oneshot_step. */
+ipm_status ipm_get_nodal_states(ipm_ctx* ctx, double* host, size_t count);
+
+/* Device-pointer variants: buffers live on the context's device, same layout and count;
+ * asynchronous on the context's stream. */
+ipm_status ipm_set_moments_device(ipm_ctx* ctx, const double* dev, size_t count);
+ipm_status ipm_get_moments_device(ipm_ctx* ctx, double* dev, size_t count);
+
+/* Newton solve of the dual problem in every interior cell (Eq. dualIteration1 until Eq. tauCrit),
+ * warm-started at the current duals; the nodal states of the result are kept for the next
+ * update. Synchronous when stats != NULL. */
+ipm_status ipm_dual_solve(ipm_ctx* ctx, ipm_stats* stats);
+
+/* Only the moment update c of every interior cell from the current duals (Eq. momentUpQuadrature)
+ * with the given dt > 0 (dt is not computed and t is not advanced); then the boundary condition.
+ * Requires a preceding ipm_dual_solve. */
+ipm_status ipm_update(ipm_ctx* ctx, double dt);
+
+/* One time step of Algorithm 1: dual solve in every cell, dt from the CFL rule on the new nodal
+ * states (clipped to t_end), moment update, boundary condition. Runs as one captured CUDA graph.
+ * Asynchronous when stats == NULL; otherwise waits and fills *stats. */
+ipm_status ipm_step(ipm_ctx* ctx, ipm_stats* stats);
+
+/* Steps of Algorithm 1 until t >= t_end (at most max_steps); fills *stats if not NULL. */
+ipm_status ipm_run(ipm_ctx* ctx, int64_t max_steps, ipm_stats* stats);
+
+/* One pseudo-time step of Algorithm 2 (One-Shot IPM): one damped Newton step per interior cell,
+ * ghost duals from the boundary condition, moment update with the CFL dt, steady residual
+ * (Eq. residualSteady on the zero-order moment of the first variable) into stats->residual. */
+ipm_status ipm_oneshot_step(ipm_ctx* ctx, ipm_stats* stats);
+
+/* Device time of the last ipm_step / ipm_oneshot_step, from CUDA events recorded inside its graph:
+ * the Newton kernel (with its queue reset), the moment update, and the whole step. Waits for the
+ * step to finish. Any output may be NULL. */
+ipm_status ipm_step_timing(ipm_ctx* ctx, float* newton_ms, float* update_ms, float* total_ms);
+
+/* Wait for the context's stream and fill *stats with the counters of the last step or solve. */
+ipm_status ipm_sync_stats(ipm_ctx* ctx, ipm_stats* stats);
+
+/* Host-only: the basis and quadrature tables the library uses (no GPU needed).
+ * indices: N*p ints (graded order), nodes: Q*p doubles, weights: Q doubles (density folded in,
+ * summing to 1), phi: Q*N doubles with phi[k*N + i] = phi_i(xi_k). Any output may be NULL.
+ * Returns IPM_EINVAL if p is outside 1..3 or a size exceeds the given capacities (N_cap, Q_cap). */
+ipm_status ipm_tables(int p, int total_degree, int n_per_dim, int N_cap, int Q_cap,
+                      int* indices, double* nodes, double* weights, double* phi, int* N_out, int* Q_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPM_H */

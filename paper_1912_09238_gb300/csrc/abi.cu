@@ -1,0 +1,546 @@
+// abi.cu -- the extern "C" entry points of libipm (declared and documented in include/ipm.h).
+//
+// A context owns the resident device state of one IPM problem: tables (Phi, Phi^T, weights,
+// nodes, moment pairs), moments u_hat and duals lambda [cell][moment][variable], nodal states
+// [cell][variable][node], per-cell counters, the step scalars, and the CUDA graphs of one
+// Algorithm-1 step and one Algorithm-2 step.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ipm_host.h"
+
+using namespace ipm;
+
+struct ipm_ctx {
+  ipm_problem prob;
+  ipm_basis basis;
+  ipm_quadrature quad;
+  ipm_entropy ent;
+  ipm_options opt;
+  HostTables tab;
+  int m = 0, N = 0, Q = 0, NM = 0, n_cells = 0, n_interior = 0;
+  int phys = 0, entk = 0;
+  double dx = 0.0;
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  // device state
+  double *d_Phi = nullptr, *d_PhiT = nullptr, *d_w = nullptr, *d_nodes = nullptr;
+  uint32_t* d_pairs = nullptr;
+  double *d_uhat = nullptr, *d_lam = nullptr, *d_unode = nullptr, *d_cell_resid = nullptr, *d_hwork = nullptr;
+  int *d_iters = nullptr, *d_status = nullptr, *d_ghost_list = nullptr;
+  StepScalars* d_sc = nullptr;
+  int n_fixed_ghosts = 0;
+  // launch configuration
+  size_t newton_smem = 0;
+  bool h_in_smem = true;
+  int newton_grid = 0;
+  size_t hwork_stride = 0;
+  int update_grid = 0;
+  // timing events recorded inside every step (begin, after Newton, after update, end)
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // graphs
+  cudaGraphExec_t step_exec = nullptr;
+  cudaGraphExec_t oneshot_exec = nullptr;
+  std::string err;
+};
+
+static std::mutex g_err_mu;
+static std::string g_init_err;
+
+static ipm_status fail(ipm_ctx* c, ipm_status s, const std::string& msg) {
+  if (c) {
+    c->err = msg;
+  } else {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_init_err = msg;
+  }
+  return s;
+}
+
+#define IPM_CK(ctx, call)                                                                               \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess)                                                                              \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? IPM_ENOMEM : IPM_ECUDA,                        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                                 \
+  } while (0)
+
+static Tables dev_tables(const ipm_ctx* c) {
+  Tables t;
+  t.Phi = c->d_Phi;
+  t.PhiT = c->d_PhiT;
+  t.w = c->d_w;
+  t.nodes = c->d_nodes;
+  t.pairs = c->d_pairs;
+  t.N = c->N;
+  t.Q = c->Q;
+  t.p = c->tab.p;
+  return t;
+}
+
+static EntParams ent_params(const ipm_ctx* c) {
+  EntParams e;
+  e.u_minus = c->ent.u_minus;
+  e.u_plus = c->ent.u_plus;
+  e.gamma = c->prob.gamma;
+  return e;
+}
+
+static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
+  NewtonArgs a;
+  a.tab = dev_tables(c);
+  a.ent = ent_params(c);
+  a.uhat = c->d_uhat;
+  a.lam = c->d_lam;
+  a.unode = c->d_unode;
+  a.iters = c->d_iters;
+  a.status = c->d_status;
+  a.hwork = c->d_hwork;
+  a.hwork_stride = c->hwork_stride;
+  a.sc = c->d_sc;
+  a.cell_list = nullptr;
+  a.n_work = c->n_interior;
+  a.nx = c->prob.nx;
+  a.gy = 0;
+  a.one_step = one_step;
+  a.tau = c->opt.newton_tol;
+  a.armijo_c = c->opt.armijo_c;
+  a.slack_rel = c->opt.slack_rel;
+  a.max_newton = c->opt.max_newton;
+  a.max_halvings = c->opt.max_halvings;
+  a.track_speed = 1;
+  return a;
+}
+
+static Update1DArgs update_args(const ipm_ctx* c, double dt_override, bool resid) {
+  Update1DArgs u;
+  u.tab = dev_tables(c);
+  u.uhat = c->d_uhat;
+  u.lam = c->d_lam;
+  u.unode = c->d_unode;
+  u.cell_resid = resid ? c->d_cell_resid : nullptr;
+  u.sc = c->d_sc;
+  u.nx = c->prob.nx;
+  u.bc_left = c->prob.bc_left;
+  u.bc_right = c->prob.bc_right;
+  u.dx = c->dx;
+  u.cfl = c->prob.cfl;
+  u.t_end = c->prob.t_end;
+  u.gamma = c->prob.gamma;
+  u.dt_override = dt_override;
+  return u;
+}
+
+// enqueue: queue reset, Newton over the interior
+static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  NewtonArgs a = newton_args(c, one_step);
+  return launch_newton_phys(c->entk, c->phys, c->m, a, c->newton_grid, c->newton_smem, c->h_in_smem, s);
+}
+
+// one step of Algorithm 1 (one_step = 0) or Algorithm 2 (one_step = 1)
+static cudaError_t enqueue_step(ipm_ctx* c, int one_step, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(c->ev[0], s);
+  if (e == cudaSuccess) e = enqueue_newton(c, one_step, s);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev[1], s);
+  if (e != cudaSuccess) return e;
+  Update1DArgs u = update_args(c, 0.0, true);
+  e = launch_update1d(c->phys, c->m, u, c->update_grid, s);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev[2], s);
+  if (e == cudaSuccess)
+    e = launch_finalize(c->d_sc, c->d_iters, c->d_status, c->d_cell_resid, c->n_cells, 1, c->n_interior, 1, s);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev[3], s);
+  return e;
+}
+
+static ipm_status build_graph(ipm_ctx* c, int one_step, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  IPM_CK(c, cudaStreamBeginCapture(c->own_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_step(c, one_step, c->own_stream);
+  cudaError_t e2 = cudaStreamEndCapture(c->own_stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(c, IPM_ECUDA, std::string("capture of the step: ") + cudaGetErrorString(e));
+  }
+  IPM_CK(c, e2);
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  IPM_CK(c, e);
+  return IPM_OK;
+}
+
+static void free_ctx(ipm_ctx* c) {
+  if (!c) return;
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  for (cudaEvent_t ev : c->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (c->oneshot_exec) cudaGraphExecDestroy(c->oneshot_exec);
+  void* ptrs[] = {c->d_Phi, c->d_PhiT, c->d_w, c->d_nodes, c->d_pairs, c->d_uhat, c->d_lam, c->d_unode,
+                  c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+template <typename T>
+static cudaError_t upload(T** dst, const std::vector<T>& src) {
+  cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(1, src.size()) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (src.empty()) return cudaSuccess;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+extern "C" {
+
+void ipm_default_options(ipm_options* o) {
+  if (!o) return;
+  o->precision = IPM_PREC_FP64;
+  o->newton_tol = 1e-10;
+  o->max_newton = 100;
+  o->armijo_c = 1e-4;
+  o->max_halvings = 30;
+  o->slack_rel = 1e-12;
+}
+
+const char* ipm_last_error(const ipm_ctx* c) {
+  if (c) return c->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_init_err.c_str();
+}
+
+ipm_status ipm_tables(int p, int total_degree, int n_per_dim, int N_cap, int Q_cap, int* indices, double* nodes,
+                      double* weights, double* phi, int* N_out, int* Q_out) {
+  if (p < 1 || p > 3 || total_degree < 0 || n_per_dim < 1) return fail(nullptr, IPM_EINVAL, "ipm_tables: bad sizes");
+  HostTables t;
+  build_tables(p, total_degree, n_per_dim, t);
+  if (N_out) *N_out = t.N;
+  if (Q_out) *Q_out = t.Q;
+  if (t.N > N_cap || t.Q > Q_cap) return fail(nullptr, IPM_EINVAL, "ipm_tables: capacity too small");
+  if (indices) std::memcpy(indices, t.indices.data(), t.indices.size() * sizeof(int));
+  if (nodes) std::memcpy(nodes, t.nodes.data(), t.nodes.size() * sizeof(double));
+  if (weights) std::memcpy(weights, t.w.data(), t.w.size() * sizeof(double));
+  if (phi) std::memcpy(phi, t.Phi.data(), t.Phi.size() * sizeof(double));
+  return IPM_OK;
+}
+
+ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad,
+                    const ipm_entropy* entropy, const ipm_options* options, ipm_ctx** out) {
+  if (!problem || !basis || !quad || !entropy || !out) return fail(nullptr, IPM_EINVAL, "ipm_init: NULL argument");
+  *out = nullptr;
+  ipm_options opt;
+  if (options) opt = *options;
+  else ipm_default_options(&opt);
+  if (basis->p < 1 || basis->p > 3 || basis->total_degree < 0 || quad->n_per_dim < 1)
+    return fail(nullptr, IPM_EINVAL, "ipm_init: basis needs 1 <= p <= 3, M >= 0, n_per_dim >= 1");
+  if (problem->kind != IPM_BURGERS_1D && problem->kind != IPM_EULER_1D)
+    return fail(nullptr, IPM_EINVAL, "ipm_init: only 1-D problems are built in this version");
+  if (problem->nx < 1 || !(problem->x_hi > problem->x_lo) || !(problem->cfl > 0))
+    return fail(nullptr, IPM_EINVAL, "ipm_init: bad mesh or cfl");
+  if ((problem->bc_left == IPM_BC_PERIODIC) != (problem->bc_right == IPM_BC_PERIODIC))
+    return fail(nullptr, IPM_EINVAL, "ipm_init: periodic must be set on both ends");
+  if (opt.precision != IPM_PREC_FP64)
+    return fail(nullptr, IPM_EINVAL, "ipm_init: this build provides the FP64 path only");
+
+  ipm_ctx* c = new ipm_ctx();
+  c->prob = *problem;
+  c->basis = *basis;
+  c->quad = *quad;
+  c->ent = *entropy;
+  c->opt = opt;
+  c->m = problem->kind == IPM_BURGERS_1D ? 1 : 3;
+  c->phys = problem->kind == IPM_BURGERS_1D ? PHYS_BURGERS : PHYS_EULER1D;
+  c->entk = entropy->kind == IPM_ENTROPY_QUADRATIC ? ENT_QUADRATIC
+                                                     : (entropy->kind == IPM_ENTROPY_BOUNDED_BARRIER ? ENT_BARRIER : ENT_EULER);
+  const bool ent_ok = c->entk == ENT_QUADRATIC || (c->entk == ENT_BARRIER && c->phys == PHYS_BURGERS) ||
+                      (c->entk == ENT_EULER && c->phys != PHYS_BURGERS);
+  if (!ent_ok) {
+    delete c;
+    return fail(nullptr, IPM_EINVAL, "ipm_init: entropy does not match the problem");
+  }
+  if (c->entk == ENT_BARRIER && !(entropy->u_plus > entropy->u_minus)) {
+    delete c;
+    return fail(nullptr, IPM_EINVAL, "ipm_init: barrier needs u_plus > u_minus");
+  }
+  build_tables(basis->p, basis->total_degree, quad->n_per_dim, c->tab);
+  c->N = c->tab.N;
+  c->Q = c->tab.Q;
+  c->NM = c->N * c->m;
+  c->n_interior = problem->nx;
+  c->n_cells = problem->nx + 2;
+  c->dx = (problem->x_hi - problem->x_lo) / problem->nx;
+  if (c->N > 65535) {
+    delete c;
+    return fail(nullptr, IPM_EINVAL, "ipm_init: too many moments");
+  }
+
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, IPM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  }
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, c->device);
+  // launch configuration of the Newton kernel: packed H in shared memory when it fits
+  const size_t smem_full = newton_smem_bytes(c->N, c->m, c->Q, true);
+  const size_t smem_lean = newton_smem_bytes(c->N, c->m, c->Q, false);
+  if (smem_lean > (size_t)prop.sharedMemPerBlockOptin) {
+    delete c;
+    return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for one CTA");
+  }
+  c->h_in_smem = smem_full <= (size_t)prop.sharedMemPerBlockOptin;
+  c->newton_smem = c->h_in_smem ? smem_full : smem_lean;
+  {
+    // persistent grid: resident CTAs per SM (occupancy API) times the SM count
+    int bps = 0;
+    e = prepare_newton(c->entk, c->phys, c->m, c->newton_smem, c->h_in_smem, &bps);
+    if (e == cudaSuccess) e = prepare_update1d(c->phys, c->m, c->Q);
+    if (e != cudaSuccess || bps < 1) {
+      delete c;
+      return fail(nullptr, IPM_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
+    }
+    c->newton_grid = std::max(1, std::min(c->n_interior, bps * prop.multiProcessorCount));
+  }
+  c->hwork_stride = c->h_in_smem ? 0 : (size_t)c->NM * (c->NM + 1) / 2;
+  c->update_grid = std::min(c->n_interior, 65535);
+
+  ipm_status st = IPM_OK;
+  auto CK = [&](cudaError_t err, const char* what) {
+    if (err != cudaSuccess && st == IPM_OK) {
+      st = fail(nullptr, err == cudaErrorMemoryAllocation ? IPM_ENOMEM : IPM_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(err));
+    }
+  };
+  CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  for (cudaEvent_t& ev : c->ev) CK(cudaEventCreate(&ev), "cudaEventCreate");
+  c->stream = c->own_stream;
+  CK(upload(&c->d_Phi, c->tab.Phi), "upload Phi");
+  CK(upload(&c->d_PhiT, c->tab.PhiT), "upload PhiT");
+  CK(upload(&c->d_w, c->tab.w), "upload w");
+  CK(upload(&c->d_nodes, c->tab.nodes), "upload nodes");
+  CK(upload(&c->d_pairs, c->tab.pairs), "upload pairs");
+  const size_t nstate = (size_t)c->n_cells * c->NM;
+  CK(cudaMalloc(&c->d_uhat, nstate * sizeof(double)), "cudaMalloc uhat");
+  CK(cudaMalloc(&c->d_lam, nstate * sizeof(double)), "cudaMalloc lam");
+  CK(cudaMalloc(&c->d_unode, (size_t)c->n_cells * c->m * c->Q * sizeof(double)), "cudaMalloc unode");
+  CK(cudaMalloc(&c->d_cell_resid, (size_t)c->n_cells * sizeof(double)), "cudaMalloc resid");
+  CK(cudaMalloc(&c->d_iters, (size_t)c->n_cells * sizeof(int)), "cudaMalloc iters");
+  CK(cudaMalloc(&c->d_status, (size_t)c->n_cells * sizeof(int)), "cudaMalloc status");
+  CK(cudaMalloc(&c->d_sc, sizeof(StepScalars)), "cudaMalloc scalars");
+  if (!c->h_in_smem) CK(cudaMalloc(&c->d_hwork, (size_t)c->newton_grid * c->hwork_stride * sizeof(double)), "cudaMalloc hwork");
+  if (st != IPM_OK) {
+    free_ctx(c);
+    return st;
+  }
+  CK(cudaMemsetAsync(c->d_sc, 0, sizeof(StepScalars), c->stream), "memset scalars");
+  CK(cudaMemsetAsync(c->d_iters, 0, (size_t)c->n_cells * sizeof(int), c->stream), "memset iters");
+  CK(cudaMemsetAsync(c->d_status, 0, (size_t)c->n_cells * sizeof(int), c->stream), "memset status");
+  CK(cudaMemsetAsync(c->d_cell_resid, 0, (size_t)c->n_cells * sizeof(double), c->stream), "memset resid");
+  CK(cudaMemsetAsync(c->d_unode, 0, (size_t)c->n_cells * c->m * c->Q * sizeof(double), c->stream), "memset unode");
+  // initial data on every cell, then the boundary copies
+  CK(launch_init1d(c->entk, c->m, dev_tables(c), ent_params(c), c->prob, c->d_uhat, c->d_lam, c->n_cells, c->stream),
+     "init kernel");
+  CK(launch_bc_copy1d(c->d_uhat, c->d_lam, problem->nx, c->NM, problem->bc_left, problem->bc_right, c->stream),
+     "bc kernel");
+  // Dirichlet ghosts: converge their duals once; their speed stays part of every dt
+  std::vector<int> ghosts;
+  if (problem->bc_left == IPM_BC_DIRICHLET) ghosts.push_back(0);
+  if (problem->bc_right == IPM_BC_DIRICHLET) ghosts.push_back(problem->nx + 1);
+  c->n_fixed_ghosts = (int)ghosts.size();
+  if (!ghosts.empty()) {
+    CK(upload(&c->d_ghost_list, ghosts), "upload ghosts");
+    if (st == IPM_OK) {
+      NewtonArgs a = newton_args(c, 0);
+      a.cell_list = c->d_ghost_list;
+      a.n_work = (int)ghosts.size();
+      CK(launch_newton_phys(c->entk, c->phys, c->m, a, std::min(c->newton_grid, (int)ghosts.size()), c->newton_smem,
+                            c->h_in_smem, c->stream),
+         "ghost solve");
+    }
+  }
+  if (st == IPM_OK) {
+    // fixed speed = what the ghost solve folded in (0 without Dirichlet ghosts); then reset counters
+    StepScalars h;
+    CK(cudaMemcpyAsync(&h, c->d_sc, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->stream), "read scalars");
+    CK(cudaStreamSynchronize(c->stream), "init sync");
+    if (st == IPM_OK) {
+      int gstat[2] = {0, 0};
+      for (size_t k = 0; k < ghosts.size(); ++k)
+        cudaMemcpy(&gstat[k], c->d_status + ghosts[k], sizeof(int), cudaMemcpyDeviceToHost);
+      for (size_t k = 0; k < ghosts.size(); ++k)
+        if (gstat[k] != 0) st = fail(nullptr, IPM_EINVAL, "ipm_init: Dirichlet ghost dual solve failed");
+      h.fixed_smax_bits = h.smax_bits;
+      h.work_counter = 0;
+      h.update_counter = 0;
+      h.t = 0.0;
+      h.dt = 0.0;
+      h.steps = 0;
+      CK(cudaMemcpy(c->d_sc, &h, sizeof(StepScalars), cudaMemcpyHostToDevice), "write scalars");
+    }
+  }
+  if (st == IPM_OK) st = build_graph(c, 0, &c->step_exec);
+  if (st == IPM_OK) st = build_graph(c, 1, &c->oneshot_exec);
+  if (st != IPM_OK) {
+    if (!c->err.empty()) fail(nullptr, st, c->err);
+    free_ctx(c);
+    return st;
+  }
+  *out = c;
+  return IPM_OK;
+}
+
+void ipm_destroy(ipm_ctx* c) {
+  if (c && c->stream) cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+ipm_status ipm_get_dims(const ipm_ctx* c, ipm_dims* d) {
+  if (!c || !d) return IPM_EINVAL;
+  d->N = c->N;
+  d->m = c->m;
+  d->Q = c->Q;
+  d->p = c->tab.p;
+  d->n_cells = c->n_cells;
+  d->n_interior = c->n_interior;
+  return IPM_OK;
+}
+
+ipm_status ipm_set_stream(ipm_ctx* c, void* s) {
+  if (!c) return IPM_EINVAL;
+  IPM_CK(c, cudaStreamSynchronize(c->stream));
+  c->stream = s ? static_cast<cudaStream_t>(s) : c->own_stream;
+  return IPM_OK;
+}
+
+static ipm_status copy_state(ipm_ctx* c, void* dst, const void* src, size_t count, size_t expect, cudaMemcpyKind kind,
+                             bool sync) {
+  if (!c || (!dst && count) || (!src && count)) return fail(c, IPM_EINVAL, "copy: NULL pointer");
+  if (count != expect) return fail(c, IPM_EINVAL, "copy: count does not match the state size");
+  IPM_CK(c, cudaMemcpyAsync(dst, src, count * sizeof(double), kind, c->stream));
+  if (sync) IPM_CK(c, cudaStreamSynchronize(c->stream));
+  return IPM_OK;
+}
+
+ipm_status ipm_set_moments(ipm_ctx* c, const double* h, size_t n) {
+  if (!c) return IPM_EINVAL;
+  return copy_state(c, c->d_uhat, h, n, (size_t)c->n_cells * c->NM, cudaMemcpyHostToDevice, true);
+}
+ipm_status ipm_get_moments(ipm_ctx* c, double* h, size_t n) {
+  if (!c) return IPM_EINVAL;
+  return copy_state(c, h, c->d_uhat, n, (size_t)c->n_cells * c->NM, cudaMemcpyDeviceToHost, true);
+}
+ipm_status ipm_set_duals(ipm_ctx* c, const double* h, size_t n) {
+  if (!c) return IPM_EINVAL;
+  return copy_state(c, c->d_lam, h, n, (size_t)c->n_cells * c->NM, cudaMemcpyHostToDevice, true);
+}
+ipm_status ipm_get_duals(ipm_ctx* c, double* h, size_t n) {
+  if (!c) return IPM_EINVAL;
+  return copy_state(c, h, c->d_lam, n, (size_t)c->n_cells * c->NM, cudaMemcpyDeviceToHost, true);
+}
+ipm_status ipm_get_nodal_states(ipm_ctx* c, double* h, size_t n) {
+  if (!c) return IPM_EINVAL;
+  return copy_state(c, h, c->d_unode, n, (size_t)c->n_cells * c->m * c->Q, cudaMemcpyDeviceToHost, true);
+}
+ipm_status ipm_set_moments_device(ipm_ctx* c, const double* d, size_t n) {
+  if (!c) return IPM_EINVAL;
+  return copy_state(c, c->d_uhat, d, n, (size_t)c->n_cells * c->NM, cudaMemcpyDeviceToDevice, false);
+}
+ipm_status ipm_get_moments_device(ipm_ctx* c, double* d, size_t n) {
+  if (!c) return IPM_EINVAL;
+  return copy_state(c, d, c->d_uhat, n, (size_t)c->n_cells * c->NM, cudaMemcpyDeviceToDevice, false);
+}
+
+static void fill_stats(const StepScalars& h, ipm_stats* s) {
+  s->newton_iters = h.newton_iters;
+  s->max_iters = h.max_iters;
+  s->failed_cells = h.failed_cells;
+  s->first_failed_cell = h.first_failed_cell;
+  s->first_status = h.first_status;
+  s->dt = h.dt;
+  s->t = h.t;
+  s->residual = h.residual;
+  s->steps = h.steps;
+}
+
+ipm_status ipm_sync_stats(ipm_ctx* c, ipm_stats* s) {
+  if (!c || !s) return IPM_EINVAL;
+  StepScalars h;
+  IPM_CK(c, cudaMemcpyAsync(&h, c->d_sc, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->stream));
+  IPM_CK(c, cudaStreamSynchronize(c->stream));
+  fill_stats(h, s);
+  return IPM_OK;
+}
+
+ipm_status ipm_dual_solve(ipm_ctx* c, ipm_stats* s) {
+  if (!c) return IPM_EINVAL;
+  IPM_CK(c, enqueue_newton(c, 0, c->stream));
+  IPM_CK(c, launch_finalize(c->d_sc, c->d_iters, c->d_status, nullptr, c->n_cells, 1, c->n_interior, 0, c->stream));
+  if (s) return ipm_sync_stats(c, s);
+  return IPM_OK;
+}
+
+ipm_status ipm_update(ipm_ctx* c, double dt) {
+  if (!c) return IPM_EINVAL;
+  if (!(dt > 0.0)) return fail(c, IPM_EINVAL, "ipm_update: dt must be positive");
+  Update1DArgs u = update_args(c, dt, false);
+  IPM_CK(c, launch_update1d(c->phys, c->m, u, c->update_grid, c->stream));
+  IPM_CK(c, cudaStreamSynchronize(c->stream));
+  return IPM_OK;
+}
+
+ipm_status ipm_step(ipm_ctx* c, ipm_stats* s) {
+  if (!c) return IPM_EINVAL;
+  IPM_CK(c, cudaGraphLaunch(c->step_exec, c->stream));
+  if (s) return ipm_sync_stats(c, s);
+  return IPM_OK;
+}
+
+ipm_status ipm_oneshot_step(ipm_ctx* c, ipm_stats* s) {
+  if (!c) return IPM_EINVAL;
+  IPM_CK(c, cudaGraphLaunch(c->oneshot_exec, c->stream));
+  if (s) return ipm_sync_stats(c, s);
+  return IPM_OK;
+}
+
+ipm_status ipm_step_timing(ipm_ctx* c, float* newton_ms, float* update_ms, float* total_ms) {
+  if (!c) return IPM_EINVAL;
+  IPM_CK(c, cudaEventSynchronize(c->ev[3]));
+  float a = 0.f, b = 0.f, t = 0.f;
+  IPM_CK(c, cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
+  IPM_CK(c, cudaEventElapsedTime(&b, c->ev[1], c->ev[2]));
+  IPM_CK(c, cudaEventElapsedTime(&t, c->ev[0], c->ev[3]));
+  if (newton_ms) *newton_ms = a;
+  if (update_ms) *update_ms = b;
+  if (total_ms) *total_ms = t;
+  return IPM_OK;
+}
+
+ipm_status ipm_run(ipm_ctx* c, int64_t max_steps, ipm_stats* s) {
+  if (!c) return IPM_EINVAL;
+  if (!(c->prob.t_end > 0.0)) return fail(c, IPM_EINVAL, "ipm_run: t_end must be positive");
+  ipm_stats cur;
+  ipm_status st = ipm_sync_stats(c, &cur);
+  if (st != IPM_OK) return st;
+  int64_t done = 0;
+  while (cur.t < c->prob.t_end && done < max_steps) {
+    // launch a batch sized from the last dt; extra launches after t_end are no-ops on the device
+    int64_t batch = 16;
+    if (cur.dt > 0.0) batch = (int64_t)((c->prob.t_end - cur.t) / cur.dt) + 1;
+    batch = std::max<int64_t>(1, std::min<int64_t>(batch, std::min<int64_t>(256, max_steps - done)));
+    for (int64_t k = 0; k < batch; ++k) IPM_CK(c, cudaGraphLaunch(c->step_exec, c->stream));
+    done += batch;
+    st = ipm_sync_stats(c, &cur);
+    if (st != IPM_OK) return st;
+    if (cur.failed_cells) break;
+  }
+  if (s) *s = cur;
+  return IPM_OK;
+}
+
+}  // extern "C"

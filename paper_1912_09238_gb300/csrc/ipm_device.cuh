@@ -1,0 +1,285 @@
+// ipm_device.cuh -- device-side closures, fluxes and launch-argument structs of the IPM library.
+//
+// Entropy closures (Sec. 3.1: u_s = (grad s)^-1; Sec. 2, Eq. dualProblem: s_*; App. B for Euler):
+//   per quadrature node the kernels need u_s(Lambda), its Jacobian grad u_s(Lambda) (symmetric,
+//   stored packed a <= b) and s_*(Lambda) for the dual cost L of Eq. L.
+//
+// Euler (App. B, written with beta = -Lambda_E > 0 and k = 1/(gamma-1)):
+//   ln rho = k (Lambda_1 - gamma - ln beta + |Lambda_v|^2 / (2 beta)),   v = Lambda_v / beta,
+//   E = rho (1/beta + |v|^2/2),   s_* = (gamma-1) rho,   speed = max_d |v_d| + sqrt(gamma (gamma-1) / beta).
+//   This is App. B's alpha with the exponent's gamma term taken as +2 gamma Lambda_E (the printed sign
+//   does not invert grad s). Since grad s_* = u_s and grad rho = k u, the Jacobian is
+//   grad u_s = rho [k g g^T + G],  g = (1, v, E/rho),
+//   G = [[0, 0, 0], [0, I/beta, v/beta], [0, v^T/beta, 1/beta^2 + |v|^2/beta]].
+// Bounded barrier (scalar): u = u_- + D sigma(Lambda), D = u_+ - u_-, grad u_s = D sigma (1 - sigma),
+//   s_* = D softplus(Lambda) + u_- Lambda - D ln D.
+// Quadratic: u = Lambda, grad u_s = I, s_* = |Lambda|^2 / 2 (stochastic Galerkin).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ipm {
+
+enum EntKind { ENT_QUADRATIC = 0, ENT_BARRIER = 1, ENT_EULER = 2 };
+enum PhysKind { PHYS_BURGERS = 0, PHYS_EULER1D = 1, PHYS_EULER2D = 2 };
+
+// per-cell status codes (values of ipm_status)
+enum CellStatus { ST_OK = 0, ST_NOCONV = 3, ST_NOTSPD = 4, ST_INFEASIBLE = 5, ST_LINESEARCH = 6, ST_NONFINITE = 7 };
+
+struct EntParams {
+  double u_minus, u_plus, gamma;
+};
+
+__host__ __device__ constexpr int packed_count(int m) { return m * (m + 1) / 2; }
+// index of (a, b), a <= b, in the packed upper triangle of an m x m symmetric matrix
+__host__ __device__ constexpr int packed_ab(int a, int b, int m) { return a * m - a * (a - 1) / 2 + (b - a); }
+
+#ifdef __CUDACC__
+// ------------------------------------------------------------------------------------------------
+// Closures: evaluate at one node. Lam[M] in; u[M], J[packed], sstar, speed out. Returns feasibility.
+// ------------------------------------------------------------------------------------------------
+template <int ENT, int M>
+struct Closure;
+
+template <int M>
+struct Closure<ENT_QUADRATIC, M> {
+  template <bool WANT_J>
+  __device__ static bool eval(const double* L, const EntParams&, double* u, double* J, double& sstar) {
+    double s = 0.0;
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+      u[a] = L[a];
+      s = fma(L[a], L[a], s);
+      ok = ok && isfinite(L[a]);
+    }
+    sstar = 0.5 * s;
+    if (WANT_J) {
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = a; b < M; ++b) J[packed_ab(a, b, M)] = (a == b) ? 1.0 : 0.0;
+    }
+    return ok;
+  }
+  __device__ static bool feasible_sstar(const double* L, const EntParams& p, double& sstar) {
+    double u[M];
+    return eval<false>(L, p, u, nullptr, sstar);
+  }
+};
+
+template <>
+struct Closure<ENT_BARRIER, 1> {
+  template <bool WANT_J>
+  __device__ static bool eval(const double* L, const EntParams& p, double* u, double* J, double& sstar) {
+    const double x = L[0];
+    const double D = p.u_plus - p.u_minus;
+    const double ex = exp(-fabs(x));
+    const double inv = 1.0 / (1.0 + ex);
+    const double sig = (x >= 0.0) ? inv : ex * inv;          // logistic(x) without overflow
+    u[0] = p.u_minus + D * sig;
+    if (WANT_J) J[0] = D * ex * inv * inv;                     // D sigma (1 - sigma)
+    sstar = D * (fmax(x, 0.0) + log1p(ex)) + p.u_minus * x - D * log(D);
+    return isfinite(x);
+  }
+  __device__ static bool feasible_sstar(const double* L, const EntParams& p, double& sstar) {
+    double u[1];
+    return eval<false>(L, p, u, nullptr, sstar);
+  }
+};
+
+template <int M>
+struct Closure<ENT_EULER, M> {
+  static constexpr int D = M - 2;
+  template <bool WANT_J>
+  __device__ static bool eval(const double* L, const EntParams& p, double* u, double* J, double& sstar) {
+    const double g = p.gamma;
+    const double k = 1.0 / (g - 1.0);
+    const double LE = L[M - 1];
+    if (!(LE < 0.0)) {
+      sstar = 0.0;
+#pragma unroll
+      for (int a = 0; a < M; ++a) u[a] = 0.0;
+      return false;
+    }
+    const double beta = -LE;
+    const double ib = 1.0 / beta;
+    double lvsq = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) lvsq = fma(L[1 + d], L[1 + d], lvsq);
+    const double lnrho = k * (L[0] - g - log(beta) + 0.5 * lvsq * ib);
+    const double rho = exp(lnrho);
+    double v[D > 0 ? D : 1];
+    double vsq = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      v[d] = L[1 + d] * ib;
+      vsq = fma(v[d], v[d], vsq);
+    }
+    const double e = ib + 0.5 * vsq;                          // E / rho
+    u[0] = rho;
+#pragma unroll
+    for (int d = 0; d < D; ++d) u[1 + d] = rho * v[d];
+    u[M - 1] = rho * e;
+    sstar = (g - 1.0) * rho;
+    const bool ok = (rho > 0.0) && isfinite(rho) && isfinite(e);
+    if (WANT_J) {
+      double gv[M];
+      gv[0] = 1.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) gv[1 + d] = v[d];
+      gv[M - 1] = e;
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = a; b < M; ++b) {
+          double G = 0.0;
+          if (a >= 1 && a <= D && b >= 1 && b <= D) G = (a == b) ? ib : 0.0;
+          else if (a >= 1 && a <= D && b == M - 1) G = v[a - 1] * ib;
+          else if (a == M - 1 && b == M - 1) G = ib * ib + vsq * ib;
+          J[packed_ab(a, b, M)] = rho * fma(k * gv[a], gv[b], G);
+        }
+    }
+    return ok;
+  }
+  __device__ static bool feasible_sstar(const double* L, const EntParams& p, double& sstar) {
+    double u[M];
+    return eval<false>(L, p, u, nullptr, sstar);
+  }
+  // fastest signal speed from the dual state (used at the converged duals)
+  __device__ static double speed_from_dual(const double* L, const EntParams& p) {
+    const double beta = -L[M - 1];
+    double vmax = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) vmax = fmax(vmax, fabs(L[1 + d] / beta));
+    return vmax + sqrt(p.gamma * (p.gamma - 1.0) / beta);
+  }
+};
+
+// grad s(u): entropy variables of a conserved state (initial duals only).
+template <int ENT, int M>
+__device__ inline void entropy_gradient(const double* u, const EntParams& p, double* out) {
+  if (ENT == ENT_QUADRATIC) {
+#pragma unroll
+    for (int a = 0; a < M; ++a) out[a] = u[a];
+  } else if (ENT == ENT_BARRIER) {
+    out[0] = log(u[0] - p.u_minus) - log(p.u_plus - u[0]);
+  } else {
+    constexpr int D = M - 2;
+    const double rho = u[0], E = u[M - 1];
+    double msq = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) msq = fma(u[1 + d], u[1 + d], msq);
+    const double eps = E - 0.5 * msq / rho;                   // internal energy density
+    out[0] = -log(pow(rho, -p.gamma) * eps) - 0.5 * msq / (rho * eps) + p.gamma;
+#pragma unroll
+    for (int d = 0; d < D; ++d) out[1 + d] = u[1 + d] / eps;
+    out[M - 1] = -rho / eps;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Physics on conserved states (Burgers App. A; Euler Sec. 7.1).
+// ------------------------------------------------------------------------------------------------
+template <int PHYS, int M>
+struct Physics;
+
+template <>
+struct Physics<PHYS_BURGERS, 1> {
+  __device__ static void flux(const double* u, double, double* f) { f[0] = 0.5 * u[0] * u[0]; }
+  __device__ static double speed(const double* u, double) { return fabs(u[0]); }
+};
+
+template <>
+struct Physics<PHYS_EULER1D, 3> {
+  __device__ static void flux(const double* u, double g, double* f) {
+    const double v = u[1] / u[0];
+    const double p = (g - 1.0) * (u[2] - 0.5 * u[1] * v);
+    f[0] = u[1];
+    f[1] = u[1] * v + p;
+    f[2] = (u[2] + p) * v;
+  }
+  __device__ static double speed(const double* u, double g) {
+    const double v = u[1] / u[0];
+    const double p = (g - 1.0) * (u[2] - 0.5 * u[1] * v);
+    return fabs(v) + sqrt(g * p / u[0]);
+  }
+};
+
+#endif  // __CUDACC__
+
+// ------------------------------------------------------------------------------------------------
+// Launch arguments
+// ------------------------------------------------------------------------------------------------
+struct Tables {
+  const double* Phi;     // [Q][N]  phi_i(xi_k)
+  const double* PhiT;    // [N][Q]
+  const double* w;       // [Q]     weights with the density folded in
+  const double* nodes;   // [Q][p]
+  const uint32_t* pairs; // [N(N+1)/2] (i << 16) | j with i >= j, row-major over i
+  int N, Q, p;
+};
+
+struct StepScalars {
+  unsigned long long smax_bits;  // max signal speed over cells and nodes (positive double bits)
+  unsigned long long fixed_smax_bits; // speed of the fixed (Dirichlet) ghosts
+  int work_counter;              // persistent-queue counter of the Newton kernel
+  int update_counter;
+  double t;                      // current time
+  double dt;                     // last time step
+  double residual;               // last steady residual
+  int64_t steps;
+  int64_t newton_iters;
+  int max_iters;
+  int failed_cells;
+  int first_failed_cell;
+  int first_status;
+};
+
+struct NewtonArgs {
+  Tables tab;
+  EntParams ent;
+  double* uhat;          // [C][N][m]
+  double* lam;           // [C][N][m]
+  double* unode;         // [C][m][Q]  nodal states at the final duals
+  int* iters;            // [C]
+  int* status;           // [C]
+  double* hwork;         // global workspace for packed Hessians when they do not fit in shared memory
+  size_t hwork_stride;   // doubles per CTA slot
+  StepScalars* sc;
+  const int* cell_list;  // explicit cell indices, or nullptr for the interior of the mesh
+  int n_work;            // number of cells to process
+  int nx, gy;            // interior mapping: cell = (w / nx + gy) * (nx + 2) + (w % nx + 1)
+  int one_step;          // 1: exactly one damped Newton step (Algorithm 2)
+  double tau, armijo_c, slack_rel;
+  int max_newton, max_halvings;
+  int track_speed;       // 1: fold the nodal signal speeds of the result into sc->smax_bits
+};
+
+struct Update1DArgs {
+  Tables tab;
+  double* uhat;          // [C][N][m]  (written for interior cells and outflow/periodic ghosts)
+  double* lam;           // [C][N][m]  (ghost copies only)
+  const double* unode;   // [C][m][Q]
+  double* cell_resid;    // [C] per-cell contribution to the steady residual
+  StepScalars* sc;
+  int nx;
+  int bc_left, bc_right;
+  double dx, cfl, t_end, gamma;
+  double dt_override;    // > 0: use this dt instead of the CFL rule
+};
+
+#ifdef __CUDACC__
+// positive doubles order like their bit patterns
+__device__ inline void atomic_max_pos(unsigned long long* addr, double v) {
+  if (v > 0.0) atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+#endif  // __CUDACC__
+
+}  // namespace ipm

@@ -1,0 +1,42 @@
+// ipm_host.h -- host-side internals shared by the translation units of libipm.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ipm.h"
+#include "ipm_device.cuh"
+
+namespace ipm {
+
+struct HostTables {
+  int p = 0, M = 0, N = 0, Q = 0;
+  std::vector<int> indices;     // [N][p]
+  std::vector<double> nodes;    // [Q][p]
+  std::vector<double> w;        // [Q]
+  std::vector<double> Phi;      // [Q][N]
+  std::vector<double> PhiT;     // [N][Q]
+  std::vector<uint32_t> pairs;  // [N(N+1)/2]
+};
+
+void gauss_legendre_1d(int n, std::vector<double>& x, std::vector<double>& w);
+void build_tables(int p, int M, int nq, HostTables& t);
+
+// kernel launchers (newton.cu, update.cu)
+size_t newton_smem_bytes(int N, int m, int Q, bool h_in_smem);
+int newton_threads();
+cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, int grid, size_t smem, bool h_in_smem,
+                               cudaStream_t s);
+cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, int* blocks_per_sm);
+cudaError_t prepare_update1d(int phys, int m, int Q);
+cudaError_t launch_update1d(int phys, int m, const Update1DArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_init1d(int ent, int m, const Tables& tab, const EntParams& ent_p, const ipm_problem& prob,
+                          double* uhat, double* lam, int n_cells, cudaStream_t s);
+cudaError_t launch_finalize(StepScalars* sc, const int* iters, const int* status, const double* cell_resid,
+                            int n_cells, int first, int count, int advance_time, cudaStream_t s);
+cudaError_t launch_bc_copy1d(double* uhat, double* lam, int nx, int Nm, int bc_left, int bc_right,
+                             cudaStream_t s);
+
+}  // namespace ipm

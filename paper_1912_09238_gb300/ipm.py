@@ -1,0 +1,263 @@
+"""Thin ctypes binding of libipm (include/ipm.h). Argument marshalling only: every step of the IPM
+path runs in the library's CUDA kernels. There is no CPU fallback: if libipm.so is missing or no
+CUDA device is present the calls raise."""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libipm.so")
+
+IPM_OK = 0
+STATUS_NAMES = {0: "IPM_OK", 1: "IPM_EINVAL", 2: "IPM_ENOMEM", 3: "IPM_ENOCONV", 4: "IPM_ENOTSPD",
+                5: "IPM_EINFEASIBLE", 6: "IPM_ELINESEARCH", 7: "IPM_ENONFINITE", 8: "IPM_EAGAIN",
+                9: "IPM_ECUDA", 10: "IPM_ETIMEOUT"}
+PROBLEM = {"burgers1d": 0, "euler1d": 1, "euler2d": 2}
+BC = {"outflow": 0, "periodic": 1, "dirichlet": 2}
+ENTROPY = {"quadratic": 0, "barrier": 1, "euler": 2}
+PRECISION = {"fp64": 0, "mixed": 1}
+
+
+class ipm_problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double),
+                ("bc_left", ctypes.c_int), ("bc_right", ctypes.c_int),
+                ("cfl", ctypes.c_double), ("t_end", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("ic_kind", ctypes.c_int), ("ic_x0", ctypes.c_double), ("ic_dx0", ctypes.c_double * 3),
+                ("ic_left", ctypes.c_double * 4), ("ic_dleft", (ctypes.c_double * 3) * 4),
+                ("ic_right", ctypes.c_double * 4), ("ic_dright", (ctypes.c_double * 3) * 4)]
+
+
+class ipm_basis(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("total_degree", ctypes.c_int)]
+
+
+class ipm_quadrature(ctypes.Structure):
+    _fields_ = [("n_per_dim", ctypes.c_int)]
+
+
+class ipm_entropy(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("u_minus", ctypes.c_double), ("u_plus", ctypes.c_double)]
+
+
+class ipm_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("newton_tol", ctypes.c_double), ("max_newton", ctypes.c_int),
+                ("armijo_c", ctypes.c_double), ("max_halvings", ctypes.c_int), ("slack_rel", ctypes.c_double)]
+
+
+class ipm_dims(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("m", ctypes.c_int), ("Q", ctypes.c_int), ("p", ctypes.c_int),
+                ("n_cells", ctypes.c_int), ("n_interior", ctypes.c_int)]
+
+
+class ipm_stats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int64), ("max_iters", ctypes.c_int32), ("failed_cells", ctypes.c_int32),
+                ("first_failed_cell", ctypes.c_int32), ("first_status", ctypes.c_int32),
+                ("dt", ctypes.c_double), ("t", ctypes.c_double), ("residual", ctypes.c_double),
+                ("steps", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class IpmError(RuntimeError):
+    def __init__(self, call, status, msg):
+        super().__init__(f"{call} -> {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_dp = _P(ctypes.c_double)
+
+# (name, restype, argtypes): every entry point declared in include/ipm.h
+SIGNATURES = [
+    ("ipm_default_options", None, [_P(ipm_options)]),
+    ("ipm_init", ctypes.c_int, [_P(ipm_problem), _P(ipm_basis), _P(ipm_quadrature), _P(ipm_entropy),
+                                _P(ipm_options), _P(_vp)]),
+    ("ipm_destroy", None, [_vp]),
+    ("ipm_last_error", ctypes.c_char_p, [_vp]),
+    ("ipm_get_dims", ctypes.c_int, [_vp, _P(ipm_dims)]),
+    ("ipm_set_stream", ctypes.c_int, [_vp, _vp]),
+    ("ipm_set_moments", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
+    ("ipm_get_moments", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
+    ("ipm_set_duals", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
+    ("ipm_get_duals", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
+    ("ipm_get_nodal_states", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
+    ("ipm_set_moments_device", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    ("ipm_get_moments_device", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    ("ipm_dual_solve", ctypes.c_int, [_vp, _P(ipm_stats)]),
+    ("ipm_update", ctypes.c_int, [_vp, ctypes.c_double]),
+    ("ipm_step", ctypes.c_int, [_vp, _P(ipm_stats)]),
+    ("ipm_run", ctypes.c_int, [_vp, ctypes.c_int64, _P(ipm_stats)]),
+    ("ipm_oneshot_step", ctypes.c_int, [_vp, _P(ipm_stats)]),
+    ("ipm_sync_stats", ctypes.c_int, [_vp, _P(ipm_stats)]),
+    ("ipm_step_timing", ctypes.c_int, [_vp, _P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float)]),
+    ("ipm_tables", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  _P(ctypes.c_int), _dp, _dp, _dp, _P(ctypes.c_int), _P(ctypes.c_int)]),
+]
+
+
+def lib():
+    """Load libipm.so (built in-tree by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libipm.so not found at {LIB_PATH}: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(call, status, ctx=None):
+    if status != IPM_OK:
+        msg = lib().ipm_last_error(ctx)
+        raise IpmError(call, status, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def default_options(precision="fp64", **kw):
+    o = ipm_options()
+    lib().ipm_default_options(ctypes.byref(o))
+    o.precision = PRECISION[precision]
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def ipm_tables(p, total_degree, n_per_dim):
+    """Host-only tables of the library: (indices (N,p), nodes (Q,p), weights (Q,), Phi (Q,N))."""
+    N = ctypes.c_int()
+    Q = ctypes.c_int()
+    # size query: with zero capacity the call returns IPM_EINVAL but fills N and Q
+    lib().ipm_tables(p, total_degree, n_per_dim, 0, 0, None, None, None, None, ctypes.byref(N), ctypes.byref(Q))
+    n, q = N.value, Q.value
+    idx = np.zeros((n, p), dtype=np.int32)
+    nodes = np.zeros((q, p))
+    w = np.zeros(q)
+    phi = np.zeros((q, n))
+    _check("ipm_tables", lib().ipm_tables(p, total_degree, n_per_dim, n, q, idx.ctypes.data_as(_P(ctypes.c_int)),
+                                          _dptr(nodes), _dptr(w), _dptr(phi), ctypes.byref(N), ctypes.byref(Q)))
+    return idx, nodes, w, phi
+
+
+def make_problem(kind, nx, x_lo, x_hi, bc=("outflow", "outflow"), cfl=0.5, t_end=0.0, gamma=1.4,
+                 x0=0.5, dx0=(0, 0, 0), left=(0, 0, 0, 0), dleft=None, right=(0, 0, 0, 0), dright=None):
+    pr = ipm_problem()
+    pr.kind = PROBLEM[kind]
+    pr.nx, pr.ny = nx, 1
+    pr.x_lo, pr.x_hi = x_lo, x_hi
+    pr.bc_left, pr.bc_right = BC[bc[0]], BC[bc[1]]
+    pr.cfl, pr.t_end, pr.gamma = cfl, t_end, gamma
+    pr.ic_kind = 0
+    pr.ic_x0 = x0
+    for d in range(3):
+        pr.ic_dx0[d] = dx0[d]
+    for v in range(4):
+        pr.ic_left[v] = left[v] if v < len(left) else 0.0
+        pr.ic_right[v] = right[v] if v < len(right) else 0.0
+        for d in range(3):
+            pr.ic_dleft[v][d] = dleft[v][d] if dleft is not None and v < len(dleft) else 0.0
+            pr.ic_dright[v][d] = dright[v][d] if dright is not None and v < len(dright) else 0.0
+    return pr
+
+
+class Context:
+    """One resident IPM problem on the current CUDA device (wraps ipm_ctx*)."""
+
+    def __init__(self, problem, p, total_degree, n_per_dim, entropy, u_minus=0.0, u_plus=0.0, options=None):
+        b = ipm_basis(p, total_degree)
+        q = ipm_quadrature(n_per_dim)
+        e = ipm_entropy(ENTROPY[entropy], u_minus, u_plus)
+        o = options if options is not None else default_options()
+        h = _vp()
+        _check("ipm_init", lib().ipm_init(ctypes.byref(problem), ctypes.byref(b), ctypes.byref(q), ctypes.byref(e),
+                                          ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        d = ipm_dims()
+        _check("ipm_get_dims", lib().ipm_get_dims(self.h, ctypes.byref(d)), self.h)
+        self.dims = d
+        self.shape = (d.n_cells, d.N, d.m)
+
+    def close(self):
+        if self.h:
+            lib().ipm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _get(self, fn, shape):
+        out = np.empty(shape)
+        _check(fn, getattr(lib(), fn)(self.h, _dptr(out), out.size), self.h)
+        return out
+
+    def _set(self, fn, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape)
+        _check(fn, getattr(lib(), fn)(self.h, _dptr(a), a.size), self.h)
+
+    def get_moments(self):
+        return self._get("ipm_get_moments", self.shape)
+
+    def set_moments(self, a):
+        self._set("ipm_set_moments", a)
+
+    def get_duals(self):
+        return self._get("ipm_get_duals", self.shape)
+
+    def set_duals(self, a):
+        self._set("ipm_set_duals", a)
+
+    def get_nodal_states(self):
+        d = self.dims
+        return self._get("ipm_get_nodal_states", (d.n_cells, d.m, d.Q))
+
+    def set_moments_device(self, ptr, count):
+        _check("ipm_set_moments_device", lib().ipm_set_moments_device(self.h, _vp(ptr), count), self.h)
+
+    def get_moments_device(self, ptr, count):
+        _check("ipm_get_moments_device", lib().ipm_get_moments_device(self.h, _vp(ptr), count), self.h)
+
+    def set_stream(self, stream_ptr):
+        _check("ipm_set_stream", lib().ipm_set_stream(self.h, _vp(stream_ptr) if stream_ptr else None), self.h)
+
+    def _stats_call(self, fn, *args, sync=True):
+        s = ipm_stats()
+        _check(fn, getattr(lib(), fn)(self.h, *args, ctypes.byref(s) if sync else None), self.h)
+        return s if sync else None
+
+    def dual_solve(self, sync=True):
+        return self._stats_call("ipm_dual_solve", sync=sync)
+
+    def update(self, dt):
+        _check("ipm_update", lib().ipm_update(self.h, dt), self.h)
+
+    def step(self, sync=True):
+        return self._stats_call("ipm_step", sync=sync)
+
+    def oneshot_step(self, sync=True):
+        return self._stats_call("ipm_oneshot_step", sync=sync)
+
+    def run(self, max_steps=2 ** 62):
+        return self._stats_call("ipm_run", ctypes.c_int64(max_steps))
+
+    def sync_stats(self):
+        return self._stats_call("ipm_sync_stats")
+
+    def step_timing(self):
+        """(newton_ms, update_ms, total_ms) of the last step, from events inside its graph."""
+        a, b, t = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        _check("ipm_step_timing", lib().ipm_step_timing(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t)), self.h)
+        return a.value, b.value, t.value

@@ -1,0 +1,58 @@
+"""Test helpers: set up the same workload on the CPU oracle and on the CUDA library.
+
+The oracle side is built from the workload numbers alone; the library side through the C ABI.
+No value flows from the CUDA path into the oracle."""
+import numpy as np
+
+from oracle import basis, dual, entropy, physics
+from oracle import scheme1d as s1
+
+
+def _affine(vals, dvals, nvar):
+    vals = np.asarray(vals, dtype=np.float64)
+    d = np.zeros((nvar, 3))
+    if dvals is not None:
+        for v in range(min(nvar, len(dvals))):
+            d[v, :len(dvals[v])] = dvals[v]
+    return lambda xi: vals[None, :nvar] + xi @ d[:nvar, :xi.shape[1]].T
+
+
+def oracle_problem(w, tau=None):
+    """oracle.scheme1d.Problem1D for a workload dictionary (see paper_1912_09238_gb300.workloads)."""
+    sp = basis.StochasticSpace(w["p"], w["M"], w["nq"])
+    if w["kind"] == "burgers1d":
+        phys = physics.Burgers1D()
+        ent = entropy.BoundedBarrier(w["u_minus"], w["u_plus"]) if w["entropy"] == "barrier" else entropy.Quadratic(1)
+        L = _affine(w["left"], w.get("dleft"), 1)
+        R = _affine(w["right"], w.get("dright"), 1)
+        left, right = L, R
+    else:
+        phys = physics.Euler(w["gamma"], 1)
+        ent = entropy.Euler(w["gamma"], 1) if w["entropy"] == "euler" else entropy.Quadratic(3)
+        E = entropy.Euler(w["gamma"], 1)
+        L = _affine(w["left"], w.get("dleft"), 3)
+        R = _affine(w["right"], w.get("dright"), 3)
+        left = lambda xi: E.conserved(L(xi)[:, 0], L(xi)[:, 1:2], L(xi)[:, 2])
+        right = lambda xi: E.conserved(R(xi)[:, 0], R(xi)[:, 1:2], R(xi)[:, 2])
+    dx0 = np.asarray(w["dx0"], dtype=np.float64)
+    x0 = lambda xi: w["x0"] + xi @ dx0[:xi.shape[1]]
+    prob = s1.Problem1D(phys=phys, ent=ent, space=sp, nx=w["nx"], x_lo=w["x_lo"], x_hi=w["x_hi"],
+                        ic=s1.RiemannIC(left, right, x0), bc="/".join(w["bc"]), cfl=w["cfl"], t_end=w["t_end"])
+    prob.newton = dual.NewtonOptions(tau=tau if tau is not None else w.get("newton_tol", 1e-10))
+    return prob
+
+
+def gpu_context(w, precision="fp64", tau=None, **opt):
+    from paper_1912_09238_gb300 import ipm
+    pr = ipm.make_problem(w["kind"], w["nx"], w["x_lo"], w["x_hi"], bc=w["bc"], cfl=w["cfl"], t_end=w["t_end"],
+                          gamma=w["gamma"], x0=w["x0"], dx0=w["dx0"], left=w["left"], dleft=w.get("dleft"),
+                          right=w["right"], dright=w.get("dright"))
+    o = ipm.default_options(precision, newton_tol=tau if tau is not None else w.get("newton_tol", 1e-10), **opt)
+    return ipm.Context(pr, w["p"], w["M"], w["nq"], w["entropy"], w.get("u_minus", 0.0), w.get("u_plus", 0.0), o)
+
+
+def rel_err(a, b):
+    """Normwise relative difference max|a - b| / max|b| (b is the oracle)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))

@@ -1,0 +1,67 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it builds, loads, exports every entry point
+declared in include/ipm.h, and its host-built tables agree with the oracle's independent ones."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libipm():
+    from paper_1912_09238_gb300 import build, ipm
+    build.build()
+    return ipm.lib()
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(ipm_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(libipm):
+    from paper_1912_09238_gb300 import ipm
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(libipm, n), n
+    bound = {s[0] for s in ipm.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+@pytest.mark.parametrize("p,M,nq", [(1, 5, 10), (3, 5, 6), (2, 4, 5), (3, 2, 3), (1, 0, 1)])
+def test_library_tables_match_oracle(libipm, p, M, nq):
+    from oracle.basis import StochasticSpace
+    from paper_1912_09238_gb300 import ipm
+    idx, nodes, w, phi = ipm.ipm_tables(p, M, nq)
+    sp = StochasticSpace(p, M, nq)
+    assert np.array_equal(idx, sp.indices)
+    np.testing.assert_allclose(nodes, sp.nodes, rtol=0, atol=4e-16)
+    np.testing.assert_allclose(w, sp.w, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(phi, sp.Phi, rtol=0, atol=5e-14)
+
+
+def test_tables_reject_bad_sizes(libipm):
+    import ctypes
+    n = ctypes.c_int()
+    q = ctypes.c_int()
+    assert libipm.ipm_tables(0, 3, 3, 10, 10, None, None, None, None, ctypes.byref(n), ctypes.byref(q)) == 1
+    assert libipm.ipm_tables(4, 3, 3, 10, 10, None, None, None, None, ctypes.byref(n), ctypes.byref(q)) == 1
+
+
+def test_init_without_a_gpu_fails_cleanly(libipm):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1912_09238_gb300 import ipm, workloads
+    from tests._cases import gpu_context
+    with pytest.raises(ipm.IpmError) as e:
+        gpu_context(workloads.BURGERS_1D)
+    assert e.value.status in (9, 1)
