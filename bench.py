@@ -133,10 +133,12 @@ def run_gpu(args):
     w = workload()
     precision = args.precision
     ctx = gpu_context(w, precision=precision)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()                    # a real (non-default) stream shared by torch and libipm
+    torch.cuda.set_stream(stream)
     ctx.set_stream(stream.cuda_stream)
     d = ctx.dims
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    assert torch.cuda.current_stream().cuda_stream == stream.cuda_stream != 0
 
     def barrier():
         torch.cuda.synchronize()

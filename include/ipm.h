@@ -168,7 +168,9 @@ const char* ipm_last_error(const ipm_ctx* ctx);
 
 ipm_status ipm_get_dims(const ipm_ctx* ctx, ipm_dims* out);
 
-/* Order all later work of ctx on the given cudaStream_t (NULL restores the context's own stream). */
+/* Order all later work of ctx on the given cudaStream_t, used verbatim: NULL is the CUDA legacy
+ * default stream (the stream PyTorch reports as 0). Until the first call the context uses a
+ * non-blocking stream of its own. Waits for the work already queued on the previous stream. */
 ipm_status ipm_set_stream(ipm_ctx* ctx, void* cuda_stream);
 
 /* Copy moments / duals in or out; count must equal n_cells*N*m doubles. Synchronous. */

@@ -146,16 +146,16 @@ static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
 
 // one step of Algorithm 1 (one_step = 0) or Algorithm 2 (one_step = 1)
 static cudaError_t enqueue_step(ipm_ctx* c, int one_step, cudaStream_t s) {
-  cudaError_t e = cudaEventRecord(c->ev[0], s);
+  cudaError_t e = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal);
   if (e == cudaSuccess) e = enqueue_newton(c, one_step, s);
-  if (e == cudaSuccess) e = cudaEventRecord(c->ev[1], s);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal);
   if (e != cudaSuccess) return e;
   Update1DArgs u = update_args(c, 0.0, true);
   e = launch_update1d(c->phys, c->m, u, c->update_grid, s);
-  if (e == cudaSuccess) e = cudaEventRecord(c->ev[2], s);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal);
   if (e == cudaSuccess)
     e = launch_finalize(c->d_sc, c->d_iters, c->d_status, c->d_cell_resid, c->n_cells, 1, c->n_interior, 1, s);
-  if (e == cudaSuccess) e = cudaEventRecord(c->ev[3], s);
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal);
   return e;
 }
 
@@ -414,7 +414,7 @@ ipm_status ipm_get_dims(const ipm_ctx* c, ipm_dims* d) {
 ipm_status ipm_set_stream(ipm_ctx* c, void* s) {
   if (!c) return IPM_EINVAL;
   IPM_CK(c, cudaStreamSynchronize(c->stream));
-  c->stream = s ? static_cast<cudaStream_t>(s) : c->own_stream;
+  c->stream = static_cast<cudaStream_t>(s);
   return IPM_OK;
 }
 

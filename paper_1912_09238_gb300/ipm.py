@@ -231,6 +231,7 @@ class Context:
         _check("ipm_get_moments_device", lib().ipm_get_moments_device(self.h, _vp(ptr), count), self.h)
 
     def set_stream(self, stream_ptr):
+        """Order this context's work on a cudaStream_t given as an integer handle (0 = legacy default)."""
         _check("ipm_set_stream", lib().ipm_set_stream(self.h, _vp(stream_ptr) if stream_ptr else None), self.h)
 
     def _stats_call(self, fn, *args, sync=True):
