@@ -218,6 +218,35 @@ ipm_status ipm_step_timing(ipm_ctx* ctx, float* newton_ms, float* update_ms, flo
 /* Wait for the context's stream and fill *stats with the counters of the last step or solve. */
 ipm_status ipm_sync_stats(ipm_ctx* ctx, ipm_stats* stats);
 
+/* Scratch limits of ipm_dual_solve_noalloc: one static device array of this many bytes per GPU
+ * that loads the library, and at most this many cells per call. */
+#define IPM_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define IPM_NOALLOC_MAX_CELLS 262144
+
+/* Dual solve that allocates nothing (the paper has no counterpart: this is a library-usage
+ * variant of ipm_dual_solve). For callers that cannot allocate device memory themselves -- their
+ * device memory is owned by another allocator (a framework's caching pool or a fixed budget handed
+ * to a plugin), or they run timing-critical loops that must not pay cudaMalloc's implicit
+ * synchronisation. Solves the dual problem (Newton until tau) in every one of n_cells cells of
+ * caller-owned device buffers, on the given stream (NULL = legacy default stream):
+ *   d_uhat   [n_cells][N][m] moments (in);  d_lam [n_cells][N][m] duals (in: warm start, out: result);
+ *   d_nodal  [n_cells][m][Q] nodal states u_s at the result (out);
+ *   d_iters, d_status [n_cells] Newton updates and ipm_status per cell (out).
+ * All scratch (tables, counters, cell list, Hessian workspace) comes from one file-scope device
+ * array of IPM_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until exit; no
+ * cudaMalloc, cudaFree or allocating library routine is called. Sizes beyond the scratch (or more
+ * than IPM_NOALLOC_MAX_CELLS cells) return IPM_EINVAL with a message in ipm_last_error(NULL).
+ * Calls share the array and it keeps the last call's contents (counters are cleared at the start
+ * of each call); calls that overlap on the GPU race and must not be issued concurrently. The first
+ * call on a device looks up the array's address (cudaGetSymbolAddress); make that first call before
+ * any stream capture. The call waits for the table upload on the stream; with stats != NULL it
+ * also waits for the solve and fills the counters. FP64 precision, 1-D problem kinds only. */
+ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, const ipm_basis* basis,
+                                  const ipm_quadrature* quad, const ipm_entropy* entropy,
+                                  const ipm_options* options, int n_cells, const double* d_uhat,
+                                  double* d_lam, double* d_nodal, int* d_iters, int* d_status,
+                                  void* stream, ipm_stats* stats);
+
 /* Host-only: the basis and quadrature tables the library uses (no GPU needed).
  * indices: N*p ints (graded order), nodes: Q*p doubles, weights: Q doubles (density folded in,
  * summing to 1), phi: Q*N doubles with phi[k*N + i] = phi_i(xi_k). Any output may be NULL.

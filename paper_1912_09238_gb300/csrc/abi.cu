@@ -52,6 +52,14 @@ struct ipm_ctx {
 static std::mutex g_err_mu;
 static std::string g_init_err;
 
+namespace ipm {
+// message for ipm_last_error(NULL) from calls that have no context
+void set_global_error(const std::string& msg) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_init_err = msg;
+}
+}  // namespace ipm
+
 static ipm_status fail(ipm_ctx* c, ipm_status s, const std::string& msg) {
   if (c) {
     c->err = msg;

@@ -21,6 +21,7 @@ struct HostTables {
   std::vector<uint32_t> pairs;  // [N(N+1)/2]
 };
 
+void set_global_error(const std::string& msg);
 void gauss_legendre_1d(int n, std::vector<double>& x, std::vector<double>& w);
 void build_tables(int p, int M, int nq, HostTables& t);
 

@@ -95,6 +95,9 @@ SIGNATURES = [
     ("ipm_oneshot_step", ctypes.c_int, [_vp, _P(ipm_stats)]),
     ("ipm_sync_stats", ctypes.c_int, [_vp, _P(ipm_stats)]),
     ("ipm_step_timing", ctypes.c_int, [_vp, _P(ctypes.c_float), _P(ctypes.c_float), _P(ctypes.c_float)]),
+    ("ipm_dual_solve_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_double, _P(ipm_basis), _P(ipm_quadrature),
+                                              _P(ipm_entropy), _P(ipm_options), ctypes.c_int, _vp, _vp, _vp,
+                                              _vp, _vp, _vp, _P(ipm_stats)]),
     ("ipm_tables", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   _P(ctypes.c_int), _dp, _dp, _dp, _P(ctypes.c_int), _P(ctypes.c_int)]),
 ]
@@ -148,6 +151,22 @@ def ipm_tables(p, total_degree, n_per_dim):
     _check("ipm_tables", lib().ipm_tables(p, total_degree, n_per_dim, n, q, idx.ctypes.data_as(_P(ctypes.c_int)),
                                           _dptr(nodes), _dptr(w), _dptr(phi), ctypes.byref(N), ctypes.byref(Q)))
     return idx, nodes, w, phi
+
+
+def ipm_dual_solve_noalloc(kind, gamma, p, total_degree, n_per_dim, entropy, n_cells, d_uhat, d_lam, d_nodal,
+                           d_iters, d_status, stream=0, u_minus=0.0, u_plus=0.0, options=None):
+    """Dual solve on caller-owned device buffers (integer device addresses); allocates nothing.
+    Returns the ipm_stats of the call (the call waits for the solve)."""
+    b = ipm_basis(p, total_degree)
+    q = ipm_quadrature(n_per_dim)
+    e = ipm_entropy(ENTROPY[entropy], u_minus, u_plus)
+    o = options if options is not None else default_options()
+    s = ipm_stats()
+    _check("ipm_dual_solve_noalloc",
+           lib().ipm_dual_solve_noalloc(PROBLEM[kind], gamma, ctypes.byref(b), ctypes.byref(q), ctypes.byref(e),
+                                        ctypes.byref(o), n_cells, _vp(d_uhat), _vp(d_lam), _vp(d_nodal), _vp(d_iters),
+                                        _vp(d_status), _vp(stream) if stream else None, ctypes.byref(s)))
+    return s
 
 
 def make_problem(kind, nx, x_lo, x_hi, bc=("outflow", "outflow"), cfl=0.5, t_end=0.0, gamma=1.4,
