@@ -144,6 +144,8 @@ typedef struct {
   double t;                 /* time after the call */
   double residual;          /* steady residual of the last step (Eq. residualSteady, first variable) */
   int64_t steps;            /* steps taken since ipm_init */
+  int32_t tc_timeouts;      /* mixed path: bounded tensor-core / bulk-copy waits that ran out (0 normally;
+                               the affected cells report IPM_ETIMEOUT) */
 } ipm_stats;
 
 typedef struct ipm_ctx ipm_ctx;
@@ -191,6 +193,15 @@ ipm_status ipm_get_moments_device(ipm_ctx* ctx, double* dev, size_t count);
  * warm-started at the current duals; the nodal states of the result are kept for the next
  * update. Synchronous when stats != NULL. */
 ipm_status ipm_dual_solve(ipm_ctx* ctx, ipm_stats* stats);
+
+/* The Hessian H((i,a),(j,b)) = sum_k w_k [grad u_s]_ab(Lambda_k) phi_i(xi_k) phi_j(xi_k) of the dual
+ * cost (Sec. 3.1, the Jacobian of the Newton map of Eq. dualIterationFunction) at the current duals of
+ * every interior cell, assembled exactly as the Newton kernel assembles it in the context's
+ * precision (IPM_PREC_MIXED: split-BF16 tensor-core products with FP32 accumulation, widened to
+ * float64). Output: packed lower triangles, host array [interior cell][r(r+1)/2 + c] for r >= c with
+ * flat index r = i*m + a; count = n_interior * N*m*(N*m+1)/2. Does not change the state (the nodal
+ * states are refreshed at the current duals). Allocates a temporary device buffer; synchronous. */
+ipm_status ipm_assemble_hessian(ipm_ctx* ctx, double* host, size_t count);
 
 /* Only the moment update c of every interior cell from the current duals (Eq. momentUpQuadrature)
  * with the given dt > 0 (dt is not computed and t is not advanced); then the boundary condition.

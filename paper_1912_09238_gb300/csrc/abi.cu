@@ -36,6 +36,11 @@ struct ipm_ctx {
   StepScalars* d_sc = nullptr;
   int n_fixed_ghosts = 0;
   // launch configuration
+  bool mixed = false;          // precision IPM_PREC_MIXED: tensor-core Hessian
+  MixedLayout mx;
+  NewtonSmem sm;
+  float* d_phiT32 = nullptr;
+  uint8_t* d_phi_img = nullptr;
   size_t newton_smem = 0;
   bool h_in_smem = true;
   int newton_grid = 0;
@@ -122,6 +127,18 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.max_newton = c->opt.max_newton;
   a.max_halvings = c->opt.max_halvings;
   a.track_speed = 1;
+  a.h_dump = nullptr;
+  a.mx.phi_img = c->d_phi_img;
+  a.mx.phiT32 = c->d_phiT32;
+  a.mx.n_pad = c->mx.n_pad;
+  a.mx.kc = c->mx.kc;
+  a.mx.chunks = c->mx.chunks;
+  a.mx.tiles = c->mx.tiles;
+  a.mx.tpp = c->mx.tpp;
+  a.mx.tmem_cols = c->mx.tmem_cols;
+  a.off_h = c->sm.off_h;
+  a.off_a = c->sm.off_a;
+  a.off_b = c->sm.off_b;
   return a;
 }
 
@@ -149,7 +166,7 @@ static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   NewtonArgs a = newton_args(c, one_step);
-  return launch_newton_phys(c->entk, c->phys, c->m, a, c->newton_grid, c->newton_smem, c->h_in_smem, s);
+  return launch_newton_phys(c->entk, c->phys, c->m, a, c->newton_grid, c->newton_smem, c->h_in_smem, c->mixed, s);
 }
 
 // one step of Algorithm 1 (one_step = 0) or Algorithm 2 (one_step = 1)
@@ -190,7 +207,8 @@ static void free_ctx(ipm_ctx* c) {
     if (ev) cudaEventDestroy(ev);
   if (c->oneshot_exec) cudaGraphExecDestroy(c->oneshot_exec);
   void* ptrs[] = {c->d_Phi, c->d_PhiT, c->d_w, c->d_nodes, c->d_pairs, c->d_uhat, c->d_lam, c->d_unode,
-                  c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc};
+                  c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc,
+                  c->d_phiT32, c->d_phi_img};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -253,8 +271,8 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
     return fail(nullptr, IPM_EINVAL, "ipm_init: bad mesh or cfl");
   if ((problem->bc_left == IPM_BC_PERIODIC) != (problem->bc_right == IPM_BC_PERIODIC))
     return fail(nullptr, IPM_EINVAL, "ipm_init: periodic must be set on both ends");
-  if (opt.precision != IPM_PREC_FP64)
-    return fail(nullptr, IPM_EINVAL, "ipm_init: this build provides the FP64 path only");
+  if (opt.precision != IPM_PREC_FP64 && opt.precision != IPM_PREC_MIXED)
+    return fail(nullptr, IPM_EINVAL, "ipm_init: unknown precision");
 
   ipm_ctx* c = new ipm_ctx();
   c->prob = *problem;
@@ -294,25 +312,48 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
     return fail(nullptr, IPM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   }
   cudaDeviceProp prop;
-  cudaGetDeviceProperties(&prop, c->device);
-  // launch configuration of the Newton kernel: packed H in shared memory when it fits
-  const size_t smem_full = newton_smem_bytes(c->N, c->m, c->Q, true);
-  const size_t smem_lean = newton_smem_bytes(c->N, c->m, c->Q, false);
-  if (smem_lean > (size_t)prop.sharedMemPerBlockOptin) {
+  e = cudaGetDeviceProperties(&prop, c->device);
+  if (e != cudaSuccess) {
     delete c;
-    return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for one CTA");
+    return fail(nullptr, IPM_ECUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
   }
-  c->h_in_smem = smem_full <= (size_t)prop.sharedMemPerBlockOptin;
-  c->newton_smem = c->h_in_smem ? smem_full : smem_lean;
+  // launch configuration of the Newton kernel: packed H in shared memory when it fits
+  const size_t budget = (size_t)prop.sharedMemPerBlockOptin;
+  c->mixed = opt.precision == IPM_PREC_MIXED;
+  if (c->mixed) {
+    c->h_in_smem = true;
+    c->mx = mixed_layout(c->N, c->m, c->Q, budget, true);
+    if (!c->mx.ok) {
+      c->h_in_smem = false;
+      c->mx = mixed_layout(c->N, c->m, c->Q, budget, false);
+    }
+    if (!c->mx.ok) {
+      delete c;
+      return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for the mixed-precision Newton kernel");
+    }
+    c->sm = newton_smem(c->N, c->m, c->Q, c->h_in_smem, &c->mx);
+  } else {
+    const NewtonSmem full = newton_smem(c->N, c->m, c->Q, true, nullptr);
+    const NewtonSmem lean = newton_smem(c->N, c->m, c->Q, false, nullptr);
+    if (lean.bytes > budget) {
+      delete c;
+      return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for one CTA");
+    }
+    c->h_in_smem = full.bytes <= budget;
+    c->sm = c->h_in_smem ? full : lean;
+  }
+  c->newton_smem = c->sm.bytes;
   {
-    // persistent grid: resident CTAs per SM (occupancy API) times the SM count
+    // persistent grid: resident CTAs per SM (occupancy API) times the SM count; on the mixed path
+    // the CTAs of one SM must also share its 512 tensor-memory columns
     int bps = 0;
-    e = prepare_newton(c->entk, c->phys, c->m, c->newton_smem, c->h_in_smem, &bps);
+    e = prepare_newton(c->entk, c->phys, c->m, c->newton_smem, c->h_in_smem, c->mixed, &bps);
     if (e == cudaSuccess) e = prepare_update1d(c->phys, c->m, c->Q);
     if (e != cudaSuccess || bps < 1) {
       delete c;
       return fail(nullptr, IPM_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
     }
+    if (c->mixed) bps = std::min(bps, 512 / c->mx.tmem_cols);
     c->newton_grid = std::max(1, std::min(c->n_interior, bps * prop.multiProcessorCount));
   }
   c->hwork_stride = c->h_in_smem ? 0 : (size_t)c->NM * (c->NM + 1) / 2;
@@ -333,6 +374,12 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   CK(upload(&c->d_w, c->tab.w), "upload w");
   CK(upload(&c->d_nodes, c->tab.nodes), "upload nodes");
   CK(upload(&c->d_pairs, c->tab.pairs), "upload pairs");
+  if (c->mixed) {
+    CK(cudaMalloc(&c->d_phiT32, (size_t)c->N * c->Q * sizeof(float)), "cudaMalloc phiT32");
+    CK(cudaMalloc(&c->d_phi_img, (size_t)c->mx.chunks * c->mx.b_chunk_bytes), "cudaMalloc phi image");
+    if (st == IPM_OK)
+      CK(launch_phi_images(c->d_PhiT, c->N, c->Q, c->mx, c->d_phiT32, c->d_phi_img, c->stream), "phi images");
+  }
   const size_t nstate = (size_t)c->n_cells * c->NM;
   CK(cudaMalloc(&c->d_uhat, nstate * sizeof(double)), "cudaMalloc uhat");
   CK(cudaMalloc(&c->d_lam, nstate * sizeof(double)), "cudaMalloc lam");
@@ -368,7 +415,7 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
       a.cell_list = c->d_ghost_list;
       a.n_work = (int)ghosts.size();
       CK(launch_newton_phys(c->entk, c->phys, c->m, a, std::min(c->newton_grid, (int)ghosts.size()), c->newton_smem,
-                            c->h_in_smem, c->stream),
+                            c->h_in_smem, c->mixed, c->stream),
          "ghost solve");
     }
   }
@@ -474,6 +521,7 @@ static void fill_stats(const StepScalars& h, ipm_stats* s) {
   s->t = h.t;
   s->residual = h.residual;
   s->steps = h.steps;
+  s->tc_timeouts = h.tc_timeouts;
 }
 
 ipm_status ipm_sync_stats(ipm_ctx* c, ipm_stats* s) {
@@ -490,6 +538,26 @@ ipm_status ipm_dual_solve(ipm_ctx* c, ipm_stats* s) {
   IPM_CK(c, enqueue_newton(c, 0, c->stream));
   IPM_CK(c, launch_finalize(c->d_sc, c->d_iters, c->d_status, nullptr, c->n_cells, 1, c->n_interior, 0, c->stream));
   if (s) return ipm_sync_stats(c, s);
+  return IPM_OK;
+}
+
+ipm_status ipm_assemble_hessian(ipm_ctx* c, double* h, size_t count) {
+  if (!c || (!h && count)) return IPM_EINVAL;
+  const size_t nph = (size_t)c->NM * (c->NM + 1) / 2;
+  if (count != (size_t)c->n_interior * nph) return fail(c, IPM_EINVAL, "ipm_assemble_hessian: count must be n_interior*NM(NM+1)/2");
+  double* d = nullptr;
+  IPM_CK(c, cudaMalloc(&d, count * sizeof(double)));
+  NewtonArgs a = newton_args(c, 0);
+  a.h_dump = d;
+  a.track_speed = 0;
+  cudaError_t e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess)
+    e = launch_newton_phys(c->entk, c->phys, c->m, a, c->newton_grid, c->newton_smem, c->h_in_smem, c->mixed, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(d);
+  IPM_CK(c, e);
   return IPM_OK;
 }
 

@@ -24,7 +24,9 @@ enum EntKind { ENT_QUADRATIC = 0, ENT_BARRIER = 1, ENT_EULER = 2 };
 enum PhysKind { PHYS_BURGERS = 0, PHYS_EULER1D = 1, PHYS_EULER2D = 2 };
 
 // per-cell status codes (values of ipm_status)
-enum CellStatus { ST_OK = 0, ST_NOCONV = 3, ST_NOTSPD = 4, ST_INFEASIBLE = 5, ST_LINESEARCH = 6, ST_NONFINITE = 7 };
+enum CellStatus {
+  ST_OK = 0, ST_NOCONV = 3, ST_NOTSPD = 4, ST_INFEASIBLE = 5, ST_LINESEARCH = 6, ST_NONFINITE = 7, ST_TIMEOUT = 10
+};
 
 struct EntParams {
   double u_minus, u_plus, gamma;
@@ -234,6 +236,20 @@ struct StepScalars {
   int failed_cells;
   int first_failed_cell;
   int first_status;
+  int tc_timeouts;               // bounded tensor-core / bulk-copy waits that ran out (mixed path)
+};
+
+// Mixed-precision Hessian (tensor cores): tiling of H_ab = Phi^T diag(w J_ab) Phi as MMAs with
+// rows (ab, i) of the per-cell operand, columns j, and the quadrature nodes as the K dimension.
+struct MixedTiles {
+  const uint8_t* phi_img;  // [chunk][hi, lo][n_pad x kc] BF16 K-major images of Phi (B operand)
+  const float* phiT32;     // [N][Q] Phi^T in FP32 (builds the A operand)
+  int n_pad;               // N rounded up to a multiple of 16 (MMA N)
+  int kc;                  // nodes per K-chunk (multiple of 16)
+  int chunks;              // ceil(Q / kc)
+  int tiles;               // ceil(B N / 128) row tiles of 128 (MMA M)
+  int tpp;                 // row tiles per pass (accumulators resident in tensor memory at once)
+  int tmem_cols;           // allocated tensor-memory columns (power of two >= 32)
 };
 
 struct NewtonArgs {
@@ -254,6 +270,10 @@ struct NewtonArgs {
   double tau, armijo_c, slack_rel;
   int max_newton, max_halvings;
   int track_speed;       // 1: fold the nodal signal speeds of the result into sc->smax_bits
+  double* h_dump;        // non-null: assemble the Hessian at the current duals, store it packed
+                         // [work item][NM(NM+1)/2] and stop (no Newton update)
+  MixedTiles mx;         // mixed path only
+  uint32_t off_h, off_a, off_b;  // shared-memory byte offsets: packed H, A staging, Phi chunks
 };
 
 struct Update1DArgs {

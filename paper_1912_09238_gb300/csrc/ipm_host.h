@@ -25,12 +25,29 @@ void set_global_error(const std::string& msg);
 void gauss_legendre_1d(int n, std::vector<double>& x, std::vector<double>& w);
 void build_tables(int p, int M, int nq, HostTables& t);
 
+// Tiling of the mixed-precision Hessian (see MixedTiles) and its shared-memory needs.
+struct MixedLayout {
+  bool ok = false;          // the problem fits the tensor-core path
+  int n_pad = 0, kc = 0, chunks = 0, tiles = 0, tpp = 0, tmem_cols = 0;
+  size_t a_bytes = 0;       // A staging of one pass and one K-chunk (both BF16 terms)
+  size_t b_chunk_bytes = 0; // one K-chunk of the Phi image (both BF16 terms)
+};
+// Dynamic shared memory of the Newton kernel: byte offsets of the packed H, the A staging and
+// the two Phi-chunk buffers, and the total.
+struct NewtonSmem {
+  uint32_t off_h = 0, off_a = 0, off_b = 0;
+  size_t bytes = 0;
+};
+
 // kernel launchers (newton.cu, update.cu)
-size_t newton_smem_bytes(int N, int m, int Q, bool h_in_smem);
+NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* mx);
+MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem);
 int newton_threads();
 cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, int grid, size_t smem, bool h_in_smem,
-                               cudaStream_t s);
-cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, int* blocks_per_sm);
+                               bool mixed, cudaStream_t s);
+cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, bool mixed, int* blocks_per_sm);
+cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayout& L, float* phiT32, uint8_t* img,
+                              cudaStream_t s);
 cudaError_t prepare_update1d(int phys, int m, int Q);
 cudaError_t launch_update1d(int phys, int m, const Update1DArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_init1d(int ent, int m, const Tables& tab, const EntParams& ent_p, const ipm_problem& prob,

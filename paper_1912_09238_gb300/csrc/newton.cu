@@ -1,4 +1,4 @@
-// newton.cu -- per-cell Newton solve of the IPM dual problem, FP64 path.
+// newton.cu -- per-cell Newton solve of the IPM dual problem (FP64 and mixed precision).
 //
 // One CTA owns one cell at a time and pulls cells from a persistent work queue (an atomic
 // counter bounded by the number of cells), so cells with uneven Newton counts balance out.
@@ -12,11 +12,25 @@
 // The packed Hessian lives in shared memory when it fits, else in a per-CTA slot of a global
 // workspace (L2-resident).
 //
+// Precision. FP64 path: every step in float64 on the CUDA cores. Mixed path: only (b) changes.
+// For each packed pair ab (a <= b) the block H_ab = Phi^T diag(w J_ab) Phi is one tensor-core
+// contraction over the nodes: the per-cell operand A[(ab, i)][k] = w_k J_k,ab phi_i(xi_k) and the
+// constant operand B[j][k] = phi_j(xi_k) are each split into two BF16 terms (x = x_hi + x_lo,
+// |x - x_hi - x_lo| <= 2^-16 |x|), and A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in FP32 in
+// tensor memory by tcgen05.mma. The result is widened to float64 for the Cholesky factorisation.
+// The gradient, the stopping test, the factorisation, the solves and the line search stay in
+// float64, so the converged duals satisfy the same FP64 criterion (Eq. tauCrit) as the FP64 path.
+//
 // Every loop is bounded: the queue by the cell count, Newton by max_newton, the line search by
-// max_halvings, the factorisation and solves by N*m.
+// max_halvings, the factorisation and solves by N*m, and every tensor-core / bulk-copy wait by a
+// 2 s global-timer limit (a timeout marks the cell IPM_ETIMEOUT, counts in StepScalars::tc_timeouts
+// and ends the CTA after draining its pending copies).
 #include <type_traits>
 
+#include <cuda_bf16.h>
+
 #include "ipm_host.h"
+#include "tc.cuh"
 
 namespace ipm {
 
@@ -60,11 +74,215 @@ __device__ __forceinline__ double node_speed<PHYS_EULER2D, 4>(const double* u, d
   return fmax(fabs(v1), fabs(v2)) + sqrt(g * p / u[0]);
 }
 
-template <int ENT, int PHYS, int M, bool H_SMEM>
+// (a, b) of the packed index ab (a <= b)
+template <int M>
+__device__ __forceinline__ void unpack_ab(int ab, int& a, int& b) {
+  a = 0;
+  b = 0;
+#pragma unroll
+  for (int x = 0; x < M; ++x)
+#pragma unroll
+    for (int y = x; y < M; ++y)
+      if (packed_ab(x, y, M) == ab) {
+        a = x;
+        b = y;
+      }
+}
+
+// Store the value H_ab[i][j] (a <= b) of the block form into the packed lower triangle of H
+// (row index i*M + a). Each lower entry is written by exactly one (ab, i, j).
+template <int M>
+__device__ __forceinline__ void store_block_entry(double* s_H, int a, int b, int i, int j, double v) {
+  if (a == b) {
+    if (i >= j) {
+      const size_t r = (size_t)i * M + a, c = (size_t)j * M + a;
+      s_H[r * (r + 1) / 2 + c] = v;
+    }
+  } else {
+    if (i > j) {
+      const size_t r = (size_t)i * M + a, c = (size_t)j * M + b;
+      s_H[r * (r + 1) / 2 + c] = v;
+    }
+    if (i >= j) {
+      const size_t r = (size_t)i * M + b, c = (size_t)j * M + a;
+      s_H[r * (r + 1) / 2 + c] = v;
+    }
+  }
+}
+
+// (b), FP64 on the CUDA cores: one thread per moment pair (i >= j), all B blocks at once.
+template <int M>
+__device__ __forceinline__ void hessian_fp64(const NewtonArgs& a, const double* s_wJ, double* s_H) {
+  constexpr int B = packed_count(M);
+  const int N = a.tab.N, Q = a.tab.Q, NP = N * (N + 1) / 2;
+  const double* __restrict__ Phi = a.tab.Phi;
+  for (int pidx = threadIdx.x; pidx < NP; pidx += NT) {
+    const uint32_t pr = a.tab.pairs[pidx];
+    const int i = (int)(pr >> 16), j = (int)(pr & 0xffffu);
+    double acc[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) acc[b] = 0.0;
+    for (int q = 0; q < Q; ++q) {
+      const double pq = Phi[(size_t)q * N + i] * Phi[(size_t)q * N + j];
+#pragma unroll
+      for (int b = 0; b < B; ++b) acc[b] = fma(s_wJ[b * Q + q], pq, acc[b]);
+    }
+#pragma unroll
+    for (int a1 = 0; a1 < M; ++a1)
+#pragma unroll
+      for (int b1 = 0; b1 < M; ++b1) {
+        const int r = i * M + a1, c = j * M + b1;
+        if (r < c) continue;
+        const int lo = a1 < b1 ? a1 : b1, hi = a1 < b1 ? b1 : a1;
+        s_H[(size_t)r * (r + 1) / 2 + c] = acc[packed_ab(lo, hi, M)];
+      }
+  }
+}
+
+// Tensor-core pipeline state of one CTA (uniform across its threads).
+struct TcState {
+  uint64_t* bars;     // [0] MMA completion, [1], [2] Phi chunk buffers
+  uint32_t tmem;      // tensor-memory base address
+  uint32_t ph[3];     // parity of the next phase to wait for, per barrier
+  bool pend[3];       // a phase is outstanding on the barrier
+};
+
+__device__ __forceinline__ bool tc_wait(TcState& t, int k) {
+  const bool ok = tc::mbar_wait(&t.bars[k], t.ph[k]);
+  if (ok) {
+    t.ph[k] ^= 1u;
+    t.pend[k] = false;
+  }
+  return ok;
+}
+
+// (b), mixed: split-BF16 products on the tensor cores, FP32 accumulate in tensor memory, then
+// widened into the packed FP64 H. s_wJf holds w_k J_k,ab as float [B][Q]. Returns false when a
+// bounded wait ran out (the CTA must stop).
+template <int M>
+__device__ bool hessian_tc(const NewtonArgs& a, const float* s_wJf, double* s_H, uint8_t* sA, uint8_t* sB,
+                           TcState& t, int* s_abort) {
+  constexpr int B = packed_count(M);
+  const MixedTiles& mx = a.mx;
+  const int N = a.tab.N, Q = a.tab.Q, BN = B * N;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t sbo = tc::kmajor_sbo(mx.kc);
+  const uint32_t a_img = (uint32_t)mx.tpp * 128u * (uint32_t)mx.kc * 2u;   // one BF16 term of A
+  const uint32_t b_img = (uint32_t)mx.n_pad * (uint32_t)mx.kc * 2u;         // one BF16 term of B
+  const uint32_t b_chunk = 2u * b_img;
+  const uint32_t idesc = tc::idesc_bf16_f32(128, mx.n_pad);
+  const int groups = mx.kc / 8;
+
+  for (int t0 = 0; t0 < mx.tiles; t0 += mx.tpp) {
+    const int nt = min(mx.tpp, mx.tiles - t0);
+    const int rows = nt * 128;
+    if (tid == 0) {
+      tc::mbar_arrive_expect_tx(&t.bars[1], b_chunk);
+      tc::bulk_g2s(sB, mx.phi_img, b_chunk, &t.bars[1]);
+    }
+    t.pend[1] = true;
+    for (int c = 0; c < mx.chunks; ++c) {
+      const int buf = c & 1;
+      if (c + 1 < mx.chunks) {
+        // the other buffer was last read by the MMAs of chunk c-1, which have completed
+        if (tid == 0) {
+          tc::mbar_arrive_expect_tx(&t.bars[1 + (buf ^ 1)], b_chunk);
+          tc::bulk_g2s(sB + (buf ^ 1) * b_chunk, mx.phi_img + (size_t)(c + 1) * b_chunk, b_chunk,
+                       &t.bars[1 + (buf ^ 1)]);
+        }
+        t.pend[1 + (buf ^ 1)] = true;
+      }
+      // A operand of this chunk: rows (ab, i) of this pass, nodes q0 .. q0 + kc - 1
+      const int q0 = c * mx.kc;
+      for (int item = tid; item < rows * groups; item += NT) {
+        const int rl = item / groups, g = item - rl * groups;
+        const int R = t0 * 128 + rl;
+        uint32_t hw[4] = {0u, 0u, 0u, 0u}, lw[4] = {0u, 0u, 0u, 0u};
+        if (R < BN) {
+          const int ab = R / N, i = R - ab * N;
+          const float* wj = s_wJf + ab * Q;
+          const float* ph = mx.phiT32 + (size_t)i * Q;
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            const int q = q0 + g * 8 + e;
+            const float x0 = q < Q ? wj[q] * ph[q] : 0.f;
+            const float x1 = q + 1 < Q ? wj[q + 1] * ph[q + 1] : 0.f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+            hw[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
+            lw[e / 2] = *reinterpret_cast<const uint32_t*>(&l);
+          }
+        }
+        const uint32_t off = tc::kmajor_offset(rl, g * 8, sbo);
+        *reinterpret_cast<uint4*>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(sA + a_img + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+      tc::fence_proxy_async();
+      __syncthreads();
+      const bool got_b = tc_wait(t, 1 + buf);
+      if (!got_b) *s_abort = 1;
+      if (tid == 0 && got_b) {
+        tc::fence_after_sync();
+        const uint32_t sa = tc::smem_u32(sA), sb = tc::smem_u32(sB + buf * b_chunk);
+        for (int tl = 0; tl < nt; ++tl) {
+          const uint32_t d = t.tmem + (uint32_t)(tl * mx.n_pad);
+          const uint32_t ta = sa + (uint32_t)tl * 16u * sbo;   // 128 rows = 16 row groups
+          for (int ks = 0; ks < mx.kc / 16; ++ks) {
+            const uint32_t kofs = (uint32_t)ks * 256u;
+            const uint64_t ah = tc::smem_desc(ta + kofs, sbo), al = tc::smem_desc(ta + a_img + kofs, sbo);
+            const uint64_t bh = tc::smem_desc(sb + kofs, sbo), bl = tc::smem_desc(sb + b_img + kofs, sbo);
+            tc::mma_bf16(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            tc::mma_bf16(d, ah, bl, idesc, 1u);
+            tc::mma_bf16(d, al, bh, idesc, 1u);
+          }
+        }
+        tc::mma_commit(&t.bars[0]);
+      }
+      if (got_b) t.pend[0] = true;
+      if (!tc_wait(t, 0)) *s_abort = 1;
+      tc::fence_after_sync();
+      __syncthreads();
+      if (*s_abort) return false;
+    }
+    // accumulators -> packed FP64 H. Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 and one
+    // half of the columns.
+    const int lq = warp & 3, half = warp >> 2;
+    const int hcols = mx.n_pad / 2;
+    for (int tl = 0; tl < nt; ++tl) {
+      const int R = (t0 + tl) * 128 + lq * 32 + lane;
+      const bool valid = R < BN;
+      const int ab = valid ? R / N : 0, i = valid ? R - ab * N : 0;
+      int aa, bb;
+      unpack_ab<M>(ab, aa, bb);
+      for (int cg = 0; cg < hcols; cg += 8) {
+        const int col0 = half * hcols + cg;
+        uint32_t r[8];
+        tc::tmem_ld_x8(t.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(tl * mx.n_pad + col0), r);
+        tc::tmem_wait_ld();
+        if (valid) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int j = col0 + e;
+            if (j < N) store_block_entry<M>(s_H, aa, bb, i, j, (double)__uint_as_float(r[e]));
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  return true;
+}
+
+template <int ENT, int PHYS, int M, bool H_SMEM, bool MIXED>
 __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
   constexpr int B = packed_count(M);
-  extern __shared__ __align__(16) double smem[];
+  extern __shared__ __align__(128) double smem[];
   __shared__ int s_work;
+  __shared__ int s_abort;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bars[3];
   const int N = a.tab.N, Q = a.tab.Q, NM = N * M;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* s_lam = smem;
@@ -74,16 +292,36 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
   double* s_Lam = s_d + NM;       // [M][Q]
   double* s_dLam = s_Lam + M * Q; // [M][Q]
   double* s_u = s_dLam + M * Q;   // [M][Q]
-  double* s_wJ = s_u + M * Q;     // [B][Q]
+  double* s_wJ = s_u + M * Q;     // [B][Q]  (float [B][Q] on the mixed path)
   double* s_red = s_wJ + B * Q;   // NWARPS * 8
-  double* s_H = H_SMEM ? (s_red + NWARPS * 8) : (a.hwork + (size_t)blockIdx.x * a.hwork_stride);
+  uint8_t* sbytes = reinterpret_cast<uint8_t*>(smem);
+  double* s_H = H_SMEM ? reinterpret_cast<double*>(sbytes + a.off_h) : (a.hwork + (size_t)blockIdx.x * a.hwork_stride);
+  uint8_t* sA = sbytes + a.off_a;
+  uint8_t* sB = sbytes + a.off_b;
   const double* __restrict__ PhiT = a.tab.PhiT;
-  const double* __restrict__ Phi = a.tab.Phi;
   const double* __restrict__ w = a.tab.w;
-  const uint32_t* __restrict__ pairs = a.tab.pairs;
-  const int NP = N * (N + 1) / 2;
+  const size_t NPH = (size_t)NM * (NM + 1) / 2;
 
-  for (;;) {
+  TcState tcs;
+  tcs.bars = s_bars;
+  tcs.tmem = 0;
+  tcs.ph[0] = tcs.ph[1] = tcs.ph[2] = 0u;
+  tcs.pend[0] = tcs.pend[1] = tcs.pend[2] = false;
+  if (MIXED) {
+    if (tid == 0) {
+      s_abort = 0;
+      for (int k = 0; k < 3; ++k) tc::mbar_init(&s_bars[k], 1);
+      tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&s_tmem, (uint32_t)a.mx.tmem_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tcs.tmem = s_tmem;
+  }
+
+  bool stop = false;
+  while (!stop) {
     if (tid == 0) s_work = atomicAdd(&a.sc->work_counter, 1);
     __syncthreads();
     const int wk = s_work;
@@ -123,8 +361,14 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
         const double wq = w[q];
 #pragma unroll
         for (int c = 0; c < M; ++c) s_u[c * Q + q] = u[c];
+        if (MIXED) {
+          float* s_wJf = reinterpret_cast<float*>(s_wJ);
 #pragma unroll
-        for (int b = 0; b < B; ++b) s_wJ[b * Q + q] = wq * J[b];
+          for (int b = 0; b < B; ++b) s_wJf[b * Q + q] = (float)(wq * J[b]);
+        } else {
+#pragma unroll
+          for (int b = 0; b < B; ++b) s_wJ[b * Q + q] = wq * J[b];
+        }
         red[0] = fma(wq, ss, red[0]);
         red[1] = fma(wq, fabs(ss), red[1]);
         red[2] += ok ? 0.0 : 1.0;
@@ -165,36 +409,32 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
 
       if (red[2] > 0.0) { st = ST_INFEASIBLE; break; }
       if (!isfinite(res)) { st = ST_NONFINITE; break; }
-      if (a.one_step) {
-        if (it >= 1) break;
-      } else {
-        if (res < a.tau) break;
-        if (it >= a.max_newton) { st = ST_NOCONV; break; }
+      if (!a.h_dump) {
+        if (a.one_step) {
+          if (it >= 1) break;
+        } else {
+          if (res < a.tau) break;
+          if (it >= a.max_newton) { st = ST_NOCONV; break; }
+        }
       }
 
       // (b) Hessian, packed lower triangle, row index r = i*M + a
-      for (int pidx = tid; pidx < NP; pidx += NT) {
-        const uint32_t pr = pairs[pidx];
-        const int i = (int)(pr >> 16), j = (int)(pr & 0xffffu);
-        double acc[B];
-#pragma unroll
-        for (int b = 0; b < B; ++b) acc[b] = 0.0;
-        for (int q = 0; q < Q; ++q) {
-          const double pq = Phi[(size_t)q * N + i] * Phi[(size_t)q * N + j];
-#pragma unroll
-          for (int b = 0; b < B; ++b) acc[b] = fma(s_wJ[b * Q + q], pq, acc[b]);
+      if (MIXED) {
+        if (!hessian_tc<M>(a, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, tcs, &s_abort)) {
+          if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
+          st = ST_TIMEOUT;
+          stop = true;
+          break;
         }
-#pragma unroll
-        for (int a1 = 0; a1 < M; ++a1)
-#pragma unroll
-          for (int b1 = 0; b1 < M; ++b1) {
-            const int r = i * M + a1, c = j * M + b1;
-            if (r < c) continue;
-            const int lo = a1 < b1 ? a1 : b1, hi = a1 < b1 ? b1 : a1;
-            s_H[(size_t)r * (r + 1) / 2 + c] = acc[packed_ab(lo, hi, M)];
-          }
+      } else {
+        hessian_fp64<M>(a, s_wJ, s_H);
       }
       __syncthreads();
+      if (a.h_dump) {
+        double* hd = a.h_dump + (size_t)wk * NPH;
+        for (size_t r = tid; r < NPH; r += NT) hd[r] = s_H[r];
+        break;
+      }
 
       // (c) Cholesky in place
       bool spd = true;
@@ -310,24 +550,75 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
     }
     __syncthreads();
   }
+
+  if (MIXED) {
+    // drain whatever is still outstanding (only after a timeout), then free tensor memory
+    for (int k = 0; k < 3; ++k)
+      if (tcs.pend[k]) tc_wait(tcs, k);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tcs.tmem, (uint32_t)a.mx.tmem_cols);
+  }
 }
 
 int newton_threads() { return NT; }
 
-size_t newton_smem_bytes(int N, int m, int Q, bool h_in_smem) {
+static size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
+
+NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* mx) {
+  NewtonSmem s;
   const size_t NM = (size_t)N * m;
   const size_t B = (size_t)m * (m + 1) / 2;
-  size_t d = 4 * NM + 3 * (size_t)m * Q + B * Q + NWARPS * 8;
-  if (h_in_smem) d += NM * (NM + 1) / 2;
-  return d * sizeof(double);
+  const size_t fixed = (4 * NM + 3 * (size_t)m * Q + B * Q + NWARPS * 8) * sizeof(double);
+  const size_t h_bytes = h_in_smem ? NM * (NM + 1) / 2 * sizeof(double) : 0;
+  s.off_h = (uint32_t)align128(fixed);
+  if (!mx) {
+    s.bytes = s.off_h + h_bytes;
+    return s;
+  }
+  // With one pass the A staging may alias the packed H: H is written only after the last MMA of
+  // the pass has completed. With several passes a later pass would overwrite the H entries of an
+  // earlier one, so the staging gets its own region.
+  const bool alias = h_in_smem && mx->tpp >= mx->tiles;
+  const size_t region = alias ? std::max(h_bytes, mx->a_bytes) : h_bytes;
+  s.off_a = alias ? s.off_h : (uint32_t)align128(s.off_h + h_bytes);
+  s.off_b = (uint32_t)align128(alias ? s.off_h + region : s.off_a + mx->a_bytes);
+  s.bytes = s.off_b + 2 * mx->b_chunk_bytes;
+  return s;
+}
+
+MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem) {
+  MixedLayout L;
+  const int B = m * (m + 1) / 2;
+  L.n_pad = (N + 15) / 16 * 16;
+  L.kc = Q > 16 ? 32 : 16;
+  L.chunks = (Q + L.kc - 1) / L.kc;
+  L.tiles = (B * N + 127) / 128;
+  L.b_chunk_bytes = (size_t)2 * L.n_pad * L.kc * 2;
+  if (L.n_pad > 256) return L;
+  // row tiles per pass: bounded by tensor memory (512 columns) and by the shared-memory budget
+  for (int tpp = std::min(L.tiles, 512 / L.n_pad); tpp >= 1; --tpp) {
+    L.tpp = tpp;
+    L.a_bytes = (size_t)2 * tpp * 128 * L.kc * 2;
+    if (newton_smem(N, m, Q, h_in_smem, &L).bytes <= smem_budget) {
+      int cols = 32;
+      while (cols < tpp * L.n_pad) cols *= 2;
+      L.tmem_cols = cols;
+      L.ok = true;
+      return L;
+    }
+  }
+  L.tpp = 0;
+  return L;
 }
 
 // prepare = 1: raise the kernel's dynamic shared-memory limit (outside any stream capture);
 // prepare = 0: launch.
-template <int ENT, int PHYS, int M>
+template <int ENT, int PHYS, int M, bool MIXED>
 static cudaError_t launch_t(const NewtonArgs* a, int grid, size_t smem, bool h_in_smem, cudaStream_t s, int prepare,
                             int* blocks_per_sm) {
-  auto k = h_in_smem ? k_newton<ENT, PHYS, M, true> : k_newton<ENT, PHYS, M, false>;
+  auto k = h_in_smem ? k_newton<ENT, PHYS, M, true, MIXED> : k_newton<ENT, PHYS, M, false, MIXED>;
   if (prepare) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -339,35 +630,68 @@ static cudaError_t launch_t(const NewtonArgs* a, int grid, size_t smem, bool h_i
 
 template <typename F>
 static cudaError_t dispatch(int ent, int phys, int m, F&& f) {
+  using std::integral_constant;
   if (phys == PHYS_BURGERS && m == 1) {
-    if (ent == ENT_BARRIER) return f(std::integral_constant<int, ENT_BARRIER>(), std::integral_constant<int, PHYS_BURGERS>(), std::integral_constant<int, 1>());
-    if (ent == ENT_QUADRATIC) return f(std::integral_constant<int, ENT_QUADRATIC>(), std::integral_constant<int, PHYS_BURGERS>(), std::integral_constant<int, 1>());
+    if (ent == ENT_BARRIER) return f(integral_constant<int, ENT_BARRIER>(), integral_constant<int, PHYS_BURGERS>(), integral_constant<int, 1>());
+    if (ent == ENT_QUADRATIC) return f(integral_constant<int, ENT_QUADRATIC>(), integral_constant<int, PHYS_BURGERS>(), integral_constant<int, 1>());
   }
   if (phys == PHYS_EULER1D && m == 3) {
-    if (ent == ENT_EULER) return f(std::integral_constant<int, ENT_EULER>(), std::integral_constant<int, PHYS_EULER1D>(), std::integral_constant<int, 3>());
-    if (ent == ENT_QUADRATIC) return f(std::integral_constant<int, ENT_QUADRATIC>(), std::integral_constant<int, PHYS_EULER1D>(), std::integral_constant<int, 3>());
+    if (ent == ENT_EULER) return f(integral_constant<int, ENT_EULER>(), integral_constant<int, PHYS_EULER1D>(), integral_constant<int, 3>());
+    if (ent == ENT_QUADRATIC) return f(integral_constant<int, ENT_QUADRATIC>(), integral_constant<int, PHYS_EULER1D>(), integral_constant<int, 3>());
   }
   if (phys == PHYS_EULER2D && m == 4) {
-    if (ent == ENT_EULER) return f(std::integral_constant<int, ENT_EULER>(), std::integral_constant<int, PHYS_EULER2D>(), std::integral_constant<int, 4>());
-    if (ent == ENT_QUADRATIC) return f(std::integral_constant<int, ENT_QUADRATIC>(), std::integral_constant<int, PHYS_EULER2D>(), std::integral_constant<int, 4>());
+    if (ent == ENT_EULER) return f(integral_constant<int, ENT_EULER>(), integral_constant<int, PHYS_EULER2D>(), integral_constant<int, 4>());
+    if (ent == ENT_QUADRATIC) return f(integral_constant<int, ENT_QUADRATIC>(), integral_constant<int, PHYS_EULER2D>(), integral_constant<int, 4>());
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, int* blocks_per_sm) {
+cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, bool mixed, int* blocks_per_sm) {
   return dispatch(ent, phys, m, [&](auto E, auto P, auto MM) {
-    return launch_t<decltype(E)::value, decltype(P)::value, decltype(MM)::value>(nullptr, 0, smem, h_in_smem, nullptr, 1,
-                                                                                   blocks_per_sm);
+    constexpr int e_ = decltype(E)::value, p_ = decltype(P)::value, m_ = decltype(MM)::value;
+    return mixed ? launch_t<e_, p_, m_, true>(nullptr, 0, smem, h_in_smem, nullptr, 1, blocks_per_sm)
+                 : launch_t<e_, p_, m_, false>(nullptr, 0, smem, h_in_smem, nullptr, 1, blocks_per_sm);
   });
 }
 
-// phys is the PhysKind; ent the EntKind.
 cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, int grid, size_t smem, bool h_in_smem,
-                               cudaStream_t s) {
+                               bool mixed, cudaStream_t s) {
   return dispatch(ent, phys, m, [&](auto E, auto P, auto MM) {
-    return launch_t<decltype(E)::value, decltype(P)::value, decltype(MM)::value>(&a, grid, smem, h_in_smem, s, 0,
-                                                                                   nullptr);
+    constexpr int e_ = decltype(E)::value, p_ = decltype(P)::value, m_ = decltype(MM)::value;
+    return mixed ? launch_t<e_, p_, m_, true>(&a, grid, smem, h_in_smem, s, 0, nullptr)
+                 : launch_t<e_, p_, m_, false>(&a, grid, smem, h_in_smem, s, 0, nullptr);
   });
+}
+
+// Phi in the forms the mixed path reads: FP32 Phi^T [N][Q], and per K-chunk the two BF16 terms
+// (hi, lo) of B[j][k] = phi_j(xi_k) in the K-major tile layout (zero beyond N and Q).
+__global__ void k_phi_images(const double* __restrict__ PhiT, int N, int Q, int n_pad, int kc, int chunks,
+                             float* __restrict__ phiT32, uint8_t* __restrict__ img) {
+  const uint32_t sbo = tc::kmajor_sbo(kc);
+  const size_t b_img = (size_t)n_pad * kc * 2;
+  const int total = chunks * n_pad * kc;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int c = idx / (n_pad * kc);
+    const int rem = idx - c * n_pad * kc;
+    const int j = rem / kc, k = rem - j * kc;
+    const int q = c * kc + k;
+    const float x = (j < N && q < Q) ? (float)PhiT[(size_t)j * Q + q] : 0.f;
+    if (j < N && q < Q) phiT32[(size_t)j * Q + q] = x;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+    uint8_t* base = img + (size_t)c * 2 * b_img;
+    const uint32_t off = tc::kmajor_offset(j, k, sbo);
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = h;
+    *reinterpret_cast<__nv_bfloat16*>(base + b_img + off) = l;
+  }
+}
+
+cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayout& L, float* phiT32, uint8_t* img,
+                              cudaStream_t s) {
+  const int total = L.chunks * L.n_pad * L.kc;
+  k_phi_images<<<std::max(1, std::min(1024, (total + 255) / 256)), 256, 0, s>>>(PhiT, N, Q, L.n_pad, L.kc, L.chunks,
+                                                                                 phiT32, img);
+  return cudaGetLastError();
 }
 
 }  // namespace ipm

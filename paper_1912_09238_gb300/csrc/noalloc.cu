@@ -99,14 +99,15 @@ extern "C" ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, con
   cudaDeviceProp prop;
   e = cudaGetDeviceProperties(&prop, dev);
   if (e != cudaSuccess) return noalloc_fail(IPM_ECUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
-  const size_t smem_full = newton_smem_bytes(N, m, Q, true);
-  const size_t smem_lean = newton_smem_bytes(N, m, Q, false);
-  if (smem_lean > (size_t)prop.sharedMemPerBlockOptin)
+  const NewtonSmem sm_full = newton_smem(N, m, Q, true, nullptr);
+  const NewtonSmem sm_lean = newton_smem(N, m, Q, false, nullptr);
+  if (sm_lean.bytes > (size_t)prop.sharedMemPerBlockOptin)
     return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: N*m and Q too large for one CTA");
-  const bool h_in_smem = smem_full <= (size_t)prop.sharedMemPerBlockOptin;
-  const size_t smem = h_in_smem ? smem_full : smem_lean;
+  const bool h_in_smem = sm_full.bytes <= (size_t)prop.sharedMemPerBlockOptin;
+  const NewtonSmem sm = h_in_smem ? sm_full : sm_lean;
+  const size_t smem = sm.bytes;
   int bps = 0;
-  e = prepare_newton(entk, phys, m, smem, h_in_smem, &bps);
+  e = prepare_newton(entk, phys, m, smem, h_in_smem, false, &bps);
   if (e != cudaSuccess || bps < 1) return noalloc_fail(IPM_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
 
   // carve the scratch: scalars | Phi | PhiT | w | nodes | pairs | cell list | Hessian slots
@@ -183,7 +184,9 @@ extern "C" ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, con
   a.max_newton = opt.max_newton;
   a.max_halvings = opt.max_halvings;
   a.track_speed = 0;
-  e = launch_newton_phys(entk, phys, m, a, grid, smem, h_in_smem, s);
+  a.h_dump = nullptr;
+  a.off_h = sm.off_h;
+  e = launch_newton_phys(entk, phys, m, a, grid, smem, h_in_smem, false, s);
   if (e == cudaSuccess) e = launch_finalize(a.sc, d_iters, d_status, nullptr, n_cells, 0, n_cells, 0, s);
   if (e != cudaSuccess) return noalloc_fail(IPM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   if (stats) {

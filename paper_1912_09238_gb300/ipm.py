@@ -55,7 +55,7 @@ class ipm_stats(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int64), ("max_iters", ctypes.c_int32), ("failed_cells", ctypes.c_int32),
                 ("first_failed_cell", ctypes.c_int32), ("first_status", ctypes.c_int32),
                 ("dt", ctypes.c_double), ("t", ctypes.c_double), ("residual", ctypes.c_double),
-                ("steps", ctypes.c_int64)]
+                ("steps", ctypes.c_int64), ("tc_timeouts", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +90,7 @@ SIGNATURES = [
     ("ipm_get_moments_device", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("ipm_dual_solve", ctypes.c_int, [_vp, _P(ipm_stats)]),
     ("ipm_update", ctypes.c_int, [_vp, ctypes.c_double]),
+    ("ipm_assemble_hessian", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
     ("ipm_step", ctypes.c_int, [_vp, _P(ipm_stats)]),
     ("ipm_run", ctypes.c_int, [_vp, ctypes.c_int64, _P(ipm_stats)]),
     ("ipm_oneshot_step", ctypes.c_int, [_vp, _P(ipm_stats)]),
@@ -260,6 +261,12 @@ class Context:
 
     def dual_solve(self, sync=True):
         return self._stats_call("ipm_dual_solve", sync=sync)
+
+    def assemble_hessian(self):
+        """Packed lower-triangular Hessians at the current duals, (n_interior, NM(NM+1)/2)."""
+        d = self.dims
+        nm = d.N * d.m
+        return self._get("ipm_assemble_hessian", (d.n_interior, nm * (nm + 1) // 2))
 
     def update(self, dt):
         _check("ipm_update", lib().ipm_update(self.h, dt), self.h)
