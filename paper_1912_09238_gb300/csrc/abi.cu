@@ -33,6 +33,7 @@ struct ipm_ctx {
   uint32_t* d_pairs = nullptr;
   double *d_uhat = nullptr, *d_lam = nullptr, *d_unode = nullptr, *d_cell_resid = nullptr, *d_hwork = nullptr;
   int *d_iters = nullptr, *d_status = nullptr, *d_ghost_list = nullptr;
+  int* d_order = nullptr;       // longest-first Newton queue of the interior cells
   StepScalars* d_sc = nullptr;
   int n_fixed_ghosts = 0;
   // launch configuration
@@ -164,8 +165,10 @@ static Update1DArgs update_args(const ipm_ctx* c, double dt_override, bool resid
 // enqueue: queue reset, Newton over the interior
 static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_order(c->d_iters, c->n_interior, c->prob.nx, 0, c->d_order, s);
   if (e != cudaSuccess) return e;
   NewtonArgs a = newton_args(c, one_step);
+  a.cell_list = c->d_order;
   return launch_newton_phys(c->entk, c->phys, c->m, a, c->newton_grid, c->newton_smem, c->h_in_smem, c->mixed, s);
 }
 
@@ -208,7 +211,7 @@ static void free_ctx(ipm_ctx* c) {
   if (c->oneshot_exec) cudaGraphExecDestroy(c->oneshot_exec);
   void* ptrs[] = {c->d_Phi, c->d_PhiT, c->d_w, c->d_nodes, c->d_pairs, c->d_uhat, c->d_lam, c->d_unode,
                   c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc,
-                  c->d_phiT32, c->d_phi_img};
+                  c->d_phiT32, c->d_phi_img, c->d_order};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -356,7 +359,7 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
     if (c->mixed) bps = std::min(bps, 512 / c->mx.tmem_cols);
     c->newton_grid = std::max(1, std::min(c->n_interior, bps * prop.multiProcessorCount));
   }
-  c->hwork_stride = c->h_in_smem ? 0 : (size_t)c->NM * (c->NM + 1) / 2;
+  c->hwork_stride = c->h_in_smem ? 0 : packed_aug_count(c->NM);
   c->update_grid = std::min(c->n_interior, 65535);
 
   ipm_status st = IPM_OK;
@@ -387,6 +390,7 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   CK(cudaMalloc(&c->d_cell_resid, (size_t)c->n_cells * sizeof(double)), "cudaMalloc resid");
   CK(cudaMalloc(&c->d_iters, (size_t)c->n_cells * sizeof(int)), "cudaMalloc iters");
   CK(cudaMalloc(&c->d_status, (size_t)c->n_cells * sizeof(int)), "cudaMalloc status");
+  CK(cudaMalloc(&c->d_order, (size_t)c->n_interior * sizeof(int)), "cudaMalloc order");
   CK(cudaMalloc(&c->d_sc, sizeof(StepScalars)), "cudaMalloc scalars");
   if (!c->h_in_smem) CK(cudaMalloc(&c->d_hwork, (size_t)c->newton_grid * c->hwork_stride * sizeof(double)), "cudaMalloc hwork");
   if (st != IPM_OK) {

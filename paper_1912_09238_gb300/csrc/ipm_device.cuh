@@ -33,6 +33,9 @@ struct EntParams {
 };
 
 __host__ __device__ constexpr int packed_count(int m) { return m * (m + 1) / 2; }
+// entries of the packed lower triangle of the (NM+1) x (NM+1) matrix [[H, .], [g^T, .]] that the
+// Newton kernel factorises (the extra row carries the gradient through the forward substitution)
+__host__ __device__ constexpr size_t packed_aug_count(int NM) { return (size_t)(NM + 1) * (NM + 2) / 2; }
 // index of (a, b), a <= b, in the packed upper triangle of an m x m symmetric matrix
 __host__ __device__ constexpr int packed_ab(int a, int b, int m) { return a * m - a * (a - 1) / 2 + (b - a); }
 

@@ -46,6 +46,7 @@ int newton_threads();
 cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, int grid, size_t smem, bool h_in_smem,
                                bool mixed, cudaStream_t s);
 cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, bool mixed, int* blocks_per_sm);
+cudaError_t launch_order(const int* iters, int n_work, int nx, int gy, int* order, cudaStream_t s);
 cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayout& L, float* phiT32, uint8_t* img,
                               cudaStream_t s);
 cudaError_t prepare_update1d(int phys, int m, int Q);

@@ -139,6 +139,221 @@ __device__ __forceinline__ void hessian_fp64(const NewtonArgs& a, const double* 
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// (c) Blocked Cholesky factorisation with the forward substitution folded in.
+//
+// A is the packed lower triangle (row r at offset r(r+1)/2) of the (n+1) x (n+1) matrix
+// [[H, .], [g^T, .]]: rows 0..n-1 hold H, row n holds the gradient g. Factorising the leading n x n
+// block H = L L^T right-looking also turns row n into y = L^-1 g (the forward substitution), because
+// row n takes part in every scaling and trailing update but is never a pivot.
+// Panels of NB columns: (1) the NB x NB diagonal block is factorised by one warp with its rows in
+// registers; (2) every row below it (row n included) is solved against that block by one thread;
+// (3) the trailing rows and columns are updated with a rank-NB product, 2 x 2 outputs per thread.
+// s_P holds the current panel's columns row by row (stride PSTR), s_dinv the reciprocal pivots.
+// Returns false if a pivot is not positive and finite (H not numerically SPD).
+// ------------------------------------------------------------------------------------------------
+constexpr int NB = 8;
+constexpr int PSTR = NB + 1;
+
+__device__ __forceinline__ size_t rowoff(int r) { return (size_t)r * (r + 1) / 2; }
+// cell index of work item w on the interior of an (nx+2)-wide mesh with one ghost layer, starting at row gy
+__device__ __forceinline__ int work_cell(int w, int nx, int gy) { return (w / nx + gy) * (nx + 2) + (w % nx + 1); }
+
+// A[r][c] -= sum_k P[r][k] P[c][k] for rows r0..r0+3 (<= n) and columns c0, c0+1 (< n, <= r).
+// KW = NB: full panel (no guards on k); KW = 0: kw columns.
+template <int KW>
+__device__ __forceinline__ void trailing_tile(double* A, const double* s_P, int n, int r0, int c0, int kw) {
+  double acc[4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.0;
+  bool rv[4], cv[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) rv[i] = r0 + i <= n;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) cv[j] = c0 + j < n;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    if (KW == NB || k < kw) {
+      double p[4], q[2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) p[i] = rv[i] ? s_P[(r0 + i) * PSTR + k] : 0.0;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) q[j] = cv[j] ? s_P[(c0 + j) * PSTR + k] : 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) acc[i][j] = fma(p[i], q[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+      if (rv[i] && cv[j] && c0 + j <= r0 + i) A[rowoff(r0 + i) + c0 + j] -= acc[i][j];
+}
+
+// Factorise the NB x NB diagonal block at rows/columns kb..kb+kw-1 (already updated by all earlier
+// panels); called by one full warp, lane i owning row kb + i in registers. Writes L into A and into
+// the panel buffer P, the reciprocal pivots into s_dinv; sets *s_flag on a bad pivot.
+__device__ __forceinline__ void panel_diag(double* A, int kb, int kw, double* P, double* s_dinv, int* s_flag) {
+  const int lane = threadIdx.x & 31;
+  double row[NB];
+  const bool mine = lane < kw;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) row[j] = (mine && j <= lane) ? A[rowoff(kb + lane) + kb + j] : 0.0;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    if (k < kw) {
+      const double dkk = __shfl_sync(0xffffffffu, row[k], k);
+      ok = ok && dkk > 0.0 && isfinite(dkk);
+      const double id = rsqrt(fmax(dkk, 1e-300));
+      if (lane == k) row[k] = dkk * id;
+      if (lane > k) row[k] *= id;
+#pragma unroll
+      for (int j = k + 1; j < NB; ++j) {
+        if (j < kw) {
+          const double ljk = __shfl_sync(0xffffffffu, row[k], j);
+          if (lane >= j) row[j] = fma(-row[k], ljk, row[j]);
+        }
+      }
+      if (lane == 0) s_dinv[kb + k] = id;
+    }
+  }
+  if (mine) {
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      if (j <= lane) {
+        A[rowoff(kb + lane) + kb + j] = row[j];
+        P[(kb + lane) * PSTR + j] = row[j];
+      }
+    }
+  }
+  if (lane == 0 && !ok) *s_flag = 1;
+}
+
+// Rows r = kb+kw .. n of the panel: L[r][kb..kb+kw) = A[r][kb..kb+kw) L_bb^-T, by threads t0, t0+stride, ...
+__device__ __forceinline__ void panel_trsm(double* A, int n, int kb, int kw, double* P, const double* s_dinv, int t0,
+                                           int stride) {
+  for (int r = kb + kw + t0; r <= n; r += stride) {
+    const size_t ro = rowoff(r) + kb;
+    double x[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      if (k < kw) {
+        double v = A[ro + k];
+#pragma unroll
+        for (int j = 0; j < k; ++j) v = fma(-x[j], P[(kb + k) * PSTR + j], v);
+        x[k] = v * s_dinv[kb + k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      if (k < kw) {
+        A[ro + k] = x[k];
+        P[r * PSTR + k] = x[k];
+      }
+    }
+  }
+}
+
+// Rank-kw update with panel P of rows s1..n and columns s1..min(r, n-1), tiles of 4 rows x 2 columns,
+// by threads t0, t0+stride, ...
+__device__ __forceinline__ void trailing_update(double* A, int n, const double* P, int kw, int s1, int t0, int stride) {
+  const int TR = (n + 4 - s1) / 4;                // row tiles (rows s1..n)
+  const int ntiles = TR * (TR + 1);               // row tile ti has 2 ti + 2 column tiles
+  for (int t = t0; t < ntiles; t += stride) {
+    int ti = (int)((sqrtf(4.f * (float)t + 1.f) - 1.f) * 0.5f);
+    while (ti > 0 && ti * (ti + 1) > t) --ti;
+    while ((ti + 1) * (ti + 2) <= t) ++ti;
+    const int r0 = s1 + 4 * ti, c0 = s1 + 2 * (t - ti * (ti + 1));
+    if (c0 >= n) continue;
+    if (kw == NB) trailing_tile<NB>(A, P, n, r0, c0, kw);
+    else trailing_tile<0>(A, P, n, r0, c0, kw);
+  }
+}
+
+// Blocked right-looking Cholesky with one panel of look-ahead. s_P holds two panel buffers of
+// (n+1) x PSTR. Per panel p: (A) all threads apply panel p to the columns of panel p+1; then
+// (B) warp 0 factorises panel p+1 (diagonal block, then its rows below) while warps 1.. apply
+// panel p to the rest of the trailing matrix. The latency-bound diagonal block thus overlaps the
+// FP64-throughput-bound trailing update.
+__device__ bool cholesky_aug(double* A, int n, double* s_P, double* s_dinv, int* s_flag) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int pbuf = (n + 1) * PSTR;
+  if (tid == 0) *s_flag = 0;
+  __syncthreads();
+  {
+    const int kw0 = min(NB, n);
+    if (warp == 0) panel_diag(A, 0, kw0, s_P, s_dinv, s_flag);
+    __syncthreads();
+    if (*s_flag) return false;
+    panel_trsm(A, n, 0, kw0, s_P, s_dinv, tid, NT);
+    __syncthreads();
+  }
+  int p = 0;
+  for (int kb = 0; kb < n; kb += NB, ++p) {
+    const int kw = min(NB, n - kb), s0 = kb + kw;
+    if (s0 >= n) break;                            // only the gradient row is left: nothing to update
+    const double* P = s_P + (p & 1) * pbuf;
+    double* Pn = s_P + ((p + 1) & 1) * pbuf;
+    const int kw1 = min(NB, n - s0);
+    // (A) columns s0 .. s0+kw1-1 of rows s0..n
+    const int rows = n + 1 - s0;
+    for (int item = tid; item < rows * kw1; item += NT) {
+      const int r = s0 + item / kw1, c = s0 + item % kw1;
+      if (c > r) continue;
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+        if (k < kw) acc = fma(P[r * PSTR + k], P[c * PSTR + k], acc);
+      A[rowoff(r) + c] -= acc;
+    }
+    __syncthreads();
+    // (B)
+    if (warp == 0) {
+      panel_diag(A, s0, kw1, Pn, s_dinv, s_flag);
+      __syncwarp();
+      panel_trsm(A, n, s0, kw1, Pn, s_dinv, lane, 32);
+    } else {
+      trailing_update(A, n, P, kw, s0 + kw1, tid - 32, NT - 32);
+    }
+    __syncthreads();
+    if (*s_flag) return false;
+  }
+  return true;
+}
+
+// Back substitution L^T x = b in place on x (x holds b on entry), blocks of NB from the bottom: one
+// warp solves the diagonal block (lane i holds entry kb + i), then all threads update the entries above.
+__device__ void back_substitute(const double* A, int n, const double* s_dinv, double* x) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int kb = ((n - 1) / NB) * NB; kb >= 0; kb -= NB) {
+    const int kw = min(NB, n - kb);
+    if (tid < 32) {
+      double v = lane < kw ? x[kb + lane] : 0.0;
+#pragma unroll
+      for (int k = NB - 1; k >= 0; --k) {
+        if (k < kw) {
+          const double xk = __shfl_sync(0xffffffffu, v, k) * s_dinv[kb + k];
+          if (lane == k) v = xk;
+          if (lane < k) v = fma(-A[rowoff(kb + k) + kb + lane], xk, v);
+        }
+      }
+      if (lane < kw) x[kb + lane] = v;
+    }
+    __syncthreads();
+    for (int r = tid; r < kb; r += NT) {
+      double v = x[r];
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+        if (k < kw) v = fma(-A[rowoff(kb + k) + r], x[kb + k], v);
+      x[r] = v;
+    }
+    __syncthreads();
+  }
+}
+
 // Tensor-core pipeline state of one CTA (uniform across its threads).
 struct TcState {
   uint64_t* bars;     // [0] MMA completion, [1], [2] Phi chunk buffers
@@ -276,11 +491,12 @@ __device__ bool hessian_tc(const NewtonArgs& a, const float* s_wJf, double* s_H,
 }
 
 template <int ENT, int PHYS, int M, bool H_SMEM, bool MIXED>
-__global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
+__global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
   constexpr int B = packed_count(M);
   extern __shared__ __align__(128) double smem[];
   __shared__ int s_work;
   __shared__ int s_abort;
+  __shared__ int s_flag;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bars[3];
   const int N = a.tab.N, Q = a.tab.Q, NM = N * M;
@@ -294,11 +510,15 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
   double* s_u = s_dLam + M * Q;   // [M][Q]
   double* s_wJ = s_u + M * Q;     // [B][Q]  (float [B][Q] on the mixed path)
   double* s_red = s_wJ + B * Q;   // NWARPS * 8
+  double* s_wu = s_red + NWARPS * 8;  // [M][Q] w_k u_k
+  double* s_dinv = s_wu + M * Q;      // [NM] reciprocal pivots
+  double* s_P = s_dinv + NM;          // [2][(NM + 1) * PSTR] Cholesky panels (current, next)
   uint8_t* sbytes = reinterpret_cast<uint8_t*>(smem);
   double* s_H = H_SMEM ? reinterpret_cast<double*>(sbytes + a.off_h) : (a.hwork + (size_t)blockIdx.x * a.hwork_stride);
   uint8_t* sA = sbytes + a.off_a;
   uint8_t* sB = sbytes + a.off_b;
   const double* __restrict__ PhiT = a.tab.PhiT;
+  const double* __restrict__ Phi = a.tab.Phi;
   const double* __restrict__ w = a.tab.w;
   const size_t NPH = (size_t)NM * (NM + 1) / 2;
 
@@ -326,7 +546,7 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
     __syncthreads();
     const int wk = s_work;
     if (wk >= a.n_work) break;
-    const int cell = a.cell_list ? a.cell_list[wk] : (wk / a.nx + a.gy) * (a.nx + 2) + (wk % a.nx + 1);
+    const int cell = a.cell_list ? a.cell_list[wk] : work_cell(wk, a.nx, a.gy);
     double* lam_g = a.lam + (size_t)cell * NM;
     const double* uh_g = a.uhat + (size_t)cell * NM;
     for (int r = tid; r < NM; r += NT) {
@@ -342,6 +562,7 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
         double acc[M];
 #pragma unroll
         for (int c = 0; c < M; ++c) acc[c] = 0.0;
+#pragma unroll 4
         for (int i = 0; i < N; ++i) {
           const double ph = PhiT[(size_t)i * Q + q];
 #pragma unroll
@@ -360,7 +581,10 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
         const bool ok = Closure<ENT, M>::template eval<true>(L, a.ent, u, J, ss);
         const double wq = w[q];
 #pragma unroll
-        for (int c = 0; c < M; ++c) s_u[c * Q + q] = u[c];
+        for (int c = 0; c < M; ++c) {
+          s_u[c * Q + q] = u[c];
+          s_wu[c * Q + q] = wq * u[c];
+        }
         if (MIXED) {
           float* s_wJf = reinterpret_cast<float*>(s_wJ);
 #pragma unroll
@@ -381,31 +605,25 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
       block_sum<5>(red, s_red);
       const double L0 = red[0] - red[3];
       const double slack = a.slack_rel * (1.0 + red[1] + red[4]);
-      // (a3) gradient, one warp per moment
-      double gpart = 0.0;
-      for (int i = warp; i < N; i += NWARPS) {
-        double acc[M];
-#pragma unroll
-        for (int c = 0; c < M; ++c) acc[c] = 0.0;
-        for (int q = lane; q < Q; q += 32) {
-          const double ph = w[q] * PhiT[(size_t)i * Q + q];
-#pragma unroll
-          for (int c = 0; c < M; ++c) acc[c] = fma(ph, s_u[c * Q + q], acc[c]);
-        }
+      // (a3) gradient g_(i,c) = sum_k w_k u_c(xi_k) phi_i(xi_k) - u_hat_(i,c), one thread per entry
+      for (int r = tid; r < NM; r += NT) {
+        const int i = r / M, c = r - i * M;
+        const double* wu = s_wu + c * Q;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int q = 0; q < Q; ++q) acc = fma(Phi[(size_t)q * N + i], wu[q], acc);
+        s_g[r] = acc - s_uh[r];
+      }
+      __syncthreads();
+      double gres[1] = {0.0};
+      for (int i = tid; i < N; i += NT) {
         double nrm = 0.0;
 #pragma unroll
-        for (int c = 0; c < M; ++c) {
-          const double gi = warp_sum(acc[c]) - s_uh[i * M + c];
-          nrm = fma(gi, gi, nrm);
-          if (lane == 0) s_g[i * M + c] = gi;
-        }
-        gpart += sqrt(nrm);
+        for (int c = 0; c < M; ++c) nrm = fma(s_g[i * M + c], s_g[i * M + c], nrm);
+        gres[0] += sqrt(nrm);
       }
-      if (lane == 0) s_red[warp] = gpart;
-      __syncthreads();
-      double res = 0.0;
-      for (int ww = 0; ww < NWARPS; ++ww) res += s_red[ww];
-      __syncthreads();
+      block_sum<1>(gres, s_red);
+      const double res = gres[0];
 
       if (red[2] > 0.0) { st = ST_INFEASIBLE; break; }
       if (!isfinite(res)) { st = ST_NONFINITE; break; }
@@ -436,50 +654,19 @@ __global__ void __launch_bounds__(NT) k_newton(NewtonArgs a) {
         break;
       }
 
-      // (c) Cholesky in place
-      bool spd = true;
-      for (int k = 0; k < NM; ++k) {
-        const size_t kk = (size_t)k * (k + 1) / 2 + k;
-        const double dkk = s_H[kk];
-        if (!(dkk > 0.0) || !isfinite(dkk)) { spd = false; break; }
-        const double d = sqrt(dkk), id = 1.0 / d;
-        for (int i = k + 1 + tid; i < NM; i += NT) s_H[(size_t)i * (i + 1) / 2 + k] *= id;
-        __syncthreads();
-        if (tid == 0) s_H[kk] = d;
-        for (int i = k + 1 + warp; i < NM; i += NWARPS) {
-          const size_t ri = (size_t)i * (i + 1) / 2;
-          const double lik = s_H[ri + k];
-          for (int j = k + 1 + lane; j <= i; j += 32) s_H[ri + j] = fma(-lik, s_H[(size_t)j * (j + 1) / 2 + k], s_H[ri + j]);
-        }
-        __syncthreads();
-      }
-      if (!spd) { st = ST_NOTSPD; break; }
-      // triangular solves with one warp: L y = -g, L^T Delta = y
-      if (warp == 0) {
-        for (int r = lane; r < NM; r += 32) s_d[r] = -s_g[r];
-        __syncwarp();
-        for (int k = 0; k < NM; ++k) {
-          const double yk = s_d[k] / s_H[(size_t)k * (k + 1) / 2 + k];
-          __syncwarp();
-          for (int i = k + 1 + lane; i < NM; i += 32) s_d[i] = fma(-s_H[(size_t)i * (i + 1) / 2 + k], yk, s_d[i]);
-          if (lane == 0) s_d[k] = yk;
-          __syncwarp();
-        }
-        for (int k = NM - 1; k >= 0; --k) {
-          const size_t rk = (size_t)k * (k + 1) / 2;
-          const double xk = s_d[k] / s_H[rk + k];
-          __syncwarp();
-          for (int i = lane; i < k; i += 32) s_d[i] = fma(-s_H[rk + i], xk, s_d[i]);
-          if (lane == 0) s_d[k] = xk;
-          __syncwarp();
-        }
-      }
+      // (c) Cholesky with the gradient as augmented row NM, then L^T Delta = -L^-1 g
+      for (int r = tid; r < NM; r += NT) s_H[rowoff(NM) + r] = s_g[r];
       __syncthreads();
+      if (!cholesky_aug(s_H, NM, s_P, s_dinv, &s_flag)) { st = ST_NOTSPD; break; }
+      for (int r = tid; r < NM; r += NT) s_d[r] = -s_H[rowoff(NM) + r];
+      __syncthreads();
+      back_substitute(s_H, NM, s_dinv, s_d);
       // direction at the nodes, slope, Delta . u_hat
       for (int q = tid; q < Q; q += NT) {
         double acc[M];
 #pragma unroll
         for (int c = 0; c < M; ++c) acc[c] = 0.0;
+#pragma unroll 4
         for (int i = 0; i < N; ++i) {
           const double ph = PhiT[(size_t)i * Q + q];
 #pragma unroll
@@ -570,8 +757,9 @@ NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* m
   NewtonSmem s;
   const size_t NM = (size_t)N * m;
   const size_t B = (size_t)m * (m + 1) / 2;
-  const size_t fixed = (4 * NM + 3 * (size_t)m * Q + B * Q + NWARPS * 8) * sizeof(double);
-  const size_t h_bytes = h_in_smem ? NM * (NM + 1) / 2 * sizeof(double) : 0;
+  const size_t fixed =
+      (4 * NM + 4 * (size_t)m * Q + B * Q + NWARPS * 8 + NM + 2 * (NM + 1) * PSTR) * sizeof(double);
+  const size_t h_bytes = h_in_smem ? packed_aug_count((int)NM) * sizeof(double) : 0;
   s.off_h = (uint32_t)align128(fixed);
   if (!mx) {
     s.bytes = s.off_h + h_bytes;
@@ -661,6 +849,52 @@ cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, in
     return mixed ? launch_t<e_, p_, m_, true>(&a, grid, smem, h_in_smem, s, 0, nullptr)
                  : launch_t<e_, p_, m_, false>(&a, grid, smem, h_in_smem, s, 0, nullptr);
   });
+}
+
+// Longest-first order of the Newton work queue: the work items (interior cells, mapped as in the
+// Newton kernel) sorted by the Newton count of their previous solve, descending; ties in any order.
+// The order decides only which CTA takes which cell when: each cell's arithmetic is independent of
+// it, so results do not depend on it. One CTA; warp-aggregated shared-memory atomics.
+constexpr int ORDER_KEYS = 128;
+constexpr int ORDER_T = 1024;
+
+__global__ void __launch_bounds__(ORDER_T) k_order(const int* __restrict__ iters, int n_work, int nx, int gy,
+                                                   int* __restrict__ order) {
+  __shared__ int cnt[ORDER_KEYS];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int k = tid; k < ORDER_KEYS; k += ORDER_T) cnt[k] = 0;
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int base = 0; base < n_work; base += ORDER_T) {
+      const int w = base + tid;
+      const bool valid = w < n_work;
+      const int cell = valid ? work_cell(w, nx, gy) : 0;
+      const int key = valid ? (ORDER_KEYS - 1) - min(max(iters[cell], 0), ORDER_KEYS - 1) : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      int at = 0;
+      if (valid && lane == leader) at = atomicAdd(&cnt[key], __popc(peers));
+      at = __shfl_sync(0xffffffffu, at, leader);
+      if (pass == 1 && valid) order[at + rank] = cell;
+    }
+    __syncthreads();
+    if (pass == 0 && tid == 0) {
+      // counts -> starting offsets (key 0 = most iterations first)
+      int run = 0;
+      for (int k = 0; k < ORDER_KEYS; ++k) {
+        const int c = cnt[k];
+        cnt[k] = run;
+        run += c;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_order(const int* iters, int n_work, int nx, int gy, int* order, cudaStream_t s) {
+  k_order<<<1, ORDER_T, 0, s>>>(iters, n_work, nx, gy, order);
+  return cudaGetLastError();
 }
 
 // Phi in the forms the mixed path reads: FP32 Phi^T [N][Q], and per K-chunk the two BF16 terms

@@ -127,7 +127,7 @@ extern "C" ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, con
   if (off > IPM_NOALLOC_SCRATCH_BYTES)
     return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: tables and cell list exceed the scratch size");
   int grid = std::max(1, std::min(n_cells, bps * prop.multiProcessorCount));
-  const size_t hslot = h_in_smem ? 0 : (size_t)NM * (NM + 1) / 2 * sizeof(double);
+  const size_t hslot = h_in_smem ? 0 : packed_aug_count(NM) * sizeof(double);
   size_t o_h = off;
   if (!h_in_smem) {
     const size_t room = IPM_NOALLOC_SCRATCH_BYTES - off;
