@@ -5,7 +5,10 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
 One step = one call of ipm_step: the Newton solve of the dual problem in every cell, the CFL time
-step, the kinetic-flux moment update (one captured CUDA graph). Prints one JSON line (rank 0).
+step, the kinetic-flux moment update (one captured CUDA graph). The headline is the mixed-precision
+path (Hessian on the tensor cores, everything else FP64); the plain FP64 GPU path is timed on the
+same workload in the same run and reported beside it (--precision fp64 makes FP64 the headline).
+Prints one JSON line (rank 0).
 --impl reference times the CPU oracle on the host cores instead (each step a bounded sample).
 With torchrun (N > 1) every rank runs an independent replica of the workload on its own GPU
 (the method needs no data exchange between replicas), value = all cells updated / max time.
@@ -26,6 +29,7 @@ if ROOT not in sys.path:
 METRIC = "IPM cell-steps/s (mixed+batched vs FP64 GPU at equal error); p50/p99 latency"
 UNIT = "cell-steps/s"
 FP64_PEAK_TFLOPS = 1.25      # nominal dense FP64 of a GB300 (probe: 1.19 measured with FMA chains)
+KERNELS_PER_STEP = 4         # k_order, k_newton, k_update1d, k_finalize (one CUDA graph per step)
 L2_FLUSH_BYTES = 512 << 20   # > 4x the 126 MiB L2
 WINDOW = dict(nx=200, x_lo=0.45, x_hi=0.55)   # same dx as the 2000-cell mesh, around the interface
 
@@ -104,19 +108,85 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def newton_flops(N, m, Q, cells, iters):
+def newton_fp64_flops(N, m, Q, cells, iters, with_hessian):
     """Algorithmic FP64 flops of one Newton launch: every cell evaluates the gradient (reconstruction +
-    projection) once more than it updates; every update adds the Hessian (unique entries, B*N(N+1)/2
-    Q-term dot products), the Cholesky factorisation, two triangular solves and the direction at the
-    nodes. Closures and line-search trials are not counted."""
+    projection, 4QNm) once more than it updates; every update adds the Cholesky factorisation
+    ((Nm)^3/3), two triangular solves (2 (Nm)^2) and the direction at the nodes (2QNm), and on the FP64
+    path the Hessian (B Q N(N+1): unique entries of B blocks, Q-term dot products). Closures and
+    line-search trials are not counted."""
     B = m * (m + 1) // 2
     NM = N * m
     grad_eval = 4.0 * Q * N * m
-    per_update = B * Q * N * (N + 1) + NM ** 3 / 3.0 + 2.0 * NM ** 2 + 2.0 * Q * N * m
+    per_update = NM ** 3 / 3.0 + 2.0 * NM ** 2 + 2.0 * Q * N * m
+    if with_hessian:
+        per_update += B * Q * N * (N + 1)
     return (cells + iters) * grad_eval + iters * per_update
 
 
+def hessian_tc_flops(N, m, Q, iters):
+    """Tensor-core flops of the mixed Hessian per launch: per update, row tiles of 128 over the B*N rows,
+    n_pad = N rounded up to 16 columns, Q rounded up to the K-chunk, three BF16 products each."""
+    B = m * (m + 1) // 2
+    tiles = -(-B * N // 128)
+    n_pad = -(-N // 16) * 16
+    kc = 32 if Q > 16 else 16
+    q_pad = -(-Q // kc) * kc
+    return iters * 3 * 2.0 * tiles * 128 * n_pad * q_pad
+
+
 # ------------------------------------------------------------------------------------------------
+def measure(args, precision, flush, stream, barrier, ws):
+    """W warm-up + K timed Algorithm-1 steps of one precision; returns (summary dict, context)."""
+    import numpy as np
+    import torch
+    from tests._cases import gpu_context
+
+    w = workload()
+    ctx = gpu_context(w, precision=precision)
+    ctx.set_stream(stream.cuda_stream)
+    d = ctx.dims
+    for _ in range(args.warmup):
+        flush.zero_()
+        ctx.step(sync=False)
+    barrier()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    newton_ms, iters = [], []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        ctx.step(sync=False)
+        ev[k][1].record(stream)
+        nm, _, _ = ctx.step_timing()               # waits for this step; outside the event pair
+        s = ctx.sync_stats()
+        newton_ms.append(nm)
+        iters.append(s.newton_iters)
+        if s.failed_cells or s.tc_timeouts:
+            raise RuntimeError(f"dual solve failed in {s.failed_cells} cells: {s.as_dict()}")
+    barrier()
+    cl = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    cells = d.n_interior
+    flops = [newton_fp64_flops(d.N, d.m, d.Q, cells, it, precision == "fp64") for it in iters]
+    newton_s = statistics.mean(newton_ms) / 1e3
+    out = {"value": ws * cells * args.steps / total_s, "ms_per_step": statistics.mean(step_ms),
+           "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
+           "newton_ms_mean": statistics.mean(newton_ms), "newton_share_of_step": sum(newton_ms) / sum(step_ms),
+           "fp64_flops_per_launch": sum(flops) / len(flops),
+           "fp64_tflops": (sum(flops) / len(flops)) / newton_s / 1e12,
+           "newton_iters_per_step": statistics.mean(iters), "clocks": cl, "cells": cells, "dims": d}
+    if precision == "mixed":
+        tcf = statistics.mean(hessian_tc_flops(d.N, d.m, d.Q, it) for it in iters)
+        out["tensor_flops_per_launch"] = tcf
+    return out, ctx
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -128,15 +198,10 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
     __graft_entry__.build()
-    from tests._cases import gpu_context
 
     w = workload()
-    precision = args.precision
-    ctx = gpu_context(w, precision=precision)
     stream = torch.cuda.Stream()                    # a real (non-default) stream shared by torch and libipm
     torch.cuda.set_stream(stream)
-    ctx.set_stream(stream.cuda_stream)
-    d = ctx.dims
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     assert torch.cuda.current_stream().cuda_stream == stream.cuda_stream != 0
 
@@ -146,47 +211,31 @@ def run_gpu(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        flush.zero_()
-        ctx.step(sync=False)
-    barrier()
-    clocks = Clocks(local)
-    clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    step_ms, newton_ms, iters = [], [], []
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        ctx.step(sync=False)
-        ev[k][1].record(stream)
-        nm, _, _ = ctx.step_timing()               # waits for this step; outside the event pair
-        s = ctx.sync_stats()
-        newton_ms.append(nm)
-        iters.append(s.newton_iters)
-        if s.failed_cells:
-            raise RuntimeError(f"dual solve failed in {s.failed_cells} cells: {s.as_dict()}")
-    barrier()
-    cl = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    cells = d.n_interior
-    value = ws * cells * args.steps / total_s
+    precision = args.precision
+    main, ctx = measure(args, precision, flush, stream, barrier, ws)
+    d = main["dims"]
+    cells = main["cells"]
+    # the plain FP64 GPU path on the same workload and steps (the comparison the metric names)
+    ref = None
+    if precision == "mixed" and not args.no_fp64_compare:
+        ref, rctx = measure(args, "fp64", flush, stream, barrier, ws)
+        # equal error: both paths ran the same steps from the same initial data
+        a, b = ctx.get_moments(), rctx.get_moments()
+        ref["max_rel_diff_moments_vs_mixed"] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        rctx.close()
 
-    # roofline of the dominant kernel (the Newton solve), FP64-ALU bound
-    flops = [newton_flops(d.N, d.m, d.Q, cells, it) for it in iters]
-    achieved = (sum(flops) / len(flops)) / (statistics.mean(newton_ms) / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_newton (fused dual solve: reconstruction, closure, gradient, "
-                "Hessian, Cholesky, solves, Armijo)", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "nominal GB300 dense FP64 (recipe); an FMA-chain probe measured 1.19 TFLOP/s",
-                "traffic": None, "newton_ms_mean": round(statistics.mean(newton_ms), 4),
-                "newton_share_of_step": round(sum(newton_ms) / sum(step_ms), 4),
-                "algorithmic_flops_per_launch": round(sum(flops) / len(flops)),
-                "newton_iters_per_step": round(statistics.mean(iters), 1)}
+                "Hessian" + (" on tcgen05 tensor cores" if precision == "mixed" else "") +
+                ", Cholesky, solves, Armijo)", "achieved": round(main["fp64_tflops"], 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(main["fp64_tflops"] / FP64_PEAK_TFLOPS, 4),
+                "peak_source": "nominal GB300 dense FP64 (fallback table; no FP64 figure in the measured peaks); "
+                               "an FMA-chain probe measured 1.19 TFLOP/s",
+                "traffic": None, "newton_ms_mean": round(main["newton_ms_mean"], 4),
+                "newton_share_of_step": round(main["newton_share_of_step"], 4),
+                "algorithmic_fp64_flops_per_launch": round(main["fp64_flops_per_launch"]),
+                "newton_iters_per_step": round(main["newton_iters_per_step"], 1)}
+    if precision == "mixed":
+        roofline["tensor_bf16_flops_per_launch"] = round(main["tensor_flops_per_launch"])
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     shape = ctx.shape
@@ -214,13 +263,22 @@ def run_gpu(args):
            "d2h_bytes_per_step": 2 * nbytes, "api": "ipm_set_moments + ipm_set_duals + ipm_step + "
            "ipm_get_moments + ipm_get_duals (host buffers, pinned)"}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
-            "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
+            "p50_step_ms": main["p50_step_ms"], "p99_step_ms": main["p99_step_ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if precision == "fp64" else "f64+bf16", "data": "synthetic",
             "config": workload_desc(w, precision), "roofline": roofline, "e2e": e2e,
-            "gpu_launches": 3 * args.steps, "clocks": cl}
+            "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": main["clocks"]}
+    if ref is not None:
+        line["fp64_gpu"] = {"value": ref["value"], "unit": UNIT, "ms_per_step": ref["ms_per_step"],
+                            "newton_ms_mean": ref["newton_ms_mean"],
+                            "newton_iters_per_step": ref["newton_iters_per_step"],
+                            "fp64_tflops": round(ref["fp64_tflops"], 4),
+                            "max_rel_diff_moments_vs_mixed": ref["max_rel_diff_moments_vs_mixed"],
+                            "speedup_mixed_over_fp64": main["value"] / ref["value"]}
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_bench(args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -228,6 +286,97 @@ def run_gpu(args):
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
+def _request(w, precision):
+    from paper_1912_09238_gb300 import ipm
+    pr = ipm.make_problem(w["kind"], w["nx"], w["x_lo"], w["x_hi"], bc=w["bc"], cfl=w["cfl"], t_end=w["t_end"],
+                          gamma=w["gamma"], x0=w["x0"], dx0=w["dx0"], left=w["left"], dleft=w.get("dleft"),
+                          right=w["right"], dright=w.get("dright"))
+    o = ipm.default_options(precision, newton_tol=w.get("newton_tol", 1e-10))
+    return ipm.make_request(pr, w["p"], w["M"], w["nq"], w["entropy"], w.get("u_minus", 0.0), w.get("u_plus", 0.0),
+                            o, max_steps=w["steps"])
+
+
+def _serve(reqs, arrivals, max_active):
+    """Replay the arrivals against one server; returns per-request (latency_s, cell_steps) and the makespan."""
+    import numpy as np
+    from paper_1912_09238_gb300 import ipm
+    srv = ipm.Server(mem_cap_bytes=0, max_active=max_active)
+    t0 = time.perf_counter()
+    tickets = []
+    for (req, w), at in zip(reqs, arrivals):
+        dt = at - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(req))
+    srv.drain(1800.0)
+    res = [srv.poll(t, fetch=False)[0] for t in tickets]
+    srv.close()
+    if any(r.status != 0 for r in res):
+        raise RuntimeError("served request failed: " + str([(r.status, r.error) for r in res if r.status != 0][:5]))
+    lat = np.array([r.finish_s - r.submit_s for r in res])
+    first = min(r.submit_s for r in res)
+    last = max(r.finish_s for r in res)
+    cell_steps = sum(w["nx"] * w["steps"] for _, w in reqs)
+    return lat, cell_steps, last - first
+
+
+def serving_bench(args):
+    """Serving workload (seeded Poisson arrivals of 1-D Burgers / Euler requests of mixed sizes, N 3..84,
+    Q = (degree+1)^dims): the mixed-precision server at saturation and at 0.8x its saturation rate, and the
+    same requests run one after another on the plain FP64 GPU path."""
+    import numpy as np
+    import torch
+    from paper_1912_09238_gb300 import workloads
+    from tests._cases import gpu_context
+    n, steps = args.serving_requests, args.serving_steps
+    stream = [w for _, w in workloads.serving_requests(n, seed=1234, steps=steps)]
+    reqs = [(_request(w, "mixed"), w) for w in stream]
+    # saturation: everything arrives at once
+    lat_sat, cs, span = _serve(reqs, [0.0] * n, args.serving_slots)
+    rate_sat = n / span
+    # Poisson arrivals at 0.8 x the saturation rate (same requests, seeded inter-arrival times)
+    rng = np.random.default_rng(1234)
+    arr = np.cumsum(rng.exponential(1.0 / (0.8 * rate_sat), n)) - 0.0
+    arr -= arr[0]
+    lat, cs2, span2 = _serve(reqs, list(arr), args.serving_slots)
+    # sequential FP64 GPU: one request at a time, each to completion
+    torch.cuda.synchronize()
+    t_seq = 0.0
+    seq_lat = []
+    for w in stream:
+        t0 = time.perf_counter()
+        ctx = gpu_context(w, precision="fp64")
+        for _ in range(w["steps"]):
+            ctx.step(sync=False)
+        s = ctx.sync_stats()
+        ctx.get_moments()
+        ctx.close()
+        dt = time.perf_counter() - t0
+        if s.failed_cells:
+            raise RuntimeError("sequential FP64 request failed")
+        t_seq += dt
+        seq_lat.append(dt)
+    return {
+        "workload": (f"{n} seeded requests (seed 1234), each 1-D Burgers or 1-D Euler, cells U[200,4000], total "
+                     f"degree 2-6 in 1-3 uniform dims (N 3-84), tensor Gauss (degree+1)^dims, {steps} Algorithm-1 "
+                     f"steps each, mixed precision, {args.serving_slots} slots, memory cap 90% of free HBM"),
+        "cell_steps": cs,
+        "saturation": {"value": cs / span, "unit": UNIT, "makespan_s": span, "requests_per_s": rate_sat,
+                       "p50_latency_s": float(np.percentile(lat_sat, 50)),
+                       "p99_latency_s": float(np.percentile(lat_sat, 99))},
+        "poisson_0.8x": {"value": cs2 / span2, "unit": UNIT, "makespan_s": span2, "rate_per_s": 0.8 * rate_sat,
+                         "p50_latency_s": float(np.percentile(lat, 50)),
+                         "p99_latency_s": float(np.percentile(lat, 99))},
+        "sequential_fp64_gpu": {"value": cs / t_seq, "unit": UNIT, "total_s": t_seq,
+                                "p50_latency_s": float(np.percentile(seq_lat, 50)),
+                                "p99_latency_s": float(np.percentile(seq_lat, 99)),
+                                "note": "each request alone, wall time including context set-up, as the server's "
+                                        "latencies include it"},
+        "speedup_served_mixed_over_sequential_fp64": (cs / span) / (cs / t_seq),
+    }
 
 
 # ------------------------------------------------------------------------------------------------
@@ -298,8 +447,13 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--serving-steps", type=int, default=10)
+    ap.add_argument("--serving-slots", type=int, default=32)
     ap.add_argument("--oracle-sample", choices=["first_step", "window"], default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:

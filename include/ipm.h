@@ -258,6 +258,66 @@ ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, const ipm_basi
                                   double* d_lam, double* d_nodal, int* d_iters, int* d_status,
                                   void* stream, ipm_stats* stats);
 
+/* Device bytes ipm_init would allocate for this problem (state, tables, workspaces), without
+ * allocating anything. Validates the arguments like ipm_init (IPM_EINVAL on the same errors). */
+ipm_status ipm_footprint(const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad,
+                         const ipm_entropy* entropy, const ipm_options* options, size_t* bytes);
+
+/* ------------------------------------------------------------------------------------------------
+ * Serving: a continuous-batching request server for IPM runs (the paper has no serving layer; this
+ * is the library's request API around Algorithm 1).
+ *
+ * A server owns one worker thread on the device that was current at ipm_server_create. Submitted
+ * requests wait in arrival order until a slot and device memory are free (admission by the
+ * ipm_footprint of each request against the memory cap); an admitted request gets a resident context
+ * (its moments and duals stay on the device for its whole run) on a stream of its own, and the worker
+ * keeps launching its time steps (one CUDA graph each) interleaved with every other active request,
+ * so the kernels of different requests overlap on the GPU. A request finishes when it reaches its
+ * t_end (or max_steps); its final moments are copied to the host and its slot and memory are freed
+ * for the next waiting request. Each request's results are independent of what else runs: the same
+ * request gives the same moments alone and in any mix.
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct ipm_server ipm_server;
+
+typedef struct {
+  ipm_problem problem;
+  ipm_basis basis;
+  ipm_quadrature quad;
+  ipm_entropy entropy;
+  ipm_options options;
+  int64_t max_steps;        /* at most this many Algorithm-1 steps (problem.t_end > 0: stop at t_end) */
+} ipm_request;
+
+typedef struct {
+  int32_t status;           /* ipm_status of the run: IPM_OK, or the first per-cell failure */
+  ipm_dims dims;
+  ipm_stats stats;          /* counters after the last step (t, steps, Newton updates of the last step) */
+  double submit_s;          /* server clock (seconds since ipm_server_create) at ipm_submit */
+  double start_s;           /* ... when the request was admitted */
+  double finish_s;          /* ... when its final moments were on the host */
+  size_t footprint_bytes;   /* ipm_footprint of the request */
+  char error[192];          /* message of the failing call when status is not IPM_OK, else empty */
+} ipm_result;
+
+/* Create a server. mem_cap_bytes: device memory the active requests may hold together (0 = 90% of
+ * the free device memory now); max_active: concurrent resident requests (slots), >= 1. */
+ipm_status ipm_server_create(size_t mem_cap_bytes, int max_active, ipm_server** out);
+
+/* Queue a request (copied); *ticket identifies it. IPM_EINVAL for a request ipm_init would reject,
+ * IPM_ENOMEM if its footprint alone exceeds the cap. Thread-safe. */
+ipm_status ipm_submit(ipm_server* srv, const ipm_request* req, uint64_t* ticket);
+
+/* IPM_EAGAIN while the request is waiting or running. Once it is done: fills *out, and when moments
+ * is not NULL copies its final moments ([cell][moment][variable], count = n_cells*N*m) and releases
+ * the ticket (later polls of it return IPM_EINVAL). Thread-safe. */
+ipm_status ipm_poll(ipm_server* srv, uint64_t ticket, ipm_result* out, double* moments, size_t count);
+
+/* Block until every submitted request is done (or timeout_s seconds have passed: IPM_ETIMEOUT). */
+ipm_status ipm_server_drain(ipm_server* srv, double timeout_s);
+
+/* Stop the worker: waiting requests are dropped, running ones finish first. NULL is accepted. */
+void ipm_server_destroy(ipm_server* srv);
+
 /* Host-only: the basis and quadrature tables the library uses (no GPU needed).
  * indices: N*p ints (graded order), nodes: Q*p doubles, weights: Q doubles (density folded in,
  * summing to 1), phi: Q*N doubles with phi[k*N + i] = phi_i(xi_k). Any output may be NULL.

@@ -226,6 +226,107 @@ static cudaError_t upload(T** dst, const std::vector<T>& src) {
   return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+// Validate the problem and fill every size, table and launch parameter of c (no device allocation).
+static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad,
+                           const ipm_entropy* entropy, const ipm_options& opt) {
+  if (basis->p < 1 || basis->p > 3 || basis->total_degree < 0 || quad->n_per_dim < 1)
+    return fail(nullptr, IPM_EINVAL, "ipm_init: basis needs 1 <= p <= 3, M >= 0, n_per_dim >= 1");
+  if (problem->kind != IPM_BURGERS_1D && problem->kind != IPM_EULER_1D)
+    return fail(nullptr, IPM_EINVAL, "ipm_init: only 1-D problems are built in this version");
+  if (problem->nx < 1 || !(problem->x_hi > problem->x_lo) || !(problem->cfl > 0))
+    return fail(nullptr, IPM_EINVAL, "ipm_init: bad mesh or cfl");
+  if ((problem->bc_left == IPM_BC_PERIODIC) != (problem->bc_right == IPM_BC_PERIODIC))
+    return fail(nullptr, IPM_EINVAL, "ipm_init: periodic must be set on both ends");
+  if (opt.precision != IPM_PREC_FP64 && opt.precision != IPM_PREC_MIXED)
+    return fail(nullptr, IPM_EINVAL, "ipm_init: unknown precision");
+  c->prob = *problem;
+  c->basis = *basis;
+  c->quad = *quad;
+  c->ent = *entropy;
+  c->opt = opt;
+  c->m = problem->kind == IPM_BURGERS_1D ? 1 : 3;
+  c->phys = problem->kind == IPM_BURGERS_1D ? PHYS_BURGERS : PHYS_EULER1D;
+  c->entk = entropy->kind == IPM_ENTROPY_QUADRATIC ? ENT_QUADRATIC
+                                                     : (entropy->kind == IPM_ENTROPY_BOUNDED_BARRIER ? ENT_BARRIER : ENT_EULER);
+  const bool ent_ok = c->entk == ENT_QUADRATIC || (c->entk == ENT_BARRIER && c->phys == PHYS_BURGERS) ||
+                      (c->entk == ENT_EULER && c->phys != PHYS_BURGERS);
+  if (!ent_ok) {
+    return fail(nullptr, IPM_EINVAL, "ipm_init: entropy does not match the problem");
+  }
+  if (c->entk == ENT_BARRIER && !(entropy->u_plus > entropy->u_minus)) {
+    return fail(nullptr, IPM_EINVAL, "ipm_init: barrier needs u_plus > u_minus");
+  }
+  build_tables(basis->p, basis->total_degree, quad->n_per_dim, c->tab);
+  c->N = c->tab.N;
+  c->Q = c->tab.Q;
+  c->NM = c->N * c->m;
+  c->n_interior = problem->nx;
+  c->n_cells = problem->nx + 2;
+  c->dx = (problem->x_hi - problem->x_lo) / problem->nx;
+  if (c->N > 65535) {
+    return fail(nullptr, IPM_EINVAL, "ipm_init: too many moments");
+  }
+
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    return fail(nullptr, IPM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  }
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, c->device);
+  if (e != cudaSuccess) {
+    return fail(nullptr, IPM_ECUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
+  }
+  // launch configuration of the Newton kernel: packed H in shared memory when it fits
+  const size_t budget = (size_t)prop.sharedMemPerBlockOptin;
+  c->mixed = opt.precision == IPM_PREC_MIXED;
+  if (c->mixed) {
+    c->h_in_smem = true;
+    c->mx = mixed_layout(c->N, c->m, c->Q, budget, true);
+    if (!c->mx.ok) {
+      c->h_in_smem = false;
+      c->mx = mixed_layout(c->N, c->m, c->Q, budget, false);
+    }
+    if (!c->mx.ok) {
+        return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for the mixed-precision Newton kernel");
+    }
+    c->sm = newton_smem(c->N, c->m, c->Q, c->h_in_smem, &c->mx);
+  } else {
+    const NewtonSmem full = newton_smem(c->N, c->m, c->Q, true, nullptr);
+    const NewtonSmem lean = newton_smem(c->N, c->m, c->Q, false, nullptr);
+    if (lean.bytes > budget) {
+        return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for one CTA");
+    }
+    c->h_in_smem = full.bytes <= budget;
+    c->sm = c->h_in_smem ? full : lean;
+  }
+  c->newton_smem = c->sm.bytes;
+  {
+    // persistent grid: resident CTAs per SM (occupancy API) times the SM count; on the mixed path
+    // the CTAs of one SM must also share its 512 tensor-memory columns
+    int bps = 0;
+    e = prepare_newton(c->entk, c->phys, c->m, c->newton_smem, c->h_in_smem, c->mixed, &bps);
+    if (e == cudaSuccess) e = prepare_update1d(c->phys, c->m, c->Q);
+    if (e != cudaSuccess || bps < 1) {
+        return fail(nullptr, IPM_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
+    }
+    if (c->mixed) bps = std::min(bps, 512 / c->mx.tmem_cols);
+    c->newton_grid = std::max(1, std::min(c->n_interior, bps * prop.multiProcessorCount));
+  }
+  c->hwork_stride = c->h_in_smem ? 0 : packed_aug_count(c->NM);
+  c->update_grid = std::min(c->n_interior, 65535);
+  return IPM_OK;
+}
+
+// Device bytes ipm_init allocates for a planned context.
+static size_t ctx_footprint(const ipm_ctx* c) {
+  const size_t Q = c->Q, N = c->N, nc = c->n_cells, NM = c->NM;
+  size_t b = 2 * Q * N * 8 + Q * 8 + Q * c->tab.p * 8 + (N * (N + 1) / 2) * 4;   // tables
+  b += 2 * nc * NM * 8 + nc * c->m * Q * 8 + nc * 8 + 3 * nc * 4 + sizeof(StepScalars);
+  if (!c->h_in_smem) b += (size_t)c->newton_grid * c->hwork_stride * 8;
+  if (c->mixed) b += N * Q * 4 + (size_t)c->mx.chunks * c->mx.b_chunk_bytes;
+  return b;
+}
+
 extern "C" {
 
 void ipm_default_options(ipm_options* o) {
@@ -259,6 +360,19 @@ ipm_status ipm_tables(int p, int total_degree, int n_per_dim, int N_cap, int Q_c
   return IPM_OK;
 }
 
+ipm_status ipm_footprint(const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad,
+                         const ipm_entropy* entropy, const ipm_options* options, size_t* bytes) {
+  if (!problem || !basis || !quad || !entropy || !bytes) return fail(nullptr, IPM_EINVAL, "ipm_footprint: NULL argument");
+  ipm_options opt;
+  if (options) opt = *options;
+  else ipm_default_options(&opt);
+  ipm_ctx c;
+  const ipm_status st = plan_ctx(&c, problem, basis, quad, entropy, opt);
+  if (st != IPM_OK) return st;
+  *bytes = ctx_footprint(&c);
+  return IPM_OK;
+}
+
 ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad,
                     const ipm_entropy* entropy, const ipm_options* options, ipm_ctx** out) {
   if (!problem || !basis || !quad || !entropy || !out) return fail(nullptr, IPM_EINVAL, "ipm_init: NULL argument");
@@ -266,101 +380,16 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   ipm_options opt;
   if (options) opt = *options;
   else ipm_default_options(&opt);
-  if (basis->p < 1 || basis->p > 3 || basis->total_degree < 0 || quad->n_per_dim < 1)
-    return fail(nullptr, IPM_EINVAL, "ipm_init: basis needs 1 <= p <= 3, M >= 0, n_per_dim >= 1");
-  if (problem->kind != IPM_BURGERS_1D && problem->kind != IPM_EULER_1D)
-    return fail(nullptr, IPM_EINVAL, "ipm_init: only 1-D problems are built in this version");
-  if (problem->nx < 1 || !(problem->x_hi > problem->x_lo) || !(problem->cfl > 0))
-    return fail(nullptr, IPM_EINVAL, "ipm_init: bad mesh or cfl");
-  if ((problem->bc_left == IPM_BC_PERIODIC) != (problem->bc_right == IPM_BC_PERIODIC))
-    return fail(nullptr, IPM_EINVAL, "ipm_init: periodic must be set on both ends");
-  if (opt.precision != IPM_PREC_FP64 && opt.precision != IPM_PREC_MIXED)
-    return fail(nullptr, IPM_EINVAL, "ipm_init: unknown precision");
 
   ipm_ctx* c = new ipm_ctx();
-  c->prob = *problem;
-  c->basis = *basis;
-  c->quad = *quad;
-  c->ent = *entropy;
-  c->opt = opt;
-  c->m = problem->kind == IPM_BURGERS_1D ? 1 : 3;
-  c->phys = problem->kind == IPM_BURGERS_1D ? PHYS_BURGERS : PHYS_EULER1D;
-  c->entk = entropy->kind == IPM_ENTROPY_QUADRATIC ? ENT_QUADRATIC
-                                                     : (entropy->kind == IPM_ENTROPY_BOUNDED_BARRIER ? ENT_BARRIER : ENT_EULER);
-  const bool ent_ok = c->entk == ENT_QUADRATIC || (c->entk == ENT_BARRIER && c->phys == PHYS_BURGERS) ||
-                      (c->entk == ENT_EULER && c->phys != PHYS_BURGERS);
-  if (!ent_ok) {
-    delete c;
-    return fail(nullptr, IPM_EINVAL, "ipm_init: entropy does not match the problem");
-  }
-  if (c->entk == ENT_BARRIER && !(entropy->u_plus > entropy->u_minus)) {
-    delete c;
-    return fail(nullptr, IPM_EINVAL, "ipm_init: barrier needs u_plus > u_minus");
-  }
-  build_tables(basis->p, basis->total_degree, quad->n_per_dim, c->tab);
-  c->N = c->tab.N;
-  c->Q = c->tab.Q;
-  c->NM = c->N * c->m;
-  c->n_interior = problem->nx;
-  c->n_cells = problem->nx + 2;
-  c->dx = (problem->x_hi - problem->x_lo) / problem->nx;
-  if (c->N > 65535) {
-    delete c;
-    return fail(nullptr, IPM_EINVAL, "ipm_init: too many moments");
-  }
-
-  cudaError_t e = cudaGetDevice(&c->device);
-  if (e != cudaSuccess) {
-    delete c;
-    return fail(nullptr, IPM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  }
-  cudaDeviceProp prop;
-  e = cudaGetDeviceProperties(&prop, c->device);
-  if (e != cudaSuccess) {
-    delete c;
-    return fail(nullptr, IPM_ECUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
-  }
-  // launch configuration of the Newton kernel: packed H in shared memory when it fits
-  const size_t budget = (size_t)prop.sharedMemPerBlockOptin;
-  c->mixed = opt.precision == IPM_PREC_MIXED;
-  if (c->mixed) {
-    c->h_in_smem = true;
-    c->mx = mixed_layout(c->N, c->m, c->Q, budget, true);
-    if (!c->mx.ok) {
-      c->h_in_smem = false;
-      c->mx = mixed_layout(c->N, c->m, c->Q, budget, false);
-    }
-    if (!c->mx.ok) {
-      delete c;
-      return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for the mixed-precision Newton kernel");
-    }
-    c->sm = newton_smem(c->N, c->m, c->Q, c->h_in_smem, &c->mx);
-  } else {
-    const NewtonSmem full = newton_smem(c->N, c->m, c->Q, true, nullptr);
-    const NewtonSmem lean = newton_smem(c->N, c->m, c->Q, false, nullptr);
-    if (lean.bytes > budget) {
-      delete c;
-      return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for one CTA");
-    }
-    c->h_in_smem = full.bytes <= budget;
-    c->sm = c->h_in_smem ? full : lean;
-  }
-  c->newton_smem = c->sm.bytes;
   {
-    // persistent grid: resident CTAs per SM (occupancy API) times the SM count; on the mixed path
-    // the CTAs of one SM must also share its 512 tensor-memory columns
-    int bps = 0;
-    e = prepare_newton(c->entk, c->phys, c->m, c->newton_smem, c->h_in_smem, c->mixed, &bps);
-    if (e == cudaSuccess) e = prepare_update1d(c->phys, c->m, c->Q);
-    if (e != cudaSuccess || bps < 1) {
+    const ipm_status ps = plan_ctx(c, problem, basis, quad, entropy, opt);
+    if (ps != IPM_OK) {
       delete c;
-      return fail(nullptr, IPM_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
+      return ps;
     }
-    if (c->mixed) bps = std::min(bps, 512 / c->mx.tmem_cols);
-    c->newton_grid = std::max(1, std::min(c->n_interior, bps * prop.multiProcessorCount));
   }
-  c->hwork_stride = c->h_in_smem ? 0 : packed_aug_count(c->NM);
-  c->update_grid = std::min(c->n_interior, 65535);
+  cudaError_t e = cudaSuccess;
 
   ipm_status st = IPM_OK;
   auto CK = [&](cudaError_t err, const char* what) {

@@ -39,6 +39,24 @@ struct NewtonSmem {
   size_t bytes = 0;
 };
 
+// Largest dynamic shared memory a kernel of this library may be launched with on the current
+// device (the opt-in maximum). cudaFuncAttributeMaxDynamicSharedMemorySize is a property of the
+// kernel function shared by every context and thread, so it is only ever set to this one value:
+// a context with a smaller need can never lower the limit under another context's launches.
+int max_dynamic_smem();
+
+// Raise kernel k's dynamic shared-memory limit to the most it can have next to its static shared
+// memory (the same value from every caller); fails with cudaErrorInvalidValue if `need` bytes do not fit.
+template <typename K>
+cudaError_t raise_smem_limit(K k, size_t need) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k);
+  if (e != cudaSuccess) return e;
+  const int limit = max_dynamic_smem() - (int)fa.sharedSizeBytes;
+  if ((long long)need > (long long)limit) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+}
+
 // kernel launchers (newton.cu, update.cu)
 NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* mx);
 MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem);

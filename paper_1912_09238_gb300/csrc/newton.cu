@@ -751,6 +751,13 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
 
 int newton_threads() { return NT; }
 
+int max_dynamic_smem() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  return v;
+}
+
 static size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
 
 NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* mx) {
@@ -808,7 +815,7 @@ static cudaError_t launch_t(const NewtonArgs* a, int grid, size_t smem, bool h_i
                             int* blocks_per_sm) {
   auto k = h_in_smem ? k_newton<ENT, PHYS, M, true, MIXED> : k_newton<ENT, PHYS, M, false, MIXED>;
   if (prepare) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, NT, smem);
   }

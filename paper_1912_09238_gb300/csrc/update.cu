@@ -134,10 +134,8 @@ __global__ void __launch_bounds__(UT) k_update1d(Update1DArgs a) {
 
 cudaError_t prepare_update1d(int phys, int m, int Q) {
   const int smem = (int)((size_t)m * Q * sizeof(double));
-  if (phys == PHYS_BURGERS && m == 1)
-    return cudaFuncSetAttribute(k_update1d<PHYS_BURGERS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (phys == PHYS_EULER1D && m == 3)
-    return cudaFuncSetAttribute(k_update1d<PHYS_EULER1D, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (phys == PHYS_BURGERS && m == 1) return raise_smem_limit(k_update1d<PHYS_BURGERS, 1>, smem);
+  if (phys == PHYS_EULER1D && m == 3) return raise_smem_limit(k_update1d<PHYS_EULER1D, 3>, smem);
   return cudaErrorInvalidValue;
 }
 
@@ -274,7 +272,10 @@ cudaError_t launch_init1d(int ent, int m, const Tables& tab, const EntParams& en
   const int grid = n_cells < 4096 ? n_cells : 4096;
 #define IPM_INIT_CASE(E, MM)                                                                              \
   if (ent == E && m == MM) {                                                                              \
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_init1d<E, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (smem > 48 * 1024) {                                                                               \
+      const cudaError_t e_ = raise_smem_limit(k_init1d<E, MM>, smem);                                     \
+      if (e_ != cudaSuccess) return e_;                                                                   \
+    }                                                                                                     \
     k_init1d<E, MM><<<grid, UT, smem, s>>>(a);                                                            \
     return cudaGetLastError();                                                                            \
   }

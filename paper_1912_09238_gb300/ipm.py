@@ -61,6 +61,17 @@ class ipm_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ipm_request(ctypes.Structure):
+    _fields_ = [("problem", ipm_problem), ("basis", ipm_basis), ("quad", ipm_quadrature), ("entropy", ipm_entropy),
+                ("options", ipm_options), ("max_steps", ctypes.c_int64)]
+
+
+class ipm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("dims", ipm_dims), ("stats", ipm_stats), ("submit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("finish_s", ctypes.c_double), ("footprint_bytes", ctypes.c_size_t),
+                ("error", ctypes.c_char * 192)]
+
+
 class IpmError(RuntimeError):
     def __init__(self, call, status, msg):
         super().__init__(f"{call} -> {STATUS_NAMES.get(status, status)}: {msg}")
@@ -99,6 +110,13 @@ SIGNATURES = [
     ("ipm_dual_solve_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_double, _P(ipm_basis), _P(ipm_quadrature),
                                               _P(ipm_entropy), _P(ipm_options), ctypes.c_int, _vp, _vp, _vp,
                                               _vp, _vp, _vp, _P(ipm_stats)]),
+    ("ipm_footprint", ctypes.c_int, [_P(ipm_problem), _P(ipm_basis), _P(ipm_quadrature), _P(ipm_entropy),
+                                     _P(ipm_options), _P(ctypes.c_size_t)]),
+    ("ipm_server_create", ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, _P(_vp)]),
+    ("ipm_submit", ctypes.c_int, [_vp, _P(ipm_request), _P(ctypes.c_uint64)]),
+    ("ipm_poll", ctypes.c_int, [_vp, ctypes.c_uint64, _P(ipm_result), _dp, ctypes.c_size_t]),
+    ("ipm_server_drain", ctypes.c_int, [_vp, ctypes.c_double]),
+    ("ipm_server_destroy", None, [_vp]),
     ("ipm_tables", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   _P(ctypes.c_int), _dp, _dp, _dp, _P(ctypes.c_int), _P(ctypes.c_int)]),
 ]
@@ -288,3 +306,65 @@ class Context:
         a, b, t = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
         _check("ipm_step_timing", lib().ipm_step_timing(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(t)), self.h)
         return a.value, b.value, t.value
+
+
+def make_request(problem, p, total_degree, n_per_dim, entropy, u_minus=0.0, u_plus=0.0, options=None, max_steps=2 ** 62):
+    r = ipm_request()
+    r.problem = problem
+    r.basis = ipm_basis(p, total_degree)
+    r.quad = ipm_quadrature(n_per_dim)
+    r.entropy = ipm_entropy(ENTROPY[entropy], u_minus, u_plus)
+    r.options = options if options is not None else default_options()
+    r.max_steps = max_steps
+    return r
+
+
+def footprint(req):
+    """Device bytes ipm_init would allocate for the request's problem."""
+    b = ctypes.c_size_t()
+    _check("ipm_footprint", lib().ipm_footprint(ctypes.byref(req.problem), ctypes.byref(req.basis),
+                                                ctypes.byref(req.quad), ctypes.byref(req.entropy),
+                                                ctypes.byref(req.options), ctypes.byref(b)))
+    return b.value
+
+
+class Server:
+    """Continuous-batching request server (wraps ipm_server*)."""
+
+    def __init__(self, mem_cap_bytes=0, max_active=16):
+        h = _vp()
+        _check("ipm_server_create", lib().ipm_server_create(mem_cap_bytes, max_active, ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, req):
+        t = ctypes.c_uint64()
+        _check("ipm_submit", lib().ipm_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket, fetch=True):
+        """None while the request runs; else (ipm_result, moments or None). Fetching releases the ticket."""
+        r = ipm_result()
+        st = lib().ipm_poll(self.h, ticket, ctypes.byref(r), None, 0)
+        if st == 8:
+            return None
+        _check("ipm_poll", st)
+        if not fetch or r.status != 0:
+            return r, None
+        d = r.dims
+        out = np.empty((d.n_cells, d.N, d.m))
+        _check("ipm_poll", lib().ipm_poll(self.h, ticket, None, _dptr(out), out.size))
+        return r, out
+
+    def drain(self, timeout_s=600.0):
+        _check("ipm_server_drain", lib().ipm_server_drain(self.h, timeout_s))
+
+    def close(self):
+        if self.h:
+            lib().ipm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

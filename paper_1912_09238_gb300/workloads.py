@@ -36,3 +36,45 @@ def variant(base: dict, **changes) -> dict:
 def random_dual_perturbation(shape, seed: int, scale: float) -> np.ndarray:
     """Seeded Gaussian perturbation used to build manufactured dual states for round-trip tests."""
     return scale * np.random.default_rng(seed).standard_normal(shape)
+
+
+def serving_requests(n: int, seed: int = 1234, rate_hz: float = 0.0, steps: int = 10,
+                     max_cells: int = 4000, max_degree: int = 6) -> list:
+    """A seeded stream of IPM requests shaped like the serving workload: each request is a 1-D Burgers
+    or 1-D Euler (Sod-family) problem with cells uniform in [200, max_cells], total degree uniform in
+    2..max_degree, 1..3 uniform uncertain dimensions and a tensor Gauss rule of (degree + 1) nodes per
+    dimension, running `steps` time steps. Arrivals are a Poisson process of rate rate_hz (all at t = 0
+    when rate_hz is 0). Returns [(arrival_s, workload dict)].
+
+    Uncertain parameters (affine in xi_d ~ U[-1, 1]): Burgers -- jump position 0.5 + 0.2 xi_1 on
+    [0, 3], left state 12 + 0.5 xi_2, right state 1 + 0.5 xi_3 (inside the barrier bounds 0.5, 13);
+    Euler -- the first p of (rho_L = 1 + 0.1 xi, p_L = 1 + 0.1 xi, interface 0.5 + 0.05 xi)."""
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    for k in range(n):
+        if rate_hz > 0.0:
+            t += float(rng.exponential(1.0 / rate_hz))
+        fam = "burgers1d" if rng.random() < 0.5 else "euler1d"
+        nx = int(rng.integers(200, max_cells + 1))
+        deg = int(rng.integers(2, max_degree + 1))
+        p = int(rng.integers(1, 4))
+        if fam == "burgers1d":
+            d = [0.0, 0.0, 0.0]
+            d[0] = 0.2
+            dl = [0.0, 0.5 if p >= 2 else 0.0, 0.0]
+            dr = [0.0, 0.0, 0.5 if p >= 3 else 0.0]
+            w = variant(BURGERS_1D, name=f"req{k}_burgers", nx=nx, p=p, M=deg, nq=deg + 1, t_end=0.0,
+                        dx0=tuple(d), dleft=(tuple(dl),), dright=(tuple(dr),))
+        else:
+            dl = [[0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]]
+            dx0 = [0.0, 0.0, 0.0]
+            dl[0][0] = 0.1                       # rho_L on xi_1
+            if p >= 2:
+                dl[2][1] = 0.1                   # p_L on xi_2
+            if p >= 3:
+                dx0[2] = 0.05                    # interface on xi_3
+            w = variant(SOD_1D, name=f"req{k}_euler", nx=nx, p=p, M=deg, nq=deg + 1, t_end=0.0,
+                        dx0=tuple(dx0), dleft=tuple(tuple(r) for r in dl))
+        w["steps"] = steps
+        out.append((t, w))
+    return out
