@@ -30,6 +30,9 @@ METRIC = "IPM cell-steps/s (mixed+batched vs FP64 GPU at equal error); p50/p99 l
 UNIT = "cell-steps/s"
 FP64_PEAK_TFLOPS = 1.25      # nominal dense FP64 of a GB300 (probe: 1.19 measured with FMA chains)
 KERNELS_PER_STEP = 4         # k_order, k_newton, k_update1d, k_finalize (one CUDA graph per step)
+# dram__bytes_read.sum + dram__bytes_write.sum of one mixed-path k_newton launch on this workload,
+# from an ncu capture of the current kernel (a warm step); None for the FP64 kernel (no capture yet)
+NEWTON_TRAFFIC_BYTES = {"mixed": 6.02e6, "fp64": None}
 L2_FLUSH_BYTES = 512 << 20   # > 4x the 126 MiB L2
 WINDOW = dict(nx=200, x_lo=0.45, x_hi=0.55)   # same dx as the 2000-cell mesh, around the interface
 
@@ -230,7 +233,9 @@ def run_gpu(args):
                 "unit": "TFLOP/s", "frac": round(main["fp64_tflops"] / FP64_PEAK_TFLOPS, 4),
                 "peak_source": "nominal GB300 dense FP64 (fallback table; no FP64 figure in the measured peaks); "
                                "an FMA-chain probe measured 1.19 TFLOP/s",
-                "traffic": None, "newton_ms_mean": round(main["newton_ms_mean"], 4),
+                "traffic": NEWTON_TRAFFIC_BYTES[precision],
+                "algorithmic_bytes_per_launch": 2 * 8 * d.n_cells * d.N * d.m,
+                "newton_ms_mean": round(main["newton_ms_mean"], 4),
                 "newton_share_of_step": round(main["newton_share_of_step"], 4),
                 "algorithmic_fp64_flops_per_launch": round(main["fp64_flops_per_launch"]),
                 "newton_iters_per_step": round(main["newton_iters_per_step"], 1)}
