@@ -11,7 +11,8 @@ its dual loop over j = 0..nx+1 and its update over j = 1..nx).
   count depends on this choice.
 * Moment update c (Eq. momentIterationFunction, quadrature form Eq. momentUpQuadrature):
   u_j^{n+1} = sum_k w_k [u_k^(j) - dt/dx (g(u_k^(j), u_k^(j+1)) - g(u_k^(j-1), u_k^(j)))] phi(xi_k)
-  with u_k^(j) = u_s(lambda_j^T phi(xi_k)) and g the Lax-Friedrichs flux.
+  with u_k^(j) = u_s(lambda_j^T phi(xi_k)) and g the Lax-Friedrichs flux (or, for comparisons with
+  the 2-D scheme, the local Lax-Friedrichs flux of physics.rusanov).
 * Time step (not fixed by the paper beyond "CFL"): dt = CFL dx / max_{j,k} speed(u_k^(j)) over all
   cells including ghosts, evaluated at the freshly solved duals; the last step is clipped to t_end.
 * Boundary conditions, applied to the initial state and after each update: outflow copies the
@@ -32,7 +33,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import dual as dualmod
-from .physics import lax_friedrichs
+from .physics import lax_friedrichs, rusanov
 
 
 @dataclass
@@ -60,6 +61,7 @@ class Problem1D:
     cfl: float = 0.5
     t_end: float = 0.0
     newton: dualmod.NewtonOptions = field(default_factory=dualmod.NewtonOptions)
+    flux: str = "lf"              # "lf": global Lax-Friedrichs (App. A); "rusanov": local LF (the 2-D flux)
 
     @property
     def dx(self):
@@ -141,7 +143,10 @@ def time_step(prob: Problem1D, U: np.ndarray, t: float) -> float:
 def moment_update(prob: Problem1D, lam: np.ndarray, dt: float) -> np.ndarray:
     """c(lambda_{j-1}, lambda_j, lambda_{j+1}) for j = 1..nx (Eq. momentUpQuadrature): (nx, N, m)."""
     U = nodal_states(prob, lam)                                  # (nx+2, Q, m)
-    G = lax_friedrichs(prob.phys, U[:-1], U[1:], prob.dx, dt)   # faces j+1/2, j = 0..nx: (nx+1, Q, m)
+    if prob.flux == "rusanov":
+        G = rusanov(prob.phys, U[:-1], U[1:], np.array([1.0]))
+    else:
+        G = lax_friedrichs(prob.phys, U[:-1], U[1:], prob.dx, dt)   # faces j+1/2, j = 0..nx: (nx+1, Q, m)
     inner = U[1:-1] - (dt / prob.dx) * (G[1:] - G[:-1])
     return prob.space.project(inner)
 
