@@ -65,11 +65,28 @@ typedef enum { IPM_BURGERS_1D = 0, IPM_EULER_1D = 1, IPM_EULER_2D = 2 } ipm_prob
 typedef enum {
   IPM_BC_OUTFLOW = 0,    /* ghost copies its interior neighbour (moments and duals) */
   IPM_BC_PERIODIC = 1,   /* ghost copies the opposite interior cell */
-  IPM_BC_DIRICHLET = 2   /* ghost keeps its initial state; its duals are converged once at init */
+  IPM_BC_DIRICHLET = 2,  /* ghost keeps its initial state; its duals are converged once at init */
+  IPM_BC_SLIP_WALL = 3   /* 2-D only: wall; the outside state is the cell's own with the momentum
+                            reflected about the face (Sec. 7 reflecting walls) */
 } ipm_bc;
 
+/* 2-D meshes (structured quadrilaterals, nx x ny interior cells, one ghost layer). */
 typedef enum {
-  IPM_IC_RIEMANN = 0     /* one jump at x0(xi); left/right states and x0 affine in xi */
+  IPM_MESH_CARTESIAN = 0,  /* [x_lo, x_hi] x [y_lo, y_hi], uniform */
+  IPM_MESH_RAMP = 1        /* x in [x_lo, x_hi]; lower wall y_b(x) = y_lo, rising at ramp_deg degrees from
+                              x = ramp_x0; top y_hi; rows mapped linearly y = y_b + (y_hi - y_b) eta */
+} ipm_mesh_kind;
+
+typedef enum {
+  IPM_IC_RIEMANN = 0,    /* one jump at x0(xi); left/right primitive states affine in xi. In 2-D the jump
+                            is at the fixed x = ic_x0, uniform in y, primitives (rho, v1, v2, p) */
+  IPM_IC_FREESTREAM = 1, /* 2-D: uniform state; ic_param = (rho, p, Mach, flow angle in degrees), Mach and
+                            angle affine in xi (ic_dparam[2], ic_dparam[3]); v = Mach c (cos, sin) */
+  IPM_IC_SHEAR = 2       /* 2-D: band |y - (y_lo+y_hi)/2| < w(xi) with ic_left = (rho, v1, -, p) inside and
+                            ic_right = (rho, v1, -, -) outside (pressure ic_left[3] everywhere), transverse
+                            velocity v2 = A(xi) sin(k (x + phase(xi))); ic_param = (A, phase, w, k) with
+                            ic_dparam rows their xi-derivatives. The band is averaged exactly over each cell's
+                            y-extent; v2 is taken at the cell centre's x */
 } ipm_ic_kind;
 
 typedef enum {
@@ -85,7 +102,11 @@ typedef enum {
 } ipm_precision;
 
 /* Problem description. Primitive states are (u) for Burgers and (rho, v_1[, v_2], p) for Euler;
- * every parameter X of the initial data is X + sum_d dX[d] * xi_d with xi_d ~ U[-1, 1]. */
+ * every parameter X of the initial data is X + sum_d dX[d] * xi_d with xi_d ~ U[-1, 1].
+ * 2-D Euler (Sec. 7): cells [j][i] with ghosts, cell index (j+1)*(nx+2) + (i+1) for interior i < nx,
+ * j < ny; the moment update sums local Lax-Friedrichs (Rusanov) fluxes over the four faces of each
+ * cell (face normals and lengths of the mapped mesh), dt = cfl * h / max speed with h the smallest
+ * cell area over its longest face. */
 typedef struct {
   int kind;                 /* ipm_problem_kind */
   int nx, ny;               /* interior cells (ny = 1 for 1-D problems) */
@@ -98,6 +119,12 @@ typedef struct {
   double ic_x0, ic_dx0[3];
   double ic_left[4], ic_dleft[4][3];
   double ic_right[4], ic_dright[4][3];
+  /* 2-D problems (kind IPM_EULER_2D); ignored in 1-D */
+  double y_lo, y_hi;        /* y range (IPM_MESH_RAMP: wall baseline and top) */
+  int bc_bottom, bc_top;    /* ipm_bc of the lower and upper sides (bc_left / bc_right: x sides) */
+  int mesh_kind;            /* ipm_mesh_kind */
+  double ramp_x0, ramp_deg; /* IPM_MESH_RAMP geometry */
+  double ic_param[4], ic_dparam[4][3];
 } ipm_problem;
 
 typedef struct {

@@ -25,6 +25,9 @@ struct ipm_ctx {
   int m = 0, N = 0, Q = 0, NM = 0, n_cells = 0, n_interior = 0;
   int phys = 0, entk = 0;
   double dx = 0.0;
+  bool is2d = false;
+  Mesh2DHost mesh2d;
+  double *d_area = nullptr, *d_xf = nullptr, *d_yf = nullptr;
   int device = 0;
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
@@ -120,7 +123,7 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.cell_list = nullptr;
   a.n_work = c->n_interior;
   a.nx = c->prob.nx;
-  a.gy = 0;
+  a.gy = c->is2d ? 1 : 0;
   a.one_step = one_step;
   a.tau = c->opt.newton_tol;
   a.armijo_c = c->opt.armijo_c;
@@ -162,10 +165,35 @@ static Update1DArgs update_args(const ipm_ctx* c, double dt_override, bool resid
   return u;
 }
 
+static Update2DArgs update2d_args(const ipm_ctx* c, double dt_override, bool resid, bool clip) {
+  Update2DArgs u;
+  u.tab = dev_tables(c);
+  u.mesh.area = c->d_area;
+  u.mesh.xf = c->d_xf;
+  u.mesh.yf = c->d_yf;
+  u.mesh.nx = c->prob.nx;
+  u.mesh.ny = c->prob.ny;
+  u.mesh.h_min = c->mesh2d.h_min;
+  u.uhat = c->d_uhat;
+  u.unode = c->d_unode;
+  u.cell_resid = resid ? c->d_cell_resid : nullptr;
+  u.sc = c->d_sc;
+  u.bc[0] = c->prob.bc_left;
+  u.bc[1] = c->prob.bc_right;
+  u.bc[2] = c->prob.bc_bottom;
+  u.bc[3] = c->prob.bc_top;
+  u.cfl = c->prob.cfl;
+  u.t_end = c->prob.t_end;
+  u.gamma = c->prob.gamma;
+  u.dt_override = dt_override;
+  u.clip = clip ? 1 : 0;
+  return u;
+}
+
 // enqueue: queue reset, Newton over the interior
 static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = launch_order(c->d_iters, c->n_interior, c->prob.nx, 0, c->d_order, s);
+  if (e == cudaSuccess) e = launch_order(c->d_iters, c->n_interior, c->prob.nx, c->is2d ? 1 : 0, c->d_order, s);
   if (e != cudaSuccess) return e;
   NewtonArgs a = newton_args(c, one_step);
   a.cell_list = c->d_order;
@@ -178,11 +206,16 @@ static cudaError_t enqueue_step(ipm_ctx* c, int one_step, cudaStream_t s) {
   if (e == cudaSuccess) e = enqueue_newton(c, one_step, s);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal);
   if (e != cudaSuccess) return e;
-  Update1DArgs u = update_args(c, 0.0, true);
-  e = launch_update1d(c->phys, c->m, u, c->update_grid, s);
+  if (c->is2d) {
+    e = launch_update2d(update2d_args(c, 0.0, true, one_step == 0), c->update_grid, s);
+  } else {
+    Update1DArgs u = update_args(c, 0.0, true);
+    e = launch_update1d(c->phys, c->m, u, c->update_grid, s);
+  }
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal);
-  if (e == cudaSuccess)
-    e = launch_finalize(c->d_sc, c->d_iters, c->d_status, c->d_cell_resid, c->n_cells, 1, c->n_interior, 1, s);
+  // 2-D interior cells are not contiguous: reduce over every cell (ghost counters are kept at zero)
+  const int first = c->is2d ? 0 : 1, count = c->is2d ? c->n_cells : c->n_interior;
+  if (e == cudaSuccess) e = launch_finalize(c->d_sc, c->d_iters, c->d_status, c->d_cell_resid, c->n_cells, first, count, 1, s);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal);
   return e;
 }
@@ -211,7 +244,7 @@ static void free_ctx(ipm_ctx* c) {
   if (c->oneshot_exec) cudaGraphExecDestroy(c->oneshot_exec);
   void* ptrs[] = {c->d_Phi, c->d_PhiT, c->d_w, c->d_nodes, c->d_pairs, c->d_uhat, c->d_lam, c->d_unode,
                   c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc,
-                  c->d_phiT32, c->d_phi_img, c->d_order};
+                  c->d_phiT32, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -231,8 +264,27 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
                            const ipm_entropy* entropy, const ipm_options& opt) {
   if (basis->p < 1 || basis->p > 3 || basis->total_degree < 0 || quad->n_per_dim < 1)
     return fail(nullptr, IPM_EINVAL, "ipm_init: basis needs 1 <= p <= 3, M >= 0, n_per_dim >= 1");
-  if (problem->kind != IPM_BURGERS_1D && problem->kind != IPM_EULER_1D)
-    return fail(nullptr, IPM_EINVAL, "ipm_init: only 1-D problems are built in this version");
+  if (problem->kind != IPM_BURGERS_1D && problem->kind != IPM_EULER_1D && problem->kind != IPM_EULER_2D)
+    return fail(nullptr, IPM_EINVAL, "ipm_init: unknown problem kind");
+  if (problem->kind == IPM_EULER_2D) {
+    if (problem->ny < 1 || !(problem->y_hi > problem->y_lo))
+      return fail(nullptr, IPM_EINVAL, "ipm_init: 2-D mesh needs ny >= 1 and y_hi > y_lo");
+    if ((problem->bc_bottom == IPM_BC_PERIODIC) != (problem->bc_top == IPM_BC_PERIODIC))
+      return fail(nullptr, IPM_EINVAL, "ipm_init: periodic must be set on both the bottom and the top");
+    const int sides[4] = {problem->bc_left, problem->bc_right, problem->bc_bottom, problem->bc_top};
+    for (int k = 0; k < 4; ++k)
+      if (sides[k] < IPM_BC_OUTFLOW || sides[k] > IPM_BC_SLIP_WALL) return fail(nullptr, IPM_EINVAL, "ipm_init: bad side");
+    if (problem->mesh_kind != IPM_MESH_CARTESIAN && problem->mesh_kind != IPM_MESH_RAMP)
+      return fail(nullptr, IPM_EINVAL, "ipm_init: unknown mesh kind");
+    if (problem->mesh_kind == IPM_MESH_RAMP && !(std::fabs(problem->ramp_deg) < 60.0))
+      return fail(nullptr, IPM_EINVAL, "ipm_init: ramp angle must be below 60 degrees");
+    if (problem->ic_kind != IPM_IC_RIEMANN && problem->ic_kind != IPM_IC_FREESTREAM && problem->ic_kind != IPM_IC_SHEAR)
+      return fail(nullptr, IPM_EINVAL, "ipm_init: unknown initial data");
+    if (problem->ic_kind != IPM_IC_FREESTREAM && problem->mesh_kind != IPM_MESH_CARTESIAN)
+      return fail(nullptr, IPM_EINVAL, "ipm_init: Riemann and shear data need a Cartesian mesh");
+  } else if (problem->bc_left == IPM_BC_SLIP_WALL || problem->bc_right == IPM_BC_SLIP_WALL) {
+    return fail(nullptr, IPM_EINVAL, "ipm_init: slip walls are 2-D only");
+  }
   if (problem->nx < 1 || !(problem->x_hi > problem->x_lo) || !(problem->cfl > 0))
     return fail(nullptr, IPM_EINVAL, "ipm_init: bad mesh or cfl");
   if ((problem->bc_left == IPM_BC_PERIODIC) != (problem->bc_right == IPM_BC_PERIODIC))
@@ -244,8 +296,9 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   c->quad = *quad;
   c->ent = *entropy;
   c->opt = opt;
-  c->m = problem->kind == IPM_BURGERS_1D ? 1 : 3;
-  c->phys = problem->kind == IPM_BURGERS_1D ? PHYS_BURGERS : PHYS_EULER1D;
+  c->is2d = problem->kind == IPM_EULER_2D;
+  c->m = problem->kind == IPM_BURGERS_1D ? 1 : (c->is2d ? 4 : 3);
+  c->phys = problem->kind == IPM_BURGERS_1D ? PHYS_BURGERS : (c->is2d ? PHYS_EULER2D : PHYS_EULER1D);
   c->entk = entropy->kind == IPM_ENTROPY_QUADRATIC ? ENT_QUADRATIC
                                                      : (entropy->kind == IPM_ENTROPY_BOUNDED_BARRIER ? ENT_BARRIER : ENT_EULER);
   const bool ent_ok = c->entk == ENT_QUADRATIC || (c->entk == ENT_BARRIER && c->phys == PHYS_BURGERS) ||
@@ -260,9 +313,10 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   c->N = c->tab.N;
   c->Q = c->tab.Q;
   c->NM = c->N * c->m;
-  c->n_interior = problem->nx;
-  c->n_cells = problem->nx + 2;
+  c->n_interior = c->is2d ? problem->nx * problem->ny : problem->nx;
+  c->n_cells = c->is2d ? (problem->nx + 2) * (problem->ny + 2) : problem->nx + 2;
   c->dx = (problem->x_hi - problem->x_lo) / problem->nx;
+  if (c->is2d) build_mesh2d(*problem, c->mesh2d);
   if (c->N > 65535) {
     return fail(nullptr, IPM_EINVAL, "ipm_init: too many moments");
   }
@@ -305,7 +359,7 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     // the CTAs of one SM must also share its 512 tensor-memory columns
     int bps = 0;
     e = prepare_newton(c->entk, c->phys, c->m, c->newton_smem, c->h_in_smem, c->mixed, &bps);
-    if (e == cudaSuccess) e = prepare_update1d(c->phys, c->m, c->Q);
+    if (e == cudaSuccess) e = c->is2d ? prepare_update2d(c->Q) : prepare_update1d(c->phys, c->m, c->Q);
     if (e != cudaSuccess || bps < 1) {
         return fail(nullptr, IPM_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
     }
@@ -324,6 +378,7 @@ static size_t ctx_footprint(const ipm_ctx* c) {
   b += 2 * nc * NM * 8 + nc * c->m * Q * 8 + nc * 8 + 3 * nc * 4 + sizeof(StepScalars);
   if (!c->h_in_smem) b += (size_t)c->newton_grid * c->hwork_stride * 8;
   if (c->mixed) b += N * Q * 4 + (size_t)c->mx.chunks * c->mx.b_chunk_bytes;
+  if (c->is2d) b += (c->mesh2d.area.size() + c->mesh2d.xf.size() + c->mesh2d.yf.size()) * 8;
   return b;
 }
 
@@ -431,15 +486,36 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   CK(cudaMemsetAsync(c->d_status, 0, (size_t)c->n_cells * sizeof(int), c->stream), "memset status");
   CK(cudaMemsetAsync(c->d_cell_resid, 0, (size_t)c->n_cells * sizeof(double), c->stream), "memset resid");
   CK(cudaMemsetAsync(c->d_unode, 0, (size_t)c->n_cells * c->m * c->Q * sizeof(double), c->stream), "memset unode");
-  // initial data on every cell, then the boundary copies
-  CK(launch_init1d(c->entk, c->m, dev_tables(c), ent_params(c), c->prob, c->d_uhat, c->d_lam, c->n_cells, c->stream),
-     "init kernel");
-  CK(launch_bc_copy1d(c->d_uhat, c->d_lam, problem->nx, c->NM, problem->bc_left, problem->bc_right, c->stream),
-     "bc kernel");
+  // initial data on every cell, then the boundary copies (1-D) or the mesh tables (2-D)
+  if (c->is2d) {
+    CK(upload(&c->d_area, c->mesh2d.area), "upload areas");
+    CK(upload(&c->d_xf, c->mesh2d.xf), "upload x faces");
+    CK(upload(&c->d_yf, c->mesh2d.yf), "upload y faces");
+    if (st == IPM_OK)
+      CK(launch_init2d(c->entk, dev_tables(c), ent_params(c), c->prob, c->d_uhat, c->d_lam, c->stream), "init kernel");
+  } else {
+    CK(launch_init1d(c->entk, c->m, dev_tables(c), ent_params(c), c->prob, c->d_uhat, c->d_lam, c->n_cells, c->stream),
+       "init kernel");
+    CK(launch_bc_copy1d(c->d_uhat, c->d_lam, problem->nx, c->NM, problem->bc_left, problem->bc_right, c->stream),
+       "bc kernel");
+  }
   // Dirichlet ghosts: converge their duals once; their speed stays part of every dt
   std::vector<int> ghosts;
-  if (problem->bc_left == IPM_BC_DIRICHLET) ghosts.push_back(0);
-  if (problem->bc_right == IPM_BC_DIRICHLET) ghosts.push_back(problem->nx + 1);
+  if (c->is2d) {
+    const int nx = problem->nx, ny = problem->ny;
+    auto cell = [&](int i, int j) { return (j + 1) * (nx + 2) + (i + 1); };
+    for (int j = 0; j < ny; ++j) {
+      if (problem->bc_left == IPM_BC_DIRICHLET) ghosts.push_back(cell(-1, j));
+      if (problem->bc_right == IPM_BC_DIRICHLET) ghosts.push_back(cell(nx, j));
+    }
+    for (int i = 0; i < nx; ++i) {
+      if (problem->bc_bottom == IPM_BC_DIRICHLET) ghosts.push_back(cell(i, -1));
+      if (problem->bc_top == IPM_BC_DIRICHLET) ghosts.push_back(cell(i, ny));
+    }
+  } else {
+    if (problem->bc_left == IPM_BC_DIRICHLET) ghosts.push_back(0);
+    if (problem->bc_right == IPM_BC_DIRICHLET) ghosts.push_back(problem->nx + 1);
+  }
   c->n_fixed_ghosts = (int)ghosts.size();
   if (!ghosts.empty()) {
     CK(upload(&c->d_ghost_list, ghosts), "upload ghosts");
@@ -455,14 +531,14 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   if (st == IPM_OK) {
     // fixed speed = what the ghost solve folded in (0 without Dirichlet ghosts); then reset counters
     StepScalars h;
+    std::vector<int> status(c->n_cells, 0);
     CK(cudaMemcpyAsync(&h, c->d_sc, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->stream), "read scalars");
+    CK(cudaMemcpyAsync(status.data(), c->d_status, status.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+       "read ghost status");
     CK(cudaStreamSynchronize(c->stream), "init sync");
     if (st == IPM_OK) {
-      int gstat[2] = {0, 0};
-      for (size_t k = 0; k < ghosts.size(); ++k)
-        cudaMemcpy(&gstat[k], c->d_status + ghosts[k], sizeof(int), cudaMemcpyDeviceToHost);
-      for (size_t k = 0; k < ghosts.size(); ++k)
-        if (gstat[k] != 0) st = fail(nullptr, IPM_EINVAL, "ipm_init: Dirichlet ghost dual solve failed");
+      for (int g : ghosts)
+        if (status[g] != 0) st = fail(nullptr, IPM_EINVAL, "ipm_init: Dirichlet ghost dual solve failed");
       h.fixed_smax_bits = h.smax_bits;
       h.work_counter = 0;
       h.update_counter = 0;
@@ -470,6 +546,8 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
       h.dt = 0.0;
       h.steps = 0;
       CK(cudaMemcpy(c->d_sc, &h, sizeof(StepScalars), cudaMemcpyHostToDevice), "write scalars");
+      // per-cell counters start from zero (the step reductions of 2-D meshes include the ghosts)
+      CK(cudaMemset(c->d_iters, 0, (size_t)c->n_cells * sizeof(int)), "reset iters");
     }
   }
   if (st == IPM_OK) st = build_graph(c, 0, &c->step_exec);
@@ -569,7 +647,8 @@ ipm_status ipm_sync_stats(ipm_ctx* c, ipm_stats* s) {
 ipm_status ipm_dual_solve(ipm_ctx* c, ipm_stats* s) {
   if (!c) return IPM_EINVAL;
   IPM_CK(c, enqueue_newton(c, 0, c->stream));
-  IPM_CK(c, launch_finalize(c->d_sc, c->d_iters, c->d_status, nullptr, c->n_cells, 1, c->n_interior, 0, c->stream));
+  IPM_CK(c, launch_finalize(c->d_sc, c->d_iters, c->d_status, nullptr, c->n_cells, c->is2d ? 0 : 1,
+                            c->is2d ? c->n_cells : c->n_interior, 0, c->stream));
   if (s) return ipm_sync_stats(c, s);
   return IPM_OK;
 }
@@ -597,8 +676,12 @@ ipm_status ipm_assemble_hessian(ipm_ctx* c, double* h, size_t count) {
 ipm_status ipm_update(ipm_ctx* c, double dt) {
   if (!c) return IPM_EINVAL;
   if (!(dt > 0.0)) return fail(c, IPM_EINVAL, "ipm_update: dt must be positive");
-  Update1DArgs u = update_args(c, dt, false);
-  IPM_CK(c, launch_update1d(c->phys, c->m, u, c->update_grid, c->stream));
+  if (c->is2d) {
+    IPM_CK(c, launch_update2d(update2d_args(c, dt, false, false), c->update_grid, c->stream));
+  } else {
+    Update1DArgs u = update_args(c, dt, false);
+    IPM_CK(c, launch_update1d(c->phys, c->m, u, c->update_grid, c->stream));
+  }
   IPM_CK(c, cudaStreamSynchronize(c->stream));
   return IPM_OK;
 }

@@ -292,6 +292,29 @@ struct Update1DArgs {
   double dt_override;    // > 0: use this dt instead of the CFL rule
 };
 
+// 2-D structured mesh on the device: cell areas [ny][nx]; x-faces [ny][nx+1] and y-faces [ny+1][nx]
+// as (n_x, n_y, length) with the unit normal pointing to increasing i (x-faces) or j (y-faces).
+struct Mesh2DDev {
+  const double* area;
+  const double* xf;
+  const double* yf;
+  int nx, ny;
+  double h_min;          // min over cells of area / longest face
+};
+
+struct Update2DArgs {
+  Tables tab;
+  Mesh2DDev mesh;
+  double* uhat;          // [(ny+2)(nx+2)][N][m]
+  const double* unode;   // [(ny+2)(nx+2)][m][Q]
+  double* cell_resid;    // [(ny+2)(nx+2)] area-weighted |change of the density mean|
+  StepScalars* sc;
+  int bc[4];             // left, right, bottom, top (ipm_bc)
+  double cfl, t_end, gamma;
+  double dt_override;    // > 0: use this dt
+  int clip;              // 1: clip the step to t_end
+};
+
 #ifdef __CUDACC__
 // positive doubles order like their bit patterns
 __device__ inline void atomic_max_pos(unsigned long long* addr, double v) {

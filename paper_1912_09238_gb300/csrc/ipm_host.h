@@ -1,5 +1,6 @@
 // ipm_host.h -- host-side internals shared by the translation units of libipm.
 #pragma once
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -21,7 +22,15 @@ struct HostTables {
   std::vector<uint32_t> pairs;  // [N(N+1)/2]
 };
 
+// 2-D mesh tables built on the host (update2d.cu): areas [ny][nx], x-faces [ny][nx+1] and
+// y-faces [ny+1][nx] as (n_x, n_y, length), h = min area / longest face.
+struct Mesh2DHost {
+  std::vector<double> area, xf, yf;
+  double h_min = 0.0;
+};
+
 void set_global_error(const std::string& msg);
+void build_mesh2d(const ipm_problem& pr, Mesh2DHost& m);
 void gauss_legendre_1d(int n, std::vector<double>& x, std::vector<double>& w);
 void build_tables(int p, int M, int nq, HostTables& t);
 
@@ -73,6 +82,10 @@ cudaError_t launch_init1d(int ent, int m, const Tables& tab, const EntParams& en
                           double* uhat, double* lam, int n_cells, cudaStream_t s);
 cudaError_t launch_finalize(StepScalars* sc, const int* iters, const int* status, const double* cell_resid,
                             int n_cells, int first, int count, int advance_time, cudaStream_t s);
+cudaError_t prepare_update2d(int Q);
+cudaError_t launch_update2d(const Update2DArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_init2d(int ent, const Tables& tab, const EntParams& ent_p, const ipm_problem& prob, double* uhat,
+                          double* lam, cudaStream_t s);
 cudaError_t launch_bc_copy1d(double* uhat, double* lam, int nx, int Nm, int bc_left, int bc_right,
                              cudaStream_t s);
 

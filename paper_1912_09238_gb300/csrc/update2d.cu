@@ -1,0 +1,378 @@
+// update2d.cu -- 2-D Euler (Sec. 7): mesh geometry, initial data and the kinetic-flux moment update
+// on structured quadrilateral meshes.
+//
+// Moment update of an interior cell c (Eq. momentIterationFunction in quadrature form, Eq.
+// momentUpQuadrature, with the divergence theorem over the cell's four faces):
+//   u_c^{n+1} = sum_k w_k [u_k^(c) - dt/A_c (L_r g_r - L_l g_l + L_t g_t - L_b g_b)] phi(xi_k),
+// g the local Lax-Friedrichs (Rusanov) flux across a face, node by node:
+//   g(u_a, u_b; n) = (F(u_a).n + F(u_b).n)/2 - a/2 (u_b - u_a),  a = max(|v_a.n| + c_a, |v_b.n| + c_b),
+// with u_a behind and u_b ahead of the face normal (normals point to increasing i or j).
+// Sides: periodic wraps; outflow uses the cell's own nodal state; Dirichlet ghosts keep the nodal
+// states of their duals converged at init; a slip wall reflects the momentum about the face normal.
+// dt = CFL h / s_max (h = min area / longest face, s_max from the Newton kernel's atomic maximum),
+// clipped to t_end on Algorithm-1 steps.
+#include <cmath>
+
+#include "ipm_host.h"
+
+namespace ipm {
+
+constexpr int T2 = 256;
+constexpr int W2 = T2 / 32;
+
+// F(u).n and |v.n| + c for the 2-D Euler system
+__device__ __forceinline__ double euler2d_normal_flux(const double* u, double nx, double ny, double g, double* f) {
+  const double rho = u[0], ir = 1.0 / rho;
+  const double v1 = u[1] * ir, v2 = u[2] * ir;
+  const double p = (g - 1.0) * (u[3] - 0.5 * (u[1] * v1 + u[2] * v2));
+  const double vn = v1 * nx + v2 * ny;
+  f[0] = rho * vn;
+  f[1] = fma(u[1], vn, p * nx);
+  f[2] = fma(u[2], vn, p * ny);
+  f[3] = (u[3] + p) * vn;
+  return fabs(vn) + sqrt(g * p * ir);
+}
+
+// Rusanov flux from a (behind) to b (ahead) across unit normal n
+__device__ __forceinline__ void rusanov2d(const double* ua, const double* ub, double nx, double ny, double g,
+                                          double* out) {
+  double fa[4], fb[4];
+  const double sa = euler2d_normal_flux(ua, nx, ny, g, fa);
+  const double sb = euler2d_normal_flux(ub, nx, ny, g, fb);
+  const double s = fmax(sa, sb);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out[c] = 0.5 * (fa[c] + fb[c]) - 0.5 * s * (ub[c] - ua[c]);
+}
+
+__device__ __forceinline__ void reflect(const double* u, double nx, double ny, double* out) {
+  const double mn = u[1] * nx + u[2] * ny;
+  out[0] = u[0];
+  out[1] = u[1] - 2.0 * mn * nx;
+  out[2] = u[2] - 2.0 * mn * ny;
+  out[3] = u[3];
+}
+
+__device__ __forceinline__ int cell2d(int i, int j, int nx) { return (j + 1) * (nx + 2) + (i + 1); }
+
+// state beyond a boundary face: the neighbour cell index, or -1 for the cell itself (outflow),
+// or -2 for the reflected state (slip wall)
+__device__ __forceinline__ int outside(int bc, int wrap_cell, int ghost_cell) {
+  if (bc == IPM_BC_PERIODIC) return wrap_cell;
+  if (bc == IPM_BC_DIRICHLET) return ghost_cell;
+  if (bc == IPM_BC_SLIP_WALL) return -2;
+  return -1;
+}
+
+__global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
+  extern __shared__ __align__(16) double s_v[];     // [4][Q] w * integrand
+  constexpr int M = 4;
+  const int N = a.tab.N, Q = a.tab.Q, NM = N * M;
+  const int nx = a.mesh.nx, ny = a.mesh.ny;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double dt = a.dt_override;
+  if (!(dt > 0.0)) {
+    const double smax = __longlong_as_double((long long)a.sc->smax_bits);
+    dt = a.cfl * a.mesh.h_min / smax;
+    if (a.clip && a.t_end > 0.0 && a.sc->t + dt > a.t_end) dt = a.t_end - a.sc->t;
+  }
+  if (blockIdx.x == 0 && tid == 0) a.sc->dt = dt > 0.0 ? dt : 0.0;
+  if (!(dt > 0.0)) return;
+  const double* __restrict__ w = a.tab.w;
+  const double* __restrict__ PhiT = a.tab.PhiT;
+  const int MQ = M * Q;
+  const double g = a.gamma;
+
+  for (int cidx = blockIdx.x; cidx < nx * ny; cidx += gridDim.x) {
+    const int i = cidx % nx, j = cidx / nx;
+    const int c = cell2d(i, j, nx);
+    const double area = a.mesh.area[(size_t)j * nx + i];
+    const double* xl = a.mesh.xf + ((size_t)j * (nx + 1) + i) * 3;
+    const double* xr = xl + 3;
+    const double* yb = a.mesh.yf + ((size_t)j * nx + i) * 3;
+    const double* yt = a.mesh.yf + ((size_t)(j + 1) * nx + i) * 3;
+    const int nl = i > 0 ? cell2d(i - 1, j, nx) : outside(a.bc[0], cell2d(nx - 1, j, nx), cell2d(-1, j, nx));
+    const int nr = i < nx - 1 ? cell2d(i + 1, j, nx) : outside(a.bc[1], cell2d(0, j, nx), cell2d(nx, j, nx));
+    const int nb = j > 0 ? cell2d(i, j - 1, nx) : outside(a.bc[2], cell2d(i, ny - 1, nx), cell2d(i, -1, nx));
+    const int nt = j < ny - 1 ? cell2d(i, j + 1, nx) : outside(a.bc[3], cell2d(i, 0, nx), cell2d(i, ny, nx));
+    const double r = dt / area;
+    for (int q = tid; q < Q; q += T2) {
+      double uc[M], un[M], f[M], acc[M];
+      const double* ucg = a.unode + (size_t)c * MQ;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        uc[k] = ucg[k * Q + q];
+        acc[k] = 0.0;
+      }
+      // faces: (neighbour, normal, sign): flux behind->ahead; left/bottom: neighbour behind
+      const int nbr[4] = {nl, nr, nb, nt};
+      const double* fg[4] = {xl, xr, yb, yt};
+#pragma unroll
+      for (int fa = 0; fa < 4; ++fa) {
+        const double nxn = fg[fa][0], nyn = fg[fa][1], L = fg[fa][2];
+        const int o = nbr[fa];
+        if (o >= 0) {
+          const double* ug = a.unode + (size_t)o * MQ;
+#pragma unroll
+          for (int k = 0; k < M; ++k) un[k] = ug[k * Q + q];
+        } else if (o == -1) {
+#pragma unroll
+          for (int k = 0; k < M; ++k) un[k] = uc[k];
+        } else {
+          reflect(uc, nxn, nyn, un);
+        }
+        const bool ahead = (fa & 1) != 0;            // right and top faces: the neighbour is ahead
+        if (ahead) rusanov2d(uc, un, nxn, nyn, g, f);
+        else rusanov2d(un, uc, nxn, nyn, g, f);
+        const double sL = ahead ? L : -L;
+#pragma unroll
+        for (int k = 0; k < M; ++k) acc[k] = fma(sL, f[k], acc[k]);
+      }
+      const double wq = w[q];
+#pragma unroll
+      for (int k = 0; k < M; ++k) s_v[k * Q + q] = wq * fma(-r, acc[k], uc[k]);
+    }
+    __syncthreads();
+    double* out = a.uhat + (size_t)c * NM;
+    const double old00 = out[0];
+    __syncthreads();
+    for (int ii = warp; ii < N; ii += W2) {
+      double s[M];
+#pragma unroll
+      for (int k = 0; k < M; ++k) s[k] = 0.0;
+      for (int q = lane; q < Q; q += 32) {
+        const double ph = PhiT[(size_t)ii * Q + q];
+#pragma unroll
+        for (int k = 0; k < M; ++k) s[k] = fma(ph, s_v[k * Q + q], s[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        const double v = warp_sum(s[k]);
+        if (lane == 0) out[ii * M + k] = v;
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && a.cell_resid) a.cell_resid[c] = area * fabs(out[0] - old00);
+    __syncthreads();
+  }
+}
+
+cudaError_t prepare_update2d(int Q) { return raise_smem_limit(k_update2d, (size_t)4 * Q * sizeof(double)); }
+
+cudaError_t launch_update2d(const Update2DArgs& a, int grid, cudaStream_t s) {
+  k_update2d<<<grid, T2, (size_t)4 * a.tab.Q * sizeof(double), s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Initial data on every cell (ghosts included): nodal cell averages of the 2-D initial data,
+// projected; initial duals = projection of grad s of the nodal averages.
+// ------------------------------------------------------------------------------------------------
+struct Init2DArgs {
+  Tables tab;
+  EntParams ent;
+  int nx, ny, ic_kind;
+  double x_lo, dx, y_lo, dy, gamma;
+  double x0;
+  double left[4], dleft[4][3], right[4], dright[4][3];
+  double param[4], dparam[4][3];
+  double* uhat;
+  double* lam;
+};
+
+__device__ __forceinline__ double affine3(double v0, const double* d, const double* xi, int P) {
+  double v = v0;
+  for (int k = 0; k < P; ++k) v = fma(d[k], xi[k], v);
+  return v;
+}
+
+__device__ __forceinline__ void prim4_to_cons(double rho, double v1, double v2, double p, double g, double* u) {
+  u[0] = rho;
+  u[1] = rho * v1;
+  u[2] = rho * v2;
+  u[3] = p / (g - 1.0) + 0.5 * rho * (v1 * v1 + v2 * v2);
+}
+
+template <int ENT>
+__global__ void __launch_bounds__(T2) k_init2d(Init2DArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  constexpr int M = 4;
+  const int N = a.tab.N, Q = a.tab.Q, P = a.tab.p, NM = N * M;
+  double* s_u = sm;            // [M][Q] w * ubar
+  double* s_e = sm + M * Q;    // [M][Q] w * grad s(ubar)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nx = a.nx, ny = a.ny, n_cells = (nx + 2) * (ny + 2);
+  for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
+    const int ii = c % (nx + 2), jj = c / (nx + 2);              // ghost-inclusive column and row
+    for (int q = tid; q < Q; q += T2) {
+      double xi[3] = {0.0, 0.0, 0.0};
+      for (int d = 0; d < P; ++d) xi[d] = a.tab.nodes[(size_t)q * P + d];
+      double ub[M], ge[M];
+      if (a.ic_kind == IPM_IC_FREESTREAM) {
+        const double rho = a.param[0], p = a.param[1];
+        const double mach = affine3(a.param[2], a.dparam[2], xi, P);
+        const double th = affine3(a.param[3], a.dparam[3], xi, P) * (M_PI / 180.0);
+        const double cs = sqrt(a.gamma * p / rho);
+        prim4_to_cons(rho, mach * cs * cos(th), mach * cs * sin(th), p, a.gamma, ub);
+      } else if (a.ic_kind == IPM_IC_SHEAR) {
+        // ghosts repeat the periodic interior
+        const int iw = ii == 0 ? nx : (ii == nx + 1 ? 1 : ii);
+        const int jw = jj == 0 ? ny : (jj == ny + 1 ? 1 : jj);
+        const double ylo = a.y_lo + (jw - 1) * a.dy, yhi = ylo + a.dy;
+        const double xc = a.x_lo + (iw - 0.5) * a.dx;
+        const double amp = affine3(a.param[0], a.dparam[0], xi, P);
+        const double ph = affine3(a.param[1], a.dparam[1], xi, P);
+        const double hw = affine3(a.param[2], a.dparam[2], xi, P);
+        const double ym = a.y_lo + 0.5 * a.dy * ny;
+        const double f = fmax(fmin(yhi, ym + hw) - fmax(ylo, ym - hw), 0.0) / a.dy;
+        const double v2 = amp * sin(a.param[3] * (xc + ph));
+        const double rin = a.left[0], vin = a.left[1], rout = a.right[0], vout = a.right[1], p = a.left[3];
+        const double rho = f * rin + (1.0 - f) * rout;
+        ub[0] = rho;
+        ub[1] = f * rin * vin + (1.0 - f) * rout * vout;
+        ub[2] = rho * v2;
+        ub[3] = p / (a.gamma - 1.0) + 0.5 * f * rin * (vin * vin + v2 * v2) + 0.5 * (1.0 - f) * rout * (vout * vout + v2 * v2);
+      } else {
+        // x-Riemann: exact cell average in x of the two states
+        double pl[4], pr[4], UL[M], UR[M];
+        for (int v = 0; v < 4; ++v) {
+          pl[v] = affine3(a.left[v], a.dleft[v], xi, P);
+          pr[v] = affine3(a.right[v], a.dright[v], xi, P);
+        }
+        prim4_to_cons(pl[0], pl[1], pl[2], pl[3], a.gamma, UL);
+        prim4_to_cons(pr[0], pr[1], pr[2], pr[3], a.gamma, UR);
+        const double x_left = a.x_lo + (ii - 1) * a.dx;
+        const double frac = fmin(fmax((a.x0 - x_left) / a.dx, 0.0), 1.0);
+#pragma unroll
+        for (int k = 0; k < M; ++k) ub[k] = frac * UL[k] + (1.0 - frac) * UR[k];
+      }
+      entropy_gradient<ENT, M>(ub, a.ent, ge);
+      const double wq = a.tab.w[q];
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        s_u[k * Q + q] = wq * ub[k];
+        s_e[k * Q + q] = wq * ge[k];
+      }
+    }
+    __syncthreads();
+    for (int i = warp; i < N; i += W2) {
+      double au[M], ae[M];
+#pragma unroll
+      for (int k = 0; k < M; ++k) au[k] = ae[k] = 0.0;
+      for (int q = lane; q < Q; q += 32) {
+        const double ph = a.tab.PhiT[(size_t)i * Q + q];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          au[k] = fma(ph, s_u[k * Q + q], au[k]);
+          ae[k] = fma(ph, s_e[k * Q + q], ae[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        const double vu = warp_sum(au[k]), ve = warp_sum(ae[k]);
+        if (lane == 0) {
+          a.uhat[(size_t)c * NM + i * M + k] = vu;
+          a.lam[(size_t)c * NM + i * M + k] = ve;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_init2d(int ent, const Tables& tab, const EntParams& ent_p, const ipm_problem& prob, double* uhat,
+                          double* lam, cudaStream_t s) {
+  Init2DArgs a;
+  a.tab = tab;
+  a.ent = ent_p;
+  a.nx = prob.nx;
+  a.ny = prob.ny;
+  a.ic_kind = prob.ic_kind;
+  a.x_lo = prob.x_lo;
+  a.dx = (prob.x_hi - prob.x_lo) / prob.nx;
+  a.y_lo = prob.y_lo;
+  a.dy = (prob.y_hi - prob.y_lo) / prob.ny;
+  a.gamma = prob.gamma;
+  a.x0 = prob.ic_x0;
+  for (int v = 0; v < 4; ++v) {
+    a.left[v] = prob.ic_left[v];
+    a.right[v] = prob.ic_right[v];
+    a.param[v] = prob.ic_param[v];
+    for (int d = 0; d < 3; ++d) {
+      a.dleft[v][d] = prob.ic_dleft[v][d];
+      a.dright[v][d] = prob.ic_dright[v][d];
+      a.dparam[v][d] = prob.ic_dparam[v][d];
+    }
+  }
+  a.uhat = uhat;
+  a.lam = lam;
+  const int n_cells = (prob.nx + 2) * (prob.ny + 2);
+  const size_t smem = 2 * (size_t)4 * tab.Q * sizeof(double);
+  const int grid = n_cells < 8192 ? n_cells : 8192;
+  if (ent == ENT_EULER) {
+    cudaError_t e = raise_smem_limit(k_init2d<ENT_EULER>, smem);
+    if (e != cudaSuccess) return e;
+    k_init2d<ENT_EULER><<<grid, T2, smem, s>>>(a);
+  } else if (ent == ENT_QUADRATIC) {
+    cudaError_t e = raise_smem_limit(k_init2d<ENT_QUADRATIC>, smem);
+    if (e != cudaSuccess) return e;
+    k_init2d<ENT_QUADRATIC><<<grid, T2, smem, s>>>(a);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Host: vertices of the mesh, cell areas (shoelace), face normals and lengths, h.
+// ------------------------------------------------------------------------------------------------
+void build_mesh2d(const ipm_problem& pr, Mesh2DHost& m) {
+  const int nx = pr.nx, ny = pr.ny;
+  std::vector<double> X((size_t)(nx + 1) * (ny + 1)), Y(X.size());
+  auto V = [&](int i, int j) { return (size_t)i * (ny + 1) + j; };
+  const double tr = std::tan(pr.ramp_deg * M_PI / 180.0);
+  for (int i = 0; i <= nx; ++i) {
+    const double x = pr.x_lo + (pr.x_hi - pr.x_lo) * i / nx;
+    const double yb = pr.mesh_kind == IPM_MESH_RAMP && x > pr.ramp_x0 ? pr.y_lo + (x - pr.ramp_x0) * tr : pr.y_lo;
+    for (int j = 0; j <= ny; ++j) {
+      const double eta = (double)j / ny;
+      X[V(i, j)] = x;
+      Y[V(i, j)] = pr.mesh_kind == IPM_MESH_RAMP ? yb + (pr.y_hi - yb) * eta : pr.y_lo + (pr.y_hi - pr.y_lo) * eta;
+    }
+  }
+  m.area.assign((size_t)nx * ny, 0.0);
+  m.xf.assign((size_t)ny * (nx + 1) * 3, 0.0);
+  m.yf.assign((size_t)(ny + 1) * nx * 3, 0.0);
+  for (int j = 0; j < ny; ++j)
+    for (int f = 0; f <= nx; ++f) {
+      const double dx = X[V(f, j + 1)] - X[V(f, j)], dy = Y[V(f, j + 1)] - Y[V(f, j)];
+      const double L = std::hypot(dx, dy);
+      double* o = &m.xf[((size_t)j * (nx + 1) + f) * 3];
+      o[0] = dy / L;
+      o[1] = -dx / L;
+      o[2] = L;
+    }
+  for (int g = 0; g <= ny; ++g)
+    for (int i = 0; i < nx; ++i) {
+      const double dx = X[V(i + 1, g)] - X[V(i, g)], dy = Y[V(i + 1, g)] - Y[V(i, g)];
+      const double L = std::hypot(dx, dy);
+      double* o = &m.yf[((size_t)g * nx + i) * 3];
+      o[0] = -dy / L;
+      o[1] = dx / L;
+      o[2] = L;
+    }
+  m.h_min = 1e300;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double x[4] = {X[V(i, j)], X[V(i + 1, j)], X[V(i + 1, j + 1)], X[V(i, j + 1)]};
+      const double y[4] = {Y[V(i, j)], Y[V(i + 1, j)], Y[V(i + 1, j + 1)], Y[V(i, j + 1)]};
+      double a = 0.0;
+      for (int k = 0; k < 4; ++k) a += x[k] * y[(k + 1) % 4] - x[(k + 1) % 4] * y[k];
+      a *= 0.5;
+      m.area[(size_t)j * nx + i] = a;
+      const double longest = std::max(std::max(m.xf[((size_t)j * (nx + 1) + i) * 3 + 2], m.xf[((size_t)j * (nx + 1) + i + 1) * 3 + 2]),
+                                      std::max(m.yf[((size_t)j * nx + i) * 3 + 2], m.yf[((size_t)(j + 1) * nx + i) * 3 + 2]));
+      m.h_min = std::min(m.h_min, a / longest);
+    }
+}
+
+}  // namespace ipm

@@ -14,7 +14,9 @@ STATUS_NAMES = {0: "IPM_OK", 1: "IPM_EINVAL", 2: "IPM_ENOMEM", 3: "IPM_ENOCONV",
                 5: "IPM_EINFEASIBLE", 6: "IPM_ELINESEARCH", 7: "IPM_ENONFINITE", 8: "IPM_EAGAIN",
                 9: "IPM_ECUDA", 10: "IPM_ETIMEOUT"}
 PROBLEM = {"burgers1d": 0, "euler1d": 1, "euler2d": 2}
-BC = {"outflow": 0, "periodic": 1, "dirichlet": 2}
+BC = {"outflow": 0, "periodic": 1, "dirichlet": 2, "slip": 3}
+MESH = {"cartesian": 0, "ramp": 1}
+IC = {"riemann": 0, "freestream": 1, "shear": 2}
 ENTROPY = {"quadratic": 0, "barrier": 1, "euler": 2}
 PRECISION = {"fp64": 0, "mixed": 1}
 
@@ -26,7 +28,11 @@ class ipm_problem(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("t_end", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("ic_kind", ctypes.c_int), ("ic_x0", ctypes.c_double), ("ic_dx0", ctypes.c_double * 3),
                 ("ic_left", ctypes.c_double * 4), ("ic_dleft", (ctypes.c_double * 3) * 4),
-                ("ic_right", ctypes.c_double * 4), ("ic_dright", (ctypes.c_double * 3) * 4)]
+                ("ic_right", ctypes.c_double * 4), ("ic_dright", (ctypes.c_double * 3) * 4),
+                ("y_lo", ctypes.c_double), ("y_hi", ctypes.c_double), ("bc_bottom", ctypes.c_int),
+                ("bc_top", ctypes.c_int), ("mesh_kind", ctypes.c_int), ("ramp_x0", ctypes.c_double),
+                ("ramp_deg", ctypes.c_double), ("ic_param", ctypes.c_double * 4),
+                ("ic_dparam", (ctypes.c_double * 3) * 4)]
 
 
 class ipm_basis(ctypes.Structure):
@@ -206,6 +212,25 @@ def make_problem(kind, nx, x_lo, x_hi, bc=("outflow", "outflow"), cfl=0.5, t_end
         for d in range(3):
             pr.ic_dleft[v][d] = dleft[v][d] if dleft is not None and v < len(dleft) else 0.0
             pr.ic_dright[v][d] = dright[v][d] if dright is not None and v < len(dright) else 0.0
+    return pr
+
+
+def make_problem_2d(nx, ny, x_lo, x_hi, y_lo, y_hi, sides=("periodic",) * 4, mesh="cartesian", ramp_x0=0.0,
+                    ramp_deg=0.0, cfl=0.4, t_end=0.0, gamma=1.4, ic="freestream", param=(0, 0, 0, 0), dparam=None,
+                    x0=0.5, left=(0, 0, 0, 0), dleft=None, right=(0, 0, 0, 0), dright=None):
+    """2-D Euler problem; sides = (left, right, bottom, top)."""
+    pr = make_problem("euler2d", nx, x_lo, x_hi, bc=sides[:2], cfl=cfl, t_end=t_end, gamma=gamma, x0=x0,
+                      left=left, dleft=dleft, right=right, dright=dright)
+    pr.ny = ny
+    pr.y_lo, pr.y_hi = y_lo, y_hi
+    pr.bc_bottom, pr.bc_top = BC[sides[2]], BC[sides[3]]
+    pr.mesh_kind = MESH[mesh]
+    pr.ramp_x0, pr.ramp_deg = ramp_x0, ramp_deg
+    pr.ic_kind = IC[ic]
+    for v in range(4):
+        pr.ic_param[v] = param[v]
+        for d in range(3):
+            pr.ic_dparam[v][d] = dparam[v][d] if dparam is not None and v < len(dparam) else 0.0
     return pr
 
 

@@ -26,6 +26,39 @@ SOD_1D = dict(
 )
 
 
+# 2-D steady Euler over a 15-degree ramp (One-Shot IPM): inflow Mach 2 + 0.1 xi_1 at 10 + 1 xi_2 degrees,
+# rho = p = 1; 256 x 128 cells on x in [0, 2] under y = 1 (ramp from x = 0.5); total degree 4 in 2 dims
+# (N = 15 moments x 4 variables), 5 x 5 Gauss nodes; sides: inflow (Dirichlet), outflow, slip wall,
+# far field (Dirichlet); pseudo-time steps until the steady residual falls below 1e-8.
+RAMP_2D = dict(
+    name="ramp2d_oneshot", kind="euler2d", nx=256, ny=128, x_lo=0.0, x_hi=2.0, y_lo=0.0, y_hi=1.0, mesh="ramp",
+    ramp_x0=0.5, ramp_deg=15.0, sides=("dirichlet", "outflow", "slip", "dirichlet"), cfl=0.4, t_end=0.0, gamma=1.4,
+    p=2, M=4, nq=5, entropy="euler", ic="freestream", param=(1.0, 1.0, 2.0, 10.0),
+    dparam=((0.0, 0.0, 0.0), (0.0, 0.0, 0.0), (0.1, 0.0, 0.0), (0.0, 1.0, 0.0)), newton_tol=1e-10,
+    residual_tol=1e-8,
+)
+
+# 2-D Kelvin-Helmholtz-type shear layer on the periodic unit square, 512 x 512 cells: rho = 2, v_1 = -0.5
+# inside |y - 0.5| < 0.25 + 0.02 xi_3, rho = 1, v_1 = 0.5 outside, p = 2.5, v_2 = 0.01 (1 + 0.5 xi_1)
+# sin(4 pi (x + 0.1 xi_2)); 3 dims, 7^3 = 343 Gauss nodes, total degree M (2..6).
+KH_2D = dict(
+    name="kh2d", kind="euler2d", nx=512, ny=512, x_lo=0.0, x_hi=1.0, y_lo=0.0, y_hi=1.0, mesh="cartesian",
+    ramp_x0=0.0, ramp_deg=0.0, sides=("periodic",) * 4, cfl=0.4, t_end=0.0, gamma=1.4, p=3, M=2, nq=7,
+    entropy="euler", ic="shear", left=(2.0, -0.5, 0.0, 2.5), right=(1.0, 0.5, 0.0, 2.5),
+    param=(0.01, 0.0, 0.25, 4.0 * np.pi), dparam=((0.005, 0.0, 0.0), (0.0, 0.1, 0.0), (0.0, 0.0, 0.02), (0.0, 0.0, 0.0)),
+    newton_tol=1e-10, steps=200,
+)
+
+# 2-D data varying in x only (a Sod-type jump at x = 0.5, rho_L = 1 + 0.1 xi_1, p_L = 1 + 0.1 xi_2), periodic in y
+XRIEMANN_2D = dict(
+    name="xriemann2d", kind="euler2d", nx=30, ny=2, x_lo=0.0, x_hi=1.0, y_lo=0.0, y_hi=0.2, mesh="cartesian",
+    ramp_x0=0.0, ramp_deg=0.0, sides=("outflow", "outflow", "periodic", "periodic"), cfl=0.4, t_end=0.0,
+    gamma=1.4, p=2, M=2, nq=3, entropy="euler", ic="riemann", x0=0.5, left=(1.0, 0.0, 0.0, 1.0),
+    dleft=((0.1, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.1, 0.0)), right=(0.125, 0.0, 0.0, 0.1),
+    dright=((0.0, 0.0, 0.0),) * 4, param=(0.0, 0.0, 0.0, 0.0), dparam=None, newton_tol=1e-10,
+)
+
+
 def variant(base: dict, **changes) -> dict:
     """Copy of a workload with some parameters changed (smaller meshes for parity cases)."""
     out = dict(base)

@@ -42,8 +42,42 @@ def oracle_problem(w, tau=None):
     return prob
 
 
+def oracle_problem_2d(w, tau=None):
+    """oracle.scheme2d.Problem2D for a 2-D workload dictionary."""
+    from oracle import scheme2d as s2
+    sp = basis.StochasticSpace(w["p"], w["M"], w["nq"])
+    phys = physics.Euler(w["gamma"], 2)
+    ent = entropy.Euler(w["gamma"], 2) if w["entropy"] == "euler" else entropy.Quadratic(4)
+    if w["mesh"] == "ramp":
+        mesh = s2.ramp_mesh(w["nx"], w["ny"], w["x_lo"], w["x_hi"], w["y_hi"], w["ramp_x0"], w["ramp_deg"])
+    else:
+        mesh = s2.cartesian_mesh(w["nx"], w["ny"], w["x_lo"], w["x_hi"], w["y_lo"], w["y_hi"])
+    dp = w.get("dparam") or ((0.0, 0.0, 0.0),) * 4
+    if w["ic"] == "freestream":
+        ic = s2.FreestreamIC(rho=w["param"][0], p=w["param"][1], mach=w["param"][2], angle_deg=w["param"][3],
+                             dmach=dp[2], dangle=dp[3])
+    elif w["ic"] == "shear":
+        L, R = w["left"], w["right"]
+        ic = s2.ShearIC(rho_in=L[0], v_in=L[1], rho_out=R[0], v_out=R[1], p=L[3], amp=w["param"][0],
+                        phase=w["param"][1], half_width=w["param"][2], k=w["param"][3],
+                        y_mid=0.5 * (w["y_lo"] + w["y_hi"]), damp=dp[0], dphase=dp[1], dhalf_width=dp[2])
+    else:
+        ic = s2.RiemannXIC(left=tuple(w["left"]), right=tuple(w["right"]), x0=w["x0"],
+                           dleft=w.get("dleft") or ((0.0, 0.0, 0.0),) * 4, dright=w.get("dright") or ((0.0, 0.0, 0.0),) * 4)
+    return s2.Problem2D(phys=phys, ent=ent, space=sp, mesh=mesh, ic=ic, sides=tuple(w["sides"]), cfl=w["cfl"],
+                        t_end=w["t_end"], newton=dual.NewtonOptions(tau=tau if tau is not None else w.get("newton_tol", 1e-10)))
+
+
 def gpu_context(w, precision="fp64", tau=None, **opt):
     from paper_1912_09238_gb300 import ipm
+    if w["kind"] == "euler2d":
+        pr = ipm.make_problem_2d(w["nx"], w["ny"], w["x_lo"], w["x_hi"], w["y_lo"], w["y_hi"], sides=w["sides"],
+                                 mesh=w["mesh"], ramp_x0=w["ramp_x0"], ramp_deg=w["ramp_deg"], cfl=w["cfl"],
+                                 t_end=w["t_end"], gamma=w["gamma"], ic=w["ic"], param=w["param"],
+                                 dparam=w.get("dparam"), x0=w.get("x0", 0.5), left=w.get("left", (0, 0, 0, 0)),
+                                 dleft=w.get("dleft"), right=w.get("right", (0, 0, 0, 0)), dright=w.get("dright"))
+        o = ipm.default_options(precision, newton_tol=tau if tau is not None else w.get("newton_tol", 1e-10), **opt)
+        return ipm.Context(pr, w["p"], w["M"], w["nq"], w["entropy"], 0.0, 0.0, o)
     pr = ipm.make_problem(w["kind"], w["nx"], w["x_lo"], w["x_hi"], bc=w["bc"], cfl=w["cfl"], t_end=w["t_end"],
                           gamma=w["gamma"], x0=w["x0"], dx0=w["dx0"], left=w["left"], dleft=w.get("dleft"),
                           right=w["right"], dright=w.get("dright"))
