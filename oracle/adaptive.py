@@ -1,0 +1,151 @@
+"""Adaptive IPM (Sec. 5, Algorithm 3) on 2-D meshes (test infrastructure; see ``oracle/__init__``).
+
+Refinement levels l = 0..L-1 are total degrees M_l (consecutive: M_l = M_0 + l) with N_l moments.
+In the graded ordering of the multi-indices the moments of level l are the first N_l entries of
+the finest level's moment vector, so states are stored at the finest size N_{L-1} with the entries
+beyond the cell's level held at zero. One tensor Gauss rule serves every level (exact for the
+products of every level), so the nodal states of all cells live on the same nodes.
+
+* Smoothness indicator (Eq. errorIndicator) on the first conserved variable (the density):
+  S_l = <(u_l - u_{l-1})^2> / <u_l^2> = sum_{|i| = M_l} u_i^2 / sum_{|i| <= M_l} u_i^2 (orthonormal basis).
+* DetermineRefinementLevel: keep l if delta_- <= S_l <= delta_+, go one level down if S_l < delta_-,
+  one level up if S_l > delta_+ (clamped to 0..L-1). The paper prints delta_- > delta_+; the
+  interval is taken as [min, max] of the two printed values. The indicator is evaluated on the
+  cell's moments u_hat^n at its level (Algorithm 3 writes DetermineRefinementLevel(lambda_hat), but
+  Eq. errorIndicator is defined on moments).
+* Initial level (Algorithm 3: "choose initial refinement level"): the finest-level projection of the
+  initial data, lowered one level at a time while the indicator is below delta_-.
+* Step n (Algorithm 3): dual solve of every interior cell at its level l^n (Eq.
+  dualIterationFunctionAd: Newton with the level's basis, warm-started at lambda^n); new levels l^{n+1}
+  from u_hat^n; moment update c (Eq. adaptiveFVUpdate) with every stencil cell evaluated with its
+  own level's duals and the result projected onto level l^{n+1}; the duals of the next solve are
+  lambda^{n+1} padded with zeros or truncated to l^{n+1}.
+
+Pinned by: tests/test_oracle_adaptive.py (indicator against its integral definition on the nodes,
+level rules, a single level reproducing the fixed-degree scheme, pad/truncate bookkeeping,
+conservation on periodic meshes).
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import dual as dualmod
+from . import scheme2d as s2
+
+
+class SubSpace:
+    """The first N_l basis functions of a space (same nodes and weights)."""
+
+    def __init__(self, space, n):
+        self.N = n
+        self.Q = space.Q
+        self.w = space.w
+        self.nodes = space.nodes
+        self.Phi = space.Phi[:, :n]
+
+    def project(self, values_at_nodes):
+        return np.einsum("k,...ka,ki->...ia", self.w, values_at_nodes, self.Phi)
+
+    def evaluate(self, coeffs):
+        return np.einsum("ki,...ia->...ka", self.Phi, coeffs)
+
+
+@dataclass
+class Levels:
+    degrees: tuple          # consecutive total degrees, coarsest first
+    delta_lo: float
+    delta_hi: float
+
+
+def indicator(uhat0, n_l, n_prev):
+    """S_l of Eq. errorIndicator on one variable: uhat0 (..., N) moments, level sizes N_l and N_{l-1}."""
+    idx = np.arange(uhat0.shape[-1])
+    top = np.sum(np.where((idx >= n_prev) & (idx < n_l), uhat0 ** 2, 0.0), axis=-1)
+    tot = np.sum(np.where(idx < n_l, uhat0 ** 2, 0.0), axis=-1)
+    return top / tot
+
+
+def level_sizes(space, lv: Levels):
+    """(N_l, N_{l-1}) per level; N_{-1} counts the moments of degree below the coarsest level's."""
+    deg = np.sum(space.indices, axis=1)
+    nl = [int(np.sum(deg <= M)) for M in lv.degrees]
+    nprev = [int(np.sum(deg <= M - 1)) for M in lv.degrees]
+    return nl, nprev
+
+
+def _indicator_levels(uhat, level, nl, nprev):
+    n_cur = np.asarray(nl)[level]
+    n_prv = np.asarray(nprev)[level]
+    return indicator(uhat[..., 0], n_cur[..., None], n_prv[..., None])
+
+
+def new_levels(uhat, level, nl, nprev, lv: Levels):
+    S = _indicator_levels(uhat, level, nl, nprev)
+    lo, hi = min(lv.delta_lo, lv.delta_hi), max(lv.delta_lo, lv.delta_hi)
+    new = np.where(S < lo, level - 1, np.where(S > hi, level + 1, level))
+    return np.clip(new, 0, len(nl) - 1), S
+
+
+def truncate(arr, level, nl):
+    """Zero the moments beyond each cell's level: arr (..., N, m), level (...)."""
+    idx = np.arange(arr.shape[-2])
+    keep = idx[None, :] < np.asarray(nl)[level][..., None]
+    return np.where(keep[..., None], arr, 0.0)
+
+
+@dataclass
+class AdaptiveState:
+    uhat: np.ndarray        # (ny+2, nx+2, N_max, m)
+    lam: np.ndarray
+    level: np.ndarray       # (ny+2, nx+2) int
+    t: float = 0.0
+    n: int = 0
+    last_dt: float = 0.0
+    newton_iters: np.ndarray = None
+    newton_status: np.ndarray = None
+    residual: float = np.inf
+
+
+def initial_state(prob: s2.Problem2D, lv: Levels) -> AdaptiveState:
+    """Finest projection, levels lowered while the indicator is below delta_-, then truncated.
+    Periodic sides only (the ghost cells are never read)."""
+    st = s2.initial_state(prob)
+    nl, nprev = level_sizes(prob.space, lv)
+    level = np.full(st.uhat.shape[:2], len(nl) - 1, dtype=np.int64)
+    lo = min(lv.delta_lo, lv.delta_hi)
+    for _ in range(len(nl)):
+        S = _indicator_levels(st.uhat, level, nl, nprev)
+        level = np.where((S < lo) & (level > 0), level - 1, level)
+    return AdaptiveState(uhat=truncate(st.uhat, level, nl), lam=truncate(st.lam, level, nl), level=level)
+
+
+def ipm_step(prob: s2.Problem2D, st: AdaptiveState, lv: Levels) -> AdaptiveState:
+    """One time step of Algorithm 3 on the interior cells."""
+    nl, nprev = level_sizes(prob.space, lv)
+    ny, nx = prob.mesh.ny, prob.mesh.nx
+    lam = st.lam.copy()
+    it = np.zeros((ny, nx), dtype=np.int64)
+    stat = np.zeros((ny, nx), dtype=np.int64)
+    inner_level = st.level[1:-1, 1:-1]
+    for l, n in enumerate(nl):
+        sel = np.nonzero(inner_level == l)
+        if sel[0].size == 0:
+            continue
+        sub = SubSpace(prob.space, n)
+        jj, ii = sel[0] + 1, sel[1] + 1
+        li, itl, sl, _ = dualmod.dual_solve(sub, prob.ent, st.lam[jj, ii, :n], st.uhat[jj, ii, :n], prob.newton)
+        lam[jj, ii, :n] = li
+        it[sel] = itl
+        stat[sel] = sl
+    level = st.level.copy()
+    level[1:-1, 1:-1], _ = new_levels(st.uhat[1:-1, 1:-1], inner_level, nl, nprev, lv)
+    # periodic ghosts mirror the levels of the cells they copy (they are never read by the update)
+    U = s2.nodal_states(prob, lam)
+    dt = s2.time_step(prob, U, st.t)
+    uhat = st.uhat.copy()
+    uhat[1:-1, 1:-1] = truncate(s2.moment_update(prob, lam, dt), level[1:-1, 1:-1], nl)
+    lam_next = lam.copy()
+    lam_next[1:-1, 1:-1] = truncate(lam[1:-1, 1:-1], level[1:-1, 1:-1], nl)
+    res = s2.steady_residual(prob, uhat, st.uhat)
+    return AdaptiveState(uhat=uhat, lam=lam_next, level=level, t=st.t + dt, n=st.n + 1, last_dt=dt,
+                         newton_iters=it, newton_status=stat, residual=res)
