@@ -148,6 +148,13 @@ typedef struct {
   double armijo_c;          /* sufficient-decrease constant */
   int max_halvings;         /* Armijo backtracking cap */
   double slack_rel;         /* rounding allowance of the Armijo test, relative to the terms of L */
+  /* Adaptive IPM (Sec. 5, Algorithm 3; 2-D problems): 0 = off; else every cell carries a total degree
+   * between adapt_min_degree and basis.total_degree (at most 8 levels), chosen each step by the
+   * smoothness indicator S (Eq. errorIndicator) of its density moments: kept for S in
+   * [min(delta_lo, delta_hi), max(...)], lowered one degree below, raised one above; the moments and
+   * duals beyond a cell's degree are zero (graded ordering: a lower degree is a prefix). */
+  int adapt_min_degree;
+  double delta_lo, delta_hi;
 } ipm_options;
 
 /* Sizes of a context's arrays. */
@@ -178,7 +185,7 @@ typedef struct {
 typedef struct ipm_ctx ipm_ctx;
 
 /* Fill *opt with the defaults: FP64, tau = 1e-10, 100 iterations, c = 1e-4, 30 halvings,
- * slack 1e-12. */
+ * slack 1e-12, no adaptivity (thresholds 2e-5 and 2e-4 preset). */
 void ipm_default_options(ipm_options* opt);
 
 /* Create a context on the current CUDA device: build the basis and quadrature tables, allocate
@@ -210,6 +217,9 @@ ipm_status ipm_get_duals(ipm_ctx* ctx, double* host, size_t count);
 /* Nodal states u_s(lambda_j^T phi(xi_k)) at the current duals, laid out [cell][variable][node]
  * (count = n_cells*m*Q). Valid after ipm_dual_solve / ipm_step / ipm_oneshot_step. */
 ipm_status ipm_get_nodal_states(ipm_ctx* ctx, double* host, size_t count);
+
+/* Adaptive contexts: the refinement level (index from adapt_min_degree) of every cell, count = n_cells. */
+ipm_status ipm_get_levels(ipm_ctx* ctx, int* host, size_t count);
 
 /* Device-pointer variants: buffers live on the context's device, same layout and count;
  * asynchronous on the context's stream. */

@@ -27,6 +27,9 @@ struct ipm_ctx {
   double dx = 0.0;
   bool is2d = false;
   Mesh2DHost mesh2d;
+  int n_levels = 0;                 // adaptive: levels adapt_min_degree .. total_degree
+  int lev_n[8] = {0}, lev_prev[8] = {0};
+  int* d_level = nullptr;
   double *d_area = nullptr, *d_xf = nullptr, *d_yf = nullptr;
   int device = 0;
   cudaStream_t own_stream = nullptr;
@@ -132,6 +135,8 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.max_halvings = c->opt.max_halvings;
   a.track_speed = 1;
   a.h_dump = nullptr;
+  a.level = c->n_levels ? c->d_level : nullptr;
+  for (int k = 0; k < 8; ++k) a.lev_n[k] = c->lev_n[k];
   a.mx.phi_img = c->d_phi_img;
   a.mx.phiT32 = c->d_phiT32;
   a.mx.n_pad = c->mx.n_pad;
@@ -187,6 +192,15 @@ static Update2DArgs update2d_args(const ipm_ctx* c, double dt_override, bool res
   u.gamma = c->prob.gamma;
   u.dt_override = dt_override;
   u.clip = clip ? 1 : 0;
+  u.level = c->n_levels ? c->d_level : nullptr;
+  u.lam = c->d_lam;
+  u.n_levels = c->n_levels;
+  for (int k = 0; k < 8; ++k) {
+    u.lev_n[k] = c->lev_n[k];
+    u.lev_prev[k] = c->lev_prev[k];
+  }
+  u.delta_lo = std::min(c->opt.delta_lo, c->opt.delta_hi);
+  u.delta_hi = std::max(c->opt.delta_lo, c->opt.delta_hi);
   return u;
 }
 
@@ -244,7 +258,7 @@ static void free_ctx(ipm_ctx* c) {
   if (c->oneshot_exec) cudaGraphExecDestroy(c->oneshot_exec);
   void* ptrs[] = {c->d_Phi, c->d_PhiT, c->d_w, c->d_nodes, c->d_pairs, c->d_uhat, c->d_lam, c->d_unode,
                   c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc,
-                  c->d_phiT32, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf};
+                  c->d_phiT32, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf, c->d_level};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -317,6 +331,24 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   c->n_cells = c->is2d ? (problem->nx + 2) * (problem->ny + 2) : problem->nx + 2;
   c->dx = (problem->x_hi - problem->x_lo) / problem->nx;
   if (c->is2d) build_mesh2d(*problem, c->mesh2d);
+  if (opt.adapt_min_degree > 0) {
+    if (!c->is2d) return fail(nullptr, IPM_EINVAL, "ipm_init: adaptivity is built for 2-D problems");
+    const int L = basis->total_degree - opt.adapt_min_degree + 1;
+    if (L < 1 || L > 8) return fail(nullptr, IPM_EINVAL, "ipm_init: adaptivity needs 1..8 levels up to the basis degree");
+    c->n_levels = L;
+    for (int l = 0; l < L; ++l) {
+      const int M = opt.adapt_min_degree + l;
+      int n = 0, np = 0;
+      for (int i = 0; i < c->N; ++i) {
+        int deg = 0;
+        for (int d = 0; d < c->tab.p; ++d) deg += c->tab.indices[(size_t)i * c->tab.p + d];
+        n += deg <= M;
+        np += deg <= M - 1;
+      }
+      c->lev_n[l] = n;
+      c->lev_prev[l] = np;
+    }
+  }
   if (c->N > 65535) {
     return fail(nullptr, IPM_EINVAL, "ipm_init: too many moments");
   }
@@ -379,6 +411,7 @@ static size_t ctx_footprint(const ipm_ctx* c) {
   if (!c->h_in_smem) b += (size_t)c->newton_grid * c->hwork_stride * 8;
   if (c->mixed) b += N * Q * 4 + (size_t)c->mx.chunks * c->mx.b_chunk_bytes;
   if (c->is2d) b += (c->mesh2d.area.size() + c->mesh2d.xf.size() + c->mesh2d.yf.size()) * 8;
+  if (c->n_levels) b += nc * 4;
   return b;
 }
 
@@ -392,6 +425,9 @@ void ipm_default_options(ipm_options* o) {
   o->armijo_c = 1e-4;
   o->max_halvings = 30;
   o->slack_rel = 1e-12;
+  o->adapt_min_degree = 0;
+  o->delta_lo = 2e-5;
+  o->delta_hi = 2e-4;
 }
 
 const char* ipm_last_error(const ipm_ctx* c) {
@@ -493,6 +529,11 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
     CK(upload(&c->d_yf, c->mesh2d.yf), "upload y faces");
     if (st == IPM_OK)
       CK(launch_init2d(c->entk, dev_tables(c), ent_params(c), c->prob, c->d_uhat, c->d_lam, c->stream), "init kernel");
+    if (c->n_levels) {
+      CK(cudaMalloc(&c->d_level, (size_t)c->n_cells * sizeof(int)), "cudaMalloc levels");
+      if (st == IPM_OK)
+        CK(launch_init_levels(update2d_args(c, 0.0, false, false), c->n_cells, c->stream), "initial levels");
+    }
   } else {
     CK(launch_init1d(c->entk, c->m, dev_tables(c), ent_params(c), c->prob, c->d_uhat, c->d_lam, c->n_cells, c->stream),
        "init kernel");
@@ -613,6 +654,15 @@ ipm_status ipm_get_nodal_states(ipm_ctx* c, double* h, size_t n) {
   if (!c) return IPM_EINVAL;
   return copy_state(c, h, c->d_unode, n, (size_t)c->n_cells * c->m * c->Q, cudaMemcpyDeviceToHost, true);
 }
+ipm_status ipm_get_levels(ipm_ctx* c, int* h, size_t n) {
+  if (!c || !h) return IPM_EINVAL;
+  if (!c->n_levels) return fail(c, IPM_EINVAL, "ipm_get_levels: the context is not adaptive");
+  if (n != (size_t)c->n_cells) return fail(c, IPM_EINVAL, "ipm_get_levels: count must be n_cells");
+  IPM_CK(c, cudaMemcpyAsync(h, c->d_level, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  IPM_CK(c, cudaStreamSynchronize(c->stream));
+  return IPM_OK;
+}
+
 ipm_status ipm_set_moments_device(ipm_ctx* c, const double* d, size_t n) {
   if (!c) return IPM_EINVAL;
   return copy_state(c, c->d_uhat, d, n, (size_t)c->n_cells * c->NM, cudaMemcpyDeviceToDevice, false);

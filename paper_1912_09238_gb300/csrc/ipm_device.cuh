@@ -275,6 +275,8 @@ struct NewtonArgs {
   int track_speed;       // 1: fold the nodal signal speeds of the result into sc->smax_bits
   double* h_dump;        // non-null: assemble the Hessian at the current duals, store it packed
                          // [work item][NM(NM+1)/2] and stop (no Newton update)
+  const int* level;      // adaptive meshes: refinement level per cell (nullptr: every cell at tab.N)
+  int lev_n[8];          // moments per level (graded prefixes of the table's basis)
   MixedTiles mx;         // mixed path only
   uint32_t off_h, off_a, off_b;  // shared-memory byte offsets: packed H, A staging, Phi chunks
 };
@@ -313,6 +315,12 @@ struct Update2DArgs {
   double cfl, t_end, gamma;
   double dt_override;    // > 0: use this dt
   int clip;              // 1: clip the step to t_end
+  // adaptive meshes (Algorithm 3): level per cell, or nullptr
+  int* level;
+  double* lam;           // [(ny+2)(nx+2)][N][m]  duals (truncated to the new level)
+  int n_levels;
+  int lev_n[8], lev_prev[8];   // moments of each level and of the level's lower-degree part
+  double delta_lo, delta_hi;
 };
 
 #ifdef __CUDACC__

@@ -112,9 +112,9 @@ __device__ __forceinline__ void store_block_entry(double* s_H, int a, int b, int
 
 // (b), FP64 on the CUDA cores: one thread per moment pair (i >= j), all B blocks at once.
 template <int M>
-__device__ __forceinline__ void hessian_fp64(const NewtonArgs& a, const double* s_wJ, double* s_H) {
+__device__ __forceinline__ void hessian_fp64(const NewtonArgs& a, int N, const double* s_wJ, double* s_H) {
   constexpr int B = packed_count(M);
-  const int N = a.tab.N, Q = a.tab.Q, NP = N * (N + 1) / 2;
+  const int ldN = a.tab.N, Q = a.tab.Q, NP = N * (N + 1) / 2;
   const double* __restrict__ Phi = a.tab.Phi;
   for (int pidx = threadIdx.x; pidx < NP; pidx += NT) {
     const uint32_t pr = a.tab.pairs[pidx];
@@ -123,7 +123,7 @@ __device__ __forceinline__ void hessian_fp64(const NewtonArgs& a, const double* 
 #pragma unroll
     for (int b = 0; b < B; ++b) acc[b] = 0.0;
     for (int q = 0; q < Q; ++q) {
-      const double pq = Phi[(size_t)q * N + i] * Phi[(size_t)q * N + j];
+      const double pq = Phi[(size_t)q * ldN + i] * Phi[(size_t)q * ldN + j];
 #pragma unroll
       for (int b = 0; b < B; ++b) acc[b] = fma(s_wJ[b * Q + q], pq, acc[b]);
     }
@@ -375,21 +375,26 @@ __device__ __forceinline__ bool tc_wait(TcState& t, int k) {
 // widened into the packed FP64 H. s_wJf holds w_k J_k,ab as float [B][Q]. Returns false when a
 // bounded wait ran out (the CTA must stop).
 template <int M>
-__device__ bool hessian_tc(const NewtonArgs& a, const float* s_wJf, double* s_H, uint8_t* sA, uint8_t* sB,
+__device__ bool hessian_tc(const NewtonArgs& a, int N, const float* s_wJf, double* s_H, uint8_t* sA, uint8_t* sB,
                            TcState& t, int* s_abort) {
   constexpr int B = packed_count(M);
   const MixedTiles& mx = a.mx;
-  const int N = a.tab.N, Q = a.tab.Q, BN = B * N;
+  const int Q = a.tab.Q, BN = B * N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t sbo = tc::kmajor_sbo(mx.kc);
   const uint32_t a_img = (uint32_t)mx.tpp * 128u * (uint32_t)mx.kc * 2u;   // one BF16 term of A
-  const uint32_t b_img = (uint32_t)mx.n_pad * (uint32_t)mx.kc * 2u;         // one BF16 term of B
+  const uint32_t b_img = (uint32_t)mx.n_pad * (uint32_t)mx.kc * 2u;         // one BF16 term of B (table size)
   const uint32_t b_chunk = 2u * b_img;
-  const uint32_t idesc = tc::idesc_bf16_f32(128, mx.n_pad);
+  // this cell's tiling (N may be below the table's on adaptive meshes: the Phi image rows beyond N
+  // only feed accumulator columns that are never read back)
+  const int n_pad = (N + 15) / 16 * 16;
+  const int tiles = (BN + 127) / 128;
+  const int tpp = min(mx.tpp, tiles);
+  const uint32_t idesc = tc::idesc_bf16_f32(128, n_pad);
   const int groups = mx.kc / 8;
 
-  for (int t0 = 0; t0 < mx.tiles; t0 += mx.tpp) {
-    const int nt = min(mx.tpp, mx.tiles - t0);
+  for (int t0 = 0; t0 < tiles; t0 += tpp) {
+    const int nt = min(tpp, tiles - t0);
     const int rows = nt * 128;
     if (tid == 0) {
       tc::mbar_arrive_expect_tx(&t.bars[1], b_chunk);
@@ -441,7 +446,7 @@ __device__ bool hessian_tc(const NewtonArgs& a, const float* s_wJf, double* s_H,
         tc::fence_after_sync();
         const uint32_t sa = tc::smem_u32(sA), sb = tc::smem_u32(sB + buf * b_chunk);
         for (int tl = 0; tl < nt; ++tl) {
-          const uint32_t d = t.tmem + (uint32_t)(tl * mx.n_pad);
+          const uint32_t d = t.tmem + (uint32_t)(tl * n_pad);
           const uint32_t ta = sa + (uint32_t)tl * 16u * sbo;   // 128 rows = 16 row groups
           for (int ks = 0; ks < mx.kc / 16; ++ks) {
             const uint32_t kofs = (uint32_t)ks * 256u;
@@ -463,7 +468,7 @@ __device__ bool hessian_tc(const NewtonArgs& a, const float* s_wJf, double* s_H,
     // accumulators -> packed FP64 H. Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 and one
     // half of the columns.
     const int lq = warp & 3, half = warp >> 2;
-    const int hcols = mx.n_pad / 2;
+    const int hcols = n_pad / 2;
     for (int tl = 0; tl < nt; ++tl) {
       const int R = (t0 + tl) * 128 + lq * 32 + lane;
       const bool valid = R < BN;
@@ -473,7 +478,7 @@ __device__ bool hessian_tc(const NewtonArgs& a, const float* s_wJf, double* s_H,
       for (int cg = 0; cg < hcols; cg += 8) {
         const int col0 = half * hcols + cg;
         uint32_t r[8];
-        tc::tmem_ld_x8(t.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(tl * mx.n_pad + col0), r);
+        tc::tmem_ld_x8(t.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(tl * n_pad + col0), r);
         tc::tmem_wait_ld();
         if (valid) {
 #pragma unroll
@@ -499,20 +504,21 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
   __shared__ int s_flag;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bars[3];
-  const int N = a.tab.N, Q = a.tab.Q, NM = N * M;
+  // shared arrays are sized for the table's N (the finest level); a cell may use fewer moments
+  const int NX = a.tab.N, Q = a.tab.Q, NMX = NX * M;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   double* s_lam = smem;
-  double* s_uh = s_lam + NM;
-  double* s_g = s_uh + NM;
-  double* s_d = s_g + NM;
-  double* s_Lam = s_d + NM;       // [M][Q]
+  double* s_uh = s_lam + NMX;
+  double* s_g = s_uh + NMX;
+  double* s_d = s_g + NMX;
+  double* s_Lam = s_d + NMX;      // [M][Q]
   double* s_dLam = s_Lam + M * Q; // [M][Q]
   double* s_u = s_dLam + M * Q;   // [M][Q]
   double* s_wJ = s_u + M * Q;     // [B][Q]  (float [B][Q] on the mixed path)
   double* s_red = s_wJ + B * Q;   // NWARPS * 8
   double* s_wu = s_red + NWARPS * 8;  // [M][Q] w_k u_k
   double* s_dinv = s_wu + M * Q;      // [NM] reciprocal pivots
-  double* s_P = s_dinv + NM;          // [2][(NM + 1) * PSTR] Cholesky panels (current, next)
+  double* s_P = s_dinv + NMX;         // [2][(NM + 1) * PSTR] Cholesky panels (current, next)
   uint8_t* sbytes = reinterpret_cast<uint8_t*>(smem);
   double* s_H = H_SMEM ? reinterpret_cast<double*>(sbytes + a.off_h) : (a.hwork + (size_t)blockIdx.x * a.hwork_stride);
   uint8_t* sA = sbytes + a.off_a;
@@ -520,7 +526,6 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
   const double* __restrict__ PhiT = a.tab.PhiT;
   const double* __restrict__ Phi = a.tab.Phi;
   const double* __restrict__ w = a.tab.w;
-  const size_t NPH = (size_t)NM * (NM + 1) / 2;
 
   TcState tcs;
   tcs.bars = s_bars;
@@ -547,8 +552,10 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
     const int wk = s_work;
     if (wk >= a.n_work) break;
     const int cell = a.cell_list ? a.cell_list[wk] : work_cell(wk, a.nx, a.gy);
-    double* lam_g = a.lam + (size_t)cell * NM;
-    const double* uh_g = a.uhat + (size_t)cell * NM;
+    const int N = a.level ? a.lev_n[a.level[cell]] : NX;     // moments of this cell's level
+    const int NM = N * M;
+    double* lam_g = a.lam + (size_t)cell * NMX;
+    const double* uh_g = a.uhat + (size_t)cell * NMX;
     for (int r = tid; r < NM; r += NT) {
       s_lam[r] = lam_g[r];
       s_uh[r] = uh_g[r];
@@ -611,7 +618,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
         const double* wu = s_wu + c * Q;
         double acc = 0.0;
 #pragma unroll 8
-        for (int q = 0; q < Q; ++q) acc = fma(Phi[(size_t)q * N + i], wu[q], acc);
+        for (int q = 0; q < Q; ++q) acc = fma(Phi[(size_t)q * NX + i], wu[q], acc);
         s_g[r] = acc - s_uh[r];
       }
       __syncthreads();
@@ -638,17 +645,18 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
 
       // (b) Hessian, packed lower triangle, row index r = i*M + a
       if (MIXED) {
-        if (!hessian_tc<M>(a, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, tcs, &s_abort)) {
+        if (!hessian_tc<M>(a, N, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, tcs, &s_abort)) {
           if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
           st = ST_TIMEOUT;
           stop = true;
           break;
         }
       } else {
-        hessian_fp64<M>(a, s_wJ, s_H);
+        hessian_fp64<M>(a, N, s_wJ, s_H);
       }
       __syncthreads();
       if (a.h_dump) {
+        const size_t NPH = (size_t)NM * (NM + 1) / 2;
         double* hd = a.h_dump + (size_t)wk * NPH;
         for (size_t r = tid; r < NPH; r += NT) hd[r] = s_H[r];
         break;

@@ -134,8 +134,36 @@ __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
     __syncthreads();
     double* out = a.uhat + (size_t)c * NM;
     const double old00 = out[0];
+    // adaptive meshes: the new level from the smoothness indicator of the density moments u_hat^n at
+    // the cell's level (Eq. errorIndicator): keep inside [delta_lo, delta_hi], one level down below,
+    // one level up above
+    int n_new = N;
+    int lev_new = 0;
+    if (a.level) {
+      const int lev = a.level[c];
+      const int n_lev = a.lev_n[lev], n_prv = a.lev_prev[lev];
+      double top = 0.0, tot = 0.0;
+      for (int ii = lane; ii < n_lev; ii += 32) {
+        const double v = out[ii * M];
+        tot = fma(v, v, tot);
+        if (ii >= n_prv) top = fma(v, v, top);
+      }
+      top = warp_sum(top);
+      tot = warp_sum(tot);
+      const double S = top / tot;
+      lev_new = S < a.delta_lo ? lev - 1 : (S > a.delta_hi ? lev + 1 : lev);
+      lev_new = min(max(lev_new, 0), a.n_levels - 1);
+      n_new = a.lev_n[lev_new];
+    }
     __syncthreads();
     for (int ii = warp; ii < N; ii += W2) {
+      if (ii >= n_new) {                                   // beyond the new level: moments and duals are zero
+        if (lane < M) {
+          out[ii * M + lane] = 0.0;
+          a.lam[(size_t)c * NM + ii * M + lane] = 0.0;
+        }
+        continue;
+      }
       double s[M];
 #pragma unroll
       for (int k = 0; k < M; ++k) s[k] = 0.0;
@@ -152,8 +180,45 @@ __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
     }
     __syncthreads();
     if (tid == 0 && a.cell_resid) a.cell_resid[c] = area * fabs(out[0] - old00);
+    if (tid == 0 && a.level) a.level[c] = lev_new;
     __syncthreads();
   }
+}
+
+// Initial refinement levels (adaptive meshes): from the finest projection, lower the level of every
+// cell one step at a time while its indicator is below delta_lo, then zero the moments and duals
+// beyond the level. One warp per cell.
+__global__ void k_init_levels(Update2DArgs a, int n_cells) {
+  constexpr int M = 4;
+  const int N = a.tab.N, NM = N * M;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (c >= n_cells) return;
+  const double* u = a.uhat + (size_t)c * NM;
+  int lev = a.n_levels - 1;
+  for (int k = 0; k < a.n_levels; ++k) {
+    const int nl = a.lev_n[lev], np = a.lev_prev[lev];
+    double top = 0.0, tot = 0.0;
+    for (int ii = lane; ii < nl; ii += 32) {
+      const double v = u[ii * M];
+      tot = fma(v, v, tot);
+      if (ii >= np) top = fma(v, v, top);
+    }
+    top = warp_sum(top);
+    tot = warp_sum(tot);
+    if (lev > 0 && top / tot < a.delta_lo) --lev;
+  }
+  const int n = a.lev_n[lev];
+  for (int r = n * M + lane; r < NM; r += 32) {
+    a.uhat[(size_t)c * NM + r] = 0.0;
+    a.lam[(size_t)c * NM + r] = 0.0;
+  }
+  if (lane == 0) a.level[c] = lev;
+}
+
+cudaError_t launch_init_levels(const Update2DArgs& a, int n_cells, cudaStream_t s) {
+  k_init_levels<<<(n_cells + 7) / 8, 256, 0, s>>>(a, n_cells);
+  return cudaGetLastError();
 }
 
 cudaError_t prepare_update2d(int Q) { return raise_smem_limit(k_update2d, (size_t)4 * Q * sizeof(double)); }

@@ -49,7 +49,8 @@ class ipm_entropy(ctypes.Structure):
 
 class ipm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("newton_tol", ctypes.c_double), ("max_newton", ctypes.c_int),
-                ("armijo_c", ctypes.c_double), ("max_halvings", ctypes.c_int), ("slack_rel", ctypes.c_double)]
+                ("armijo_c", ctypes.c_double), ("max_halvings", ctypes.c_int), ("slack_rel", ctypes.c_double),
+                ("adapt_min_degree", ctypes.c_int), ("delta_lo", ctypes.c_double), ("delta_hi", ctypes.c_double)]
 
 
 class ipm_dims(ctypes.Structure):
@@ -103,6 +104,7 @@ SIGNATURES = [
     ("ipm_set_duals", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
     ("ipm_get_duals", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
     ("ipm_get_nodal_states", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
+    ("ipm_get_levels", ctypes.c_int, [_vp, _P(ctypes.c_int), ctypes.c_size_t]),
     ("ipm_set_moments_device", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("ipm_get_moments_device", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("ipm_dual_solve", ctypes.c_int, [_vp, _P(ipm_stats)]),
@@ -286,6 +288,11 @@ class Context:
     def get_nodal_states(self):
         d = self.dims
         return self._get("ipm_get_nodal_states", (d.n_cells, d.m, d.Q))
+
+    def get_levels(self):
+        out = np.empty(self.dims.n_cells, dtype=np.int32)
+        _check("ipm_get_levels", lib().ipm_get_levels(self.h, out.ctypes.data_as(_P(ctypes.c_int)), out.size), self.h)
+        return out
 
     def set_moments_device(self, ptr, count):
         _check("ipm_set_moments_device", lib().ipm_set_moments_device(self.h, _vp(ptr), count), self.h)

@@ -1,0 +1,60 @@
+"""GPU parity of adaptive IPM (Algorithm 3, per-cell total degree from Eq. errorIndicator) against the
+adaptive oracle, on the periodic shear-layer workload at reduced size, through the C ABI.
+
+The levels are integers decided by FP64 comparisons on both sides and must agree exactly; moments
+and duals to 1e-10 (FP64 path) or 1e-6 (mixed path)."""
+import numpy as np
+import pytest
+
+from oracle import adaptive as ad
+from paper_1912_09238_gb300 import workloads
+from tests._cases import gpu_context, oracle_problem_2d, rel_err
+
+pytestmark = pytest.mark.gpu
+
+KH = workloads.variant(workloads.KH_2D, nx=12, ny=12, M=4, nq=5)
+LV = ad.Levels(degrees=(2, 3, 4), delta_lo=2e-4, delta_hi=2e-5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_09238_gb300 import build
+    build.build()
+
+
+def _grid(a, w):
+    return a.reshape(w["ny"] + 2, w["nx"] + 2, *a.shape[1:])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_adaptive_steps_match_the_oracle(precision):
+    prob = oracle_problem_2d(KH)
+    st = ad.initial_state(prob, LV)
+    ctx = gpu_context(KH, precision=precision, adapt_min_degree=2, delta_lo=2e-4, delta_hi=2e-5)
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    assert np.array_equal(_grid(ctx.get_levels(), KH)[1:-1, 1:-1], st.level[1:-1, 1:-1])
+    assert rel_err(_grid(ctx.get_moments(), KH)[1:-1, 1:-1], st.uhat[1:-1, 1:-1]) < 1e-13
+    seen = set()
+    for n in range(5):
+        st = ad.ipm_step(prob, st, LV)
+        s = ctx.step()
+        assert s.failed_cells == 0 and s.tc_timeouts == 0
+        lev = _grid(ctx.get_levels(), KH)[1:-1, 1:-1]
+        assert np.array_equal(lev, st.level[1:-1, 1:-1]), n
+        seen |= set(np.unique(lev).tolist())
+        assert rel_err(_grid(ctx.get_moments(), KH)[1:-1, 1:-1], st.uhat[1:-1, 1:-1]) < tol, n
+        if precision == "fp64":
+            assert rel_err(_grid(ctx.get_duals(), KH)[1:-1, 1:-1], st.lam[1:-1, 1:-1]) < 1e-9
+            assert s.newton_iters == int(st.newton_iters.sum())
+    assert len(seen) >= 2                      # the levels did change
+
+
+def test_adaptive_rejects_1d_and_bad_ranges():
+    from paper_1912_09238_gb300 import ipm
+    with pytest.raises(ipm.IpmError):
+        gpu_context(workloads.variant(workloads.BURGERS_1D, nx=10), adapt_min_degree=2)
+    with pytest.raises(ipm.IpmError):
+        gpu_context(KH, adapt_min_degree=5)       # above the basis degree
