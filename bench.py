@@ -284,6 +284,8 @@ def run_gpu(args):
                             "speedup_mixed_over_fp64": main["value"] / ref["value"]}
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_bench(args)
+    if rank == 0 and not args.no_workloads:
+        line["workloads"] = workloads_bench(args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -291,6 +293,89 @@ def run_gpu(args):
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------------
+def _timed_steps(ctx, n, oneshot=False, stop_residual=None):
+    """n steps (or until the steady residual falls below stop_residual), CUDA-event timed on the
+    context's stream; returns (steps, seconds, last stats)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    done, secs, s = 0, 0.0, None
+    chunk = 50 if stop_residual else n
+    while done < n:
+        k = min(chunk, n - done)
+        a.record(stream)
+        for _ in range(k):
+            (ctx.oneshot_step if oneshot else ctx.step)(sync=False)
+        b.record(stream)
+        b.synchronize()
+        secs += a.elapsed_time(b) / 1e3
+        done += k
+        s = ctx.sync_stats()
+        if s.failed_cells:
+            raise RuntimeError(f"failed cells: {s.as_dict()}")
+        if stop_residual and s.residual < stop_residual:
+            break
+    return done, secs, s
+
+
+def workloads_bench(args):
+    """The other workloads, each as a bounded run on both precision paths (cell-steps/s by CUDA events):
+    1-D Burgers to its t_end; the 2-D ramp by One-Shot pseudo-time steps towards its 1e-8 residual (step
+    cap); the 2-D shear layer with adaptive degree 2-6 and 7^3 nodes (a bounded number of steps)."""
+    import numpy as np
+    from paper_1912_09238_gb300 import workloads
+    from tests._cases import gpu_context
+    import torch
+    out = {}
+    stream = torch.cuda.current_stream()
+    # 1-D Burgers (200 cells, N = 6, Q = 10), Algorithm 1 to t_end = 0.11
+    w = workloads.BURGERS_1D
+    r = {}
+    for prec in ("mixed", "fp64"):
+        ctx = gpu_context(w, precision=prec)
+        ctx.set_stream(stream.cuda_stream)
+        n, secs, s = _timed_steps(ctx, 176)
+        r[prec] = {"value": w["nx"] * n / secs, "steps": n, "t": s.t, "seconds": secs}
+        ctx.close()
+    out["burgers1d"] = {"workload": "1-D Burgers IPM, 200 cells, N = 6, Q = 10, barrier entropy, to t_end = 0.11",
+                        "unit": UNIT, **r}
+    # 2-D ramp, One-Shot towards residual 1e-8
+    w = workloads.RAMP_2D
+    cells = w["nx"] * w["ny"]
+    r = {}
+    for prec in ("mixed", "fp64"):
+        ctx = gpu_context(w, precision=prec)
+        ctx.set_stream(stream.cuda_stream)
+        cap = args.ramp_steps if prec == "mixed" else min(args.ramp_steps, 200)
+        tune = ctx.tuning()
+        n, secs, s = _timed_steps(ctx, cap, oneshot=True, stop_residual=w["residual_tol"] if prec == "mixed" else None)
+        r[prec] = {"value": cells * n / secs, "steps": n, "residual": s.residual, "seconds": secs,
+                   "newton_kernel": {1: "cta_per_cell", 2: "warp_per_cell"}[tune[0]],
+                   "autotune_ms": {"cta_per_cell": tune[1], "warp_per_cell": tune[2]}}
+        ctx.close()
+    out["ramp2d_oneshot"] = {"workload": "2-D steady Euler, 15-degree ramp, 256 x 128 cells, 2 uniform dims, "
+                             "total degree 4 (15 x 4 moments), 5 x 5 nodes, One-Shot IPM (Algorithm 2); mixed "
+                             "runs towards residual 1e-8 (capped), FP64 times the first 200 steps",
+                             "unit": UNIT, **r}
+    # 2-D shear layer, adaptive degree 2..6, 7^3 nodes
+    w = workloads.variant(workloads.KH_2D, M=6, nq=7)
+    cells = w["nx"] * w["ny"]
+    r = {}
+    for prec in ("mixed", "fp64"):
+        ctx = gpu_context(w, precision=prec, adapt_min_degree=2, delta_lo=2e-5, delta_hi=2e-4)
+        ctx.set_stream(stream.cuda_stream)
+        n, secs, s = _timed_steps(ctx, args.kh_steps)
+        lev = ctx.get_levels().reshape(w["ny"] + 2, w["nx"] + 2)[1:-1, 1:-1]
+        r[prec] = {"value": cells * n / secs, "steps": n, "seconds": secs,
+                   "cells_per_degree": {str(2 + k): int(v) for k, v in enumerate(np.bincount(lev.ravel(), minlength=5))}}
+        ctx.close()
+    out["kh2d_adaptive"] = {"workload": f"2-D shear layer, 512 x 512 periodic, 3 uniform dims, adaptive total degree "
+                            f"2-6 (10-84 x 4 moments), 7^3 = 343 nodes, first {args.kh_steps} of the 200 steps",
+                            "unit": UNIT, **r}
+    return out
 
 
 # ------------------------------------------------------------------------------------------------
@@ -456,6 +541,9 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the Burgers / ramp / shear-layer runs")
+    ap.add_argument("--ramp-steps", type=int, default=1000, help="One-Shot step cap of the ramp workload")
+    ap.add_argument("--kh-steps", type=int, default=10, help="steps of the adaptive shear-layer workload")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-steps", type=int, default=10)
     ap.add_argument("--serving-slots", type=int, default=32)

@@ -155,6 +155,9 @@ typedef struct {
    * duals beyond a cell's degree are zero (graded ordering: a lower degree is a prefix). */
   int adapt_min_degree;
   double delta_lo, delta_hi;
+  /* Newton kernel: 0 = autotune (time each applicable variant on the initial state at ipm_init and
+   * keep the fastest), 1 = one CTA per cell, 2 = one warp per cell (cells with N*m <= 64, fixed degree) */
+  int newton_kernel;
 } ipm_options;
 
 /* Sizes of a context's arrays. */
@@ -217,6 +220,10 @@ ipm_status ipm_get_duals(ipm_ctx* ctx, double* host, size_t count);
 /* Nodal states u_s(lambda_j^T phi(xi_k)) at the current duals, laid out [cell][variable][node]
  * (count = n_cells*m*Q). Valid after ipm_dual_solve / ipm_step / ipm_oneshot_step. */
 ipm_status ipm_get_nodal_states(ipm_ctx* ctx, double* host, size_t count);
+
+/* The Newton kernel variant in use (1 = CTA per cell, 2 = warp per cell) and the times of one
+ * Newton solve on the initial state measured by the autotuner (0 for a variant not timed). */
+ipm_status ipm_get_tuning(const ipm_ctx* ctx, int* kernel, float* ms_cta, float* ms_warp);
 
 /* Adaptive contexts: the refinement level (index from adapt_min_degree) of every cell, count = n_cells. */
 ipm_status ipm_get_levels(ipm_ctx* ctx, int* host, size_t count);

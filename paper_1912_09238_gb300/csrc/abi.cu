@@ -50,6 +50,11 @@ struct ipm_ctx {
   uint8_t* d_phi_img = nullptr;
   size_t newton_smem = 0;
   bool h_in_smem = true;
+  // Newton kernel variant: 0 = one CTA per cell (newton.cu), 1 = one warp per cell (newton_warp.cu,
+  // N*m <= 64), picked at init by timing both on the initial state
+  int newton_kind = 0;
+  int warp_warps = 0, warp_slice = 0, warp_grid = 0;
+  float tune_ms[3] = {0.f, 0.f, 0.f};
   int newton_grid = 0;
   size_t hwork_stride = 0;
   int update_grid = 0;
@@ -204,6 +209,16 @@ static Update2DArgs update2d_args(const ipm_ctx* c, double dt_override, bool res
   return u;
 }
 
+// the Newton kernel of the context's chosen variant
+static cudaError_t launch_newton_ctx(const ipm_ctx* c, const NewtonArgs& a, int n_work, cudaStream_t s) {
+  if (c->newton_kind == 1) {
+    const int grid = std::max(1, std::min(c->warp_grid, (n_work + c->warp_warps - 1) / c->warp_warps));
+    return launch_newton_warp(c->entk, c->phys, c->m, c->mixed, a, grid, c->warp_warps, c->warp_slice, s);
+  }
+  return launch_newton_phys(c->entk, c->phys, c->m, a, std::max(1, std::min(c->newton_grid, n_work)), c->newton_smem,
+                            c->h_in_smem, c->mixed, s);
+}
+
 // enqueue: queue reset, Newton over the interior
 static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), s);
@@ -211,7 +226,7 @@ static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   NewtonArgs a = newton_args(c, one_step);
   a.cell_list = c->d_order;
-  return launch_newton_phys(c->entk, c->phys, c->m, a, c->newton_grid, c->newton_smem, c->h_in_smem, c->mixed, s);
+  return launch_newton_ctx(c, a, c->n_interior, s);
 }
 
 // one step of Algorithm 1 (one_step = 0) or Algorithm 2 (one_step = 1)
@@ -232,6 +247,52 @@ static cudaError_t enqueue_step(ipm_ctx* c, int one_step, cudaStream_t s) {
   if (e == cudaSuccess) e = launch_finalize(c->d_sc, c->d_iters, c->d_status, c->d_cell_resid, c->n_cells, first, count, 1, s);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal);
   return e;
+}
+
+// Time one Newton solve of the interior on the initial state with each applicable kernel variant
+// (the duals are restored after every trial) and keep the fastest. Ties go to the CTA kernel.
+static ipm_status autotune_newton(ipm_ctx* c) {
+  const size_t bytes = (size_t)c->n_cells * c->NM * sizeof(double);
+  double* saved = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  IPM_CK(c, cudaMalloc(&saved, bytes));
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(saved, c->d_lam, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  float best = 1e30f;
+  int best_kind = 0;
+  for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
+    c->newton_kind = kind;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms the kernel up
+      e = cudaMemcpyAsync(c->d_lam, saved, bytes, cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), c->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+      if (e == cudaSuccess) {
+        NewtonArgs a = newton_args(c, 0);
+        a.track_speed = 0;
+        e = launch_newton_ctx(c, a, c->n_interior, c->stream);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    c->tune_ms[kind] = ms;
+    if (e == cudaSuccess && ms < best * 0.97f) {
+      best = ms;
+      best_kind = kind;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_lam, saved, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_iters, 0, (size_t)c->n_cells * sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  c->newton_kind = best_kind;
+  cudaFree(saved);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  IPM_CK(c, e);
+  return IPM_OK;
 }
 
 static ipm_status build_graph(ipm_ctx* c, int one_step, cudaGraphExec_t* out) {
@@ -305,6 +366,7 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     return fail(nullptr, IPM_EINVAL, "ipm_init: periodic must be set on both ends");
   if (opt.precision != IPM_PREC_FP64 && opt.precision != IPM_PREC_MIXED)
     return fail(nullptr, IPM_EINVAL, "ipm_init: unknown precision");
+  if (opt.newton_kernel < 0 || opt.newton_kernel > 2) return fail(nullptr, IPM_EINVAL, "ipm_init: unknown Newton kernel");
   c->prob = *problem;
   c->basis = *basis;
   c->quad = *quad;
@@ -398,6 +460,20 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     if (c->mixed) bps = std::min(bps, 512 / c->mx.tmem_cols);
     c->newton_grid = std::max(1, std::min(c->n_interior, bps * prop.multiProcessorCount));
   }
+  // warp-per-cell variant for small cells: as many warps (cells) per CTA as shared memory allows
+  if (c->NM <= 64 && c->n_levels == 0) {
+    const size_t slice = newton_warp_slice(c->N, c->m, c->Q);
+    for (int wps = 8; wps >= 2; wps /= 2) {
+      if (wps * slice * sizeof(double) > budget) continue;
+      int bps = 0;
+      if (prepare_newton_warp(c->entk, c->phys, c->m, c->mixed, wps, (int)slice, &bps) == cudaSuccess && bps >= 1) {
+        c->warp_warps = wps;
+        c->warp_slice = (int)slice;
+        c->warp_grid = bps * prop.multiProcessorCount;
+        break;
+      }
+    }
+  }
   c->hwork_stride = c->h_in_smem ? 0 : packed_aug_count(c->NM);
   c->update_grid = std::min(c->n_interior, 65535);
   return IPM_OK;
@@ -428,6 +504,7 @@ void ipm_default_options(ipm_options* o) {
   o->adapt_min_degree = 0;
   o->delta_lo = 2e-5;
   o->delta_hi = 2e-4;
+  o->newton_kernel = 0;
 }
 
 const char* ipm_last_error(const ipm_ctx* c) {
@@ -564,9 +641,7 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
       NewtonArgs a = newton_args(c, 0);
       a.cell_list = c->d_ghost_list;
       a.n_work = (int)ghosts.size();
-      CK(launch_newton_phys(c->entk, c->phys, c->m, a, std::min(c->newton_grid, (int)ghosts.size()), c->newton_smem,
-                            c->h_in_smem, c->mixed, c->stream),
-         "ghost solve");
+      CK(launch_newton_ctx(c, a, (int)ghosts.size(), c->stream), "ghost solve");
     }
   }
   if (st == IPM_OK) {
@@ -590,6 +665,12 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
       // per-cell counters start from zero (the step reductions of 2-D meshes include the ghosts)
       CK(cudaMemset(c->d_iters, 0, (size_t)c->n_cells * sizeof(int)), "reset iters");
     }
+  }
+  if (st == IPM_OK && c->warp_warps > 0) {
+    if (c->opt.newton_kernel == 0) st = autotune_newton(c);
+    else c->newton_kind = c->opt.newton_kernel == 2 ? 1 : 0;
+  } else if (st == IPM_OK && c->opt.newton_kernel == 2) {
+    st = fail(nullptr, IPM_EINVAL, "ipm_init: the warp-per-cell kernel needs N*m <= 64 and a fixed degree");
   }
   if (st == IPM_OK) st = build_graph(c, 0, &c->step_exec);
   if (st == IPM_OK) st = build_graph(c, 1, &c->oneshot_exec);
@@ -654,6 +735,14 @@ ipm_status ipm_get_nodal_states(ipm_ctx* c, double* h, size_t n) {
   if (!c) return IPM_EINVAL;
   return copy_state(c, h, c->d_unode, n, (size_t)c->n_cells * c->m * c->Q, cudaMemcpyDeviceToHost, true);
 }
+ipm_status ipm_get_tuning(const ipm_ctx* c, int* kernel, float* ms_cta, float* ms_warp) {
+  if (!c) return IPM_EINVAL;
+  if (kernel) *kernel = c->newton_kind == 1 ? 2 : 1;
+  if (ms_cta) *ms_cta = c->tune_ms[0];
+  if (ms_warp) *ms_warp = c->tune_ms[1];
+  return IPM_OK;
+}
+
 ipm_status ipm_get_levels(ipm_ctx* c, int* h, size_t n) {
   if (!c || !h) return IPM_EINVAL;
   if (!c->n_levels) return fail(c, IPM_EINVAL, "ipm_get_levels: the context is not adaptive");

@@ -329,6 +329,25 @@ __device__ inline void atomic_max_pos(unsigned long long* addr, double v) {
   if (v > 0.0) atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
+// fastest signal speed of a nodal state: |u| (Burgers), max_d |v_d| + c (Euler)
+template <int PHYS, int M>
+__device__ __forceinline__ double node_speed(const double* u, double gamma);
+
+template <>
+__device__ __forceinline__ double node_speed<PHYS_BURGERS, 1>(const double* u, double) { return fabs(u[0]); }
+template <>
+__device__ __forceinline__ double node_speed<PHYS_EULER1D, 3>(const double* u, double g) {
+  const double v = u[1] / u[0];
+  const double p = (g - 1.0) * (u[2] - 0.5 * u[1] * v);
+  return fabs(v) + sqrt(g * p / u[0]);
+}
+template <>
+__device__ __forceinline__ double node_speed<PHYS_EULER2D, 4>(const double* u, double g) {
+  const double v1 = u[1] / u[0], v2 = u[2] / u[0];
+  const double p = (g - 1.0) * (u[3] - 0.5 * (u[1] * v1 + u[2] * v2));
+  return fmax(fabs(v1), fabs(v2)) + sqrt(g * p / u[0]);
+}
+
 __device__ inline double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

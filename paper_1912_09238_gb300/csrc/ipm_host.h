@@ -73,6 +73,11 @@ int newton_threads();
 cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, int grid, size_t smem, bool h_in_smem,
                                bool mixed, cudaStream_t s);
 cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, bool mixed, int* blocks_per_sm);
+// warp-per-cell Newton kernel for small cells (newton_warp.cu)
+size_t newton_warp_slice(int N, int m, int Q);
+cudaError_t prepare_newton_warp(int ent, int phys, int m, bool mixed, int warps, int slice, int* blocks_per_sm);
+cudaError_t launch_newton_warp(int ent, int phys, int m, bool mixed, const NewtonArgs& a, int grid, int warps, int slice,
+                               cudaStream_t s);
 cudaError_t launch_order(const int* iters, int n_work, int nx, int gy, int* order, cudaStream_t s);
 cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayout& L, float* phiT32, uint8_t* img,
                               cudaStream_t s);

@@ -56,24 +56,6 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* s_red) {
   __syncthreads();
 }
 
-template <int PHYS, int M>
-__device__ __forceinline__ double node_speed(const double* u, double gamma);
-
-template <>
-__device__ __forceinline__ double node_speed<PHYS_BURGERS, 1>(const double* u, double) { return fabs(u[0]); }
-template <>
-__device__ __forceinline__ double node_speed<PHYS_EULER1D, 3>(const double* u, double g) {
-  const double v = u[1] / u[0];
-  const double p = (g - 1.0) * (u[2] - 0.5 * u[1] * v);
-  return fabs(v) + sqrt(g * p / u[0]);
-}
-template <>
-__device__ __forceinline__ double node_speed<PHYS_EULER2D, 4>(const double* u, double g) {
-  const double v1 = u[1] / u[0], v2 = u[2] / u[0];
-  const double p = (g - 1.0) * (u[3] - 0.5 * (u[1] * v1 + u[2] * v2));
-  return fmax(fabs(v1), fabs(v2)) + sqrt(g * p / u[0]);
-}
-
 // (a, b) of the packed index ab (a <= b)
 template <int M>
 __device__ __forceinline__ void unpack_ab(int ab, int& a, int& b) {

@@ -50,7 +50,8 @@ class ipm_entropy(ctypes.Structure):
 class ipm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("newton_tol", ctypes.c_double), ("max_newton", ctypes.c_int),
                 ("armijo_c", ctypes.c_double), ("max_halvings", ctypes.c_int), ("slack_rel", ctypes.c_double),
-                ("adapt_min_degree", ctypes.c_int), ("delta_lo", ctypes.c_double), ("delta_hi", ctypes.c_double)]
+                ("adapt_min_degree", ctypes.c_int), ("delta_lo", ctypes.c_double), ("delta_hi", ctypes.c_double),
+                ("newton_kernel", ctypes.c_int)]
 
 
 class ipm_dims(ctypes.Structure):
@@ -105,6 +106,7 @@ SIGNATURES = [
     ("ipm_get_duals", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
     ("ipm_get_nodal_states", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
     ("ipm_get_levels", ctypes.c_int, [_vp, _P(ctypes.c_int), ctypes.c_size_t]),
+    ("ipm_get_tuning", ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_float), _P(ctypes.c_float)]),
     ("ipm_set_moments_device", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("ipm_get_moments_device", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("ipm_dual_solve", ctypes.c_int, [_vp, _P(ipm_stats)]),
@@ -288,6 +290,12 @@ class Context:
     def get_nodal_states(self):
         d = self.dims
         return self._get("ipm_get_nodal_states", (d.n_cells, d.m, d.Q))
+
+    def tuning(self):
+        """(kernel variant 1 = CTA per cell / 2 = warp per cell, ms of the CTA trial, ms of the warp trial)."""
+        k, a, b = ctypes.c_int(), ctypes.c_float(), ctypes.c_float()
+        _check("ipm_get_tuning", lib().ipm_get_tuning(self.h, ctypes.byref(k), ctypes.byref(a), ctypes.byref(b)), self.h)
+        return k.value, a.value, b.value
 
     def get_levels(self):
         out = np.empty(self.dims.n_cells, dtype=np.int32)
