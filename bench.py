@@ -137,6 +137,19 @@ def hessian_tc_flops(N, m, Q, iters):
     return iters * 3 * 2.0 * tiles * 128 * n_pad * q_pad
 
 
+def aggregate_throughput(local_seconds, units_per_rank, ws, device):
+    """Whole-job throughput of weakly scaled replicas: every rank processed units_per_rank in
+    local_seconds; the job took the slowest rank's time. Returns (units/s over all ranks, max seconds)."""
+    secs = float(local_seconds)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([secs], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    return ws * units_per_rank / secs, secs
+
+
 # ------------------------------------------------------------------------------------------------
 def measure(args, precision, flush, stream, barrier, ws):
     """W warm-up + K timed Algorithm-1 steps of one precision; returns (summary dict, context)."""
@@ -170,15 +183,11 @@ def measure(args, precision, flush, stream, barrier, ws):
     barrier()
     cl = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
     cells = d.n_interior
+    value, _ = aggregate_throughput(sum(step_ms) / 1e3, cells * args.steps, ws, "cuda")
     flops = [newton_fp64_flops(d.N, d.m, d.Q, cells, it, precision == "fp64") for it in iters]
     newton_s = statistics.mean(newton_ms) / 1e3
-    out = {"value": ws * cells * args.steps / total_s, "ms_per_step": statistics.mean(step_ms),
+    out = {"value": value, "ms_per_step": statistics.mean(step_ms),
            "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
            "newton_ms_mean": statistics.mean(newton_ms), "newton_share_of_step": sum(newton_ms) / sum(step_ms),
            "fp64_flops_per_launch": sum(flops) / len(flops),
@@ -258,13 +267,9 @@ def run_gpu(args):
         hu[...] = ctx.get_moments()
         hl[...] = ctx.get_duals()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_value, _ = aggregate_throughput(time.perf_counter() - t0, cells * e2e_steps, ws, "cuda")
     nbytes = int(np.prod(shape)) * 8
-    e2e = {"value": ws * cells * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
            "d2h_bytes_per_step": 2 * nbytes, "api": "ipm_set_moments + ipm_set_duals + ipm_step + "
            "ipm_get_moments + ipm_get_duals (host buffers, pinned)"}
 

@@ -1,0 +1,60 @@
+"""The multi-GPU form of bench.py is weakly scaled replicas (no data-path collective): two gloo
+ranks on the CPU check the max-over-ranks timing and the whole-job throughput, and that only rank 0
+runs and prints the reference arm."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    secs = [2.0, 5.0][rank]                                   # rank 1 is the slow one
+    value, tmax = bench.aggregate_throughput(secs, 1000, ws, "cpu")
+    q.put((rank, value, tmax, bench.dist_env()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_rank_time():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert all(p.exitcode == 0 for p in procs)
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, value, tmax, env in got:
+        assert tmax == 5.0
+        assert value == pytest.approx(2 * 1000 / 5.0)
+        assert env == (2, rank, rank)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+
+    class A:
+        warmup, steps = 3, 1
+    bench.run_reference(A())                                   # rank 1: no work, no output
+    assert capsys.readouterr().out == ""
