@@ -156,7 +156,9 @@ typedef struct {
   int adapt_min_degree;
   double delta_lo, delta_hi;
   /* Newton kernel: 0 = autotune (time each applicable variant on the initial state at ipm_init and
-   * keep the fastest), 1 = one CTA per cell, 2 = one warp per cell (cells with N*m <= 64, fixed degree) */
+   * keep the fastest; the decision is remembered for the process, per problem shape, so equal shapes
+   * always run the same variant), 1 = one CTA per cell, 2 = one warp per cell (cells with N*m <= 64,
+   * fixed degree) */
   int newton_kernel;
 } ipm_options;
 
@@ -220,6 +222,19 @@ ipm_status ipm_get_duals(ipm_ctx* ctx, double* host, size_t count);
 /* Nodal states u_s(lambda_j^T phi(xi_k)) at the current duals, laid out [cell][variable][node]
  * (count = n_cells*m*Q). Valid after ipm_dual_solve / ipm_step / ipm_oneshot_step. */
 ipm_status ipm_get_nodal_states(ipm_ctx* ctx, double* host, size_t count);
+
+/* Adaptive contexts, Algorithm 4 (refinement retardation, Sec. 5): from now on no interior cell may go
+ * above level max_level (index from adapt_min_degree); cells above it are lowered at once (moments and
+ * duals beyond it set to zero). Dirichlet ghosts keep their initial levels. */
+ipm_status ipm_set_max_level(ipm_ctx* ctx, int max_level);
+
+/* Algorithm 4 (adaptive One-Shot IPM with refinement retardation) on an adaptive context: stage l
+ * allows levels up to max_levels[l]; One-Shot pseudo-time steps (ipm_oneshot_step) run until the steady
+ * residual (Eq. residualSteady) falls below tolerances[l], then the next stage begins; in the last
+ * stage the run stops at residual tol. At most max_steps steps; *stats holds the last step's counters
+ * and stats->steps the steps taken so far. Synchronous (reads the residual after every step). */
+ipm_status ipm_oneshot_retarded(ipm_ctx* ctx, const int* max_levels, const double* tolerances, int n_stages,
+                                double tol, int64_t max_steps, ipm_stats* stats);
 
 /* The Newton kernel variant in use (1 = CTA per cell, 2 = warp per cell) and the times of one
  * Newton solve on the initial state measured by the autotuner (0 for a variant not timed). */

@@ -107,8 +107,8 @@ class AdaptiveState:
 
 
 def initial_state(prob: s2.Problem2D, lv: Levels) -> AdaptiveState:
-    """Finest projection, levels lowered while the indicator is below delta_-, then truncated.
-    Periodic sides only (the ghost cells are never read)."""
+    """Finest projection, levels lowered while the indicator is below delta_-, then truncated; every
+    cell, ghosts included, gets a level. Dirichlet ghosts then converge their duals at their level."""
     st = s2.initial_state(prob)
     nl, nprev = level_sizes(prob.space, lv)
     level = np.full(st.uhat.shape[:2], len(nl) - 1, dtype=np.int64)
@@ -116,7 +116,18 @@ def initial_state(prob: s2.Problem2D, lv: Levels) -> AdaptiveState:
     for _ in range(len(nl)):
         S = _indicator_levels(st.uhat, level, nl, nprev)
         level = np.where((S < lo) & (level > 0), level - 1, level)
-    return AdaptiveState(uhat=truncate(st.uhat, level, nl), lam=truncate(st.lam, level, nl), level=level)
+    out = AdaptiveState(uhat=truncate(st.uhat, level, nl), lam=truncate(st.lam, level, nl), level=level)
+    d = s2._dirichlet_mask(prob)
+    for l, n in enumerate(nl):
+        sel = np.nonzero(d & (level == l))
+        if sel[0].size:
+            li, _, stat, _ = dualmod.dual_solve(SubSpace(prob.space, n), prob.ent, out.lam[sel][:, :n],
+                                                out.uhat[sel][:, :n], prob.newton)
+            assert np.all(stat == 0)
+            lam_sel = out.lam[sel]
+            lam_sel[:, :n] = li
+            out.lam[sel] = lam_sel
+    return out
 
 
 def ipm_step(prob: s2.Problem2D, st: AdaptiveState, lv: Levels) -> AdaptiveState:
@@ -149,3 +160,68 @@ def ipm_step(prob: s2.Problem2D, st: AdaptiveState, lv: Levels) -> AdaptiveState
     res = s2.steady_residual(prob, uhat, st.uhat)
     return AdaptiveState(uhat=uhat, lam=lam_next, level=level, t=st.t + dt, n=st.n + 1, last_dt=dt,
                          newton_iters=it, newton_status=stat, residual=res)
+
+
+def cap_levels(st: AdaptiveState, cap: int, nl) -> AdaptiveState:
+    """Lower every interior level above cap to cap and truncate its moments and duals (the ghost cells
+    keep their initial levels)."""
+    level = st.level.copy()
+    level[1:-1, 1:-1] = np.minimum(level[1:-1, 1:-1], cap)
+    return AdaptiveState(uhat=truncate(st.uhat, level, nl), lam=truncate(st.lam, level, nl), level=level, t=st.t,
+                         n=st.n, last_dt=st.last_dt, residual=st.residual)
+
+
+def oneshot_step(prob: s2.Problem2D, st: AdaptiveState, lv: Levels, cap: int) -> AdaptiveState:
+    """One pseudo-time step of Algorithm 4 (adaptive One-Shot IPM): one damped Newton step per interior
+    cell at its level l^n (Eq. dualIterationFunctionAd), new levels from u_hat^n limited by the current
+    maximal level cap, moment update projected onto the new levels, steady residual.
+
+    Reading: Algorithm 4 prints max{DetermineRefinementLevel, l*_l}; the text describes l*_l as the
+    maximal refinement level of the current stage, so the level is min{DetermineRefinementLevel, l*_l}."""
+    nl, nprev = level_sizes(prob.space, lv)
+    ny, nx = prob.mesh.ny, prob.mesh.nx
+    lam = st.lam.copy()
+    it = np.zeros((ny, nx), dtype=np.int64)
+    stat = np.zeros((ny, nx), dtype=np.int64)
+    inner_level = st.level[1:-1, 1:-1]
+    for l, n in enumerate(nl):
+        sel = np.nonzero(inner_level == l)
+        if sel[0].size == 0:
+            continue
+        sub = SubSpace(prob.space, n)
+        jj, ii = sel[0] + 1, sel[1] + 1
+        li, itl, sl, _ = dualmod.dual_solve(sub, prob.ent, st.lam[jj, ii, :n], st.uhat[jj, ii, :n], prob.newton,
+                                            one_step=True)
+        lam[jj, ii, :n] = li
+        it[sel] = itl
+        stat[sel] = sl
+    level = st.level.copy()
+    new, _ = new_levels(st.uhat[1:-1, 1:-1], inner_level, nl, nprev, lv)
+    level[1:-1, 1:-1] = np.minimum(new, cap)
+    U = s2.nodal_states(prob, lam)
+    dt = s2.time_step(prob, U, st.t, clip=False)
+    uhat = st.uhat.copy()
+    uhat[1:-1, 1:-1] = truncate(s2.moment_update(prob, lam, dt), level[1:-1, 1:-1], nl)
+    lam_next = lam.copy()
+    lam_next[1:-1, 1:-1] = truncate(lam[1:-1, 1:-1], level[1:-1, 1:-1], nl)
+    res = s2.steady_residual(prob, uhat, st.uhat)
+    return AdaptiveState(uhat=uhat, lam=lam_next, level=level, t=st.t + dt, n=st.n + 1, last_dt=dt,
+                         newton_iters=it, newton_status=stat, residual=res)
+
+
+def oneshot_retarded(prob: s2.Problem2D, lv: Levels, caps, tolerances, tol, max_steps):
+    """Algorithm 4: refinement retardation. Stage l allows levels up to caps[l]; the stage advances when
+    the steady residual falls below tolerances[l]; the run stops at residual tol (once the last stage
+    is reached) or after max_steps. Returns (state, [(step, residual, stage)])."""
+    nl, _ = level_sizes(prob.space, lv)
+    stage = 0
+    st = cap_levels(initial_state(prob, lv), caps[0], nl)
+    hist = []
+    while st.n < max_steps:
+        st = oneshot_step(prob, st, lv, caps[stage])
+        hist.append((st.n, st.residual, stage))
+        if stage + 1 < len(caps) and st.residual < tolerances[stage]:
+            stage += 1
+        elif stage + 1 == len(caps) and st.residual < tol:
+            break
+    return st, hist

@@ -7,7 +7,9 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -249,9 +251,36 @@ static cudaError_t enqueue_step(ipm_ctx* c, int one_step, cudaStream_t s) {
   return e;
 }
 
+// Process-wide record of tuning decisions, keyed by everything that shapes the Newton launch: a
+// problem of the same shape reuses the first decision, so its results do not depend on the load the
+// GPU happened to carry when it was tuned (and serving does not re-tune every request).
+struct TuneKey {
+  int kind, entk, N, m, Q, mixed, n_interior;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(kind, entk, N, m, Q, mixed, n_interior) < std::tie(o.kind, o.entk, o.N, o.m, o.Q, o.mixed, o.n_interior);
+  }
+};
+struct TuneVal {
+  int kind;
+  float ms[2];
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneVal> g_tune;
+
 // Time one Newton solve of the interior on the initial state with each applicable kernel variant
 // (the duals are restored after every trial) and keep the fastest. Ties go to the CTA kernel.
 static ipm_status autotune_newton(ipm_ctx* c) {
+  const TuneKey key{c->prob.kind, c->entk, c->N, c->m, c->Q, c->mixed ? 1 : 0, c->n_interior};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      c->newton_kind = it->second.kind;
+      c->tune_ms[0] = it->second.ms[0];
+      c->tune_ms[1] = it->second.ms[1];
+      return IPM_OK;
+    }
+  }
   const size_t bytes = (size_t)c->n_cells * c->NM * sizeof(double);
   double* saved = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -288,6 +317,10 @@ static ipm_status autotune_newton(ipm_ctx* c) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_iters, 0, (size_t)c->n_cells * sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   c->newton_kind = best_kind;
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.emplace(key, TuneVal{best_kind, {c->tune_ms[0], c->tune_ms[1]}});
+  }
   cudaFree(saved);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -656,6 +689,7 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
       for (int g : ghosts)
         if (status[g] != 0) st = fail(nullptr, IPM_EINVAL, "ipm_init: Dirichlet ghost dual solve failed");
       h.fixed_smax_bits = h.smax_bits;
+      h.level_cap = c->n_levels ? c->n_levels - 1 : 0;
       h.work_counter = 0;
       h.update_counter = 0;
       h.t = 0.0;
@@ -735,6 +769,40 @@ ipm_status ipm_get_nodal_states(ipm_ctx* c, double* h, size_t n) {
   if (!c) return IPM_EINVAL;
   return copy_state(c, h, c->d_unode, n, (size_t)c->n_cells * c->m * c->Q, cudaMemcpyDeviceToHost, true);
 }
+ipm_status ipm_set_max_level(ipm_ctx* c, int max_level) {
+  if (!c) return IPM_EINVAL;
+  if (!c->n_levels) return fail(c, IPM_EINVAL, "ipm_set_max_level: the context is not adaptive");
+  if (max_level < 0 || max_level >= c->n_levels) return fail(c, IPM_EINVAL, "ipm_set_max_level: level out of range");
+  IPM_CK(c, cudaMemcpyAsync(&c->d_sc->level_cap, &max_level, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  IPM_CK(c, launch_cap_levels(update2d_args(c, 0.0, false, false), max_level, c->stream));
+  IPM_CK(c, cudaStreamSynchronize(c->stream));
+  return IPM_OK;
+}
+
+ipm_status ipm_oneshot_retarded(ipm_ctx* c, const int* max_levels, const double* tolerances, int n_stages, double tol,
+                                int64_t max_steps, ipm_stats* s) {
+  if (!c || !max_levels || n_stages < 1 || (n_stages > 1 && !tolerances)) return IPM_EINVAL;
+  int stage = 0;
+  ipm_status st = ipm_set_max_level(c, max_levels[0]);
+  if (st != IPM_OK) return st;
+  ipm_stats cur;
+  std::memset(&cur, 0, sizeof(cur));
+  for (int64_t n = 0; n < max_steps; ++n) {
+    st = ipm_oneshot_step(c, &cur);
+    if (st != IPM_OK) return st;
+    if (cur.failed_cells) break;
+    if (stage + 1 < n_stages && cur.residual < tolerances[stage]) {
+      ++stage;
+      st = ipm_set_max_level(c, max_levels[stage]);
+      if (st != IPM_OK) return st;
+    } else if (stage + 1 == n_stages && cur.residual < tol) {
+      break;
+    }
+  }
+  if (s) *s = cur;
+  return IPM_OK;
+}
+
 ipm_status ipm_get_tuning(const ipm_ctx* c, int* kernel, float* ms_cta, float* ms_warp) {
   if (!c) return IPM_EINVAL;
   if (kernel) *kernel = c->newton_kind == 1 ? 2 : 1;

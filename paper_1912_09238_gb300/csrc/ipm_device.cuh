@@ -240,6 +240,7 @@ struct StepScalars {
   int first_failed_cell;
   int first_status;
   int tc_timeouts;               // bounded tensor-core / bulk-copy waits that ran out (mixed path)
+  int level_cap;                 // adaptive meshes: highest level the update may assign (Algorithm 4 stages)
 };
 
 // Mixed-precision Hessian (tensor cores): tiling of H_ab = Phi^T diag(w J_ab) Phi as MMAs with

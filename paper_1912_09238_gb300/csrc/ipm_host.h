@@ -90,6 +90,7 @@ cudaError_t launch_finalize(StepScalars* sc, const int* iters, const int* status
 cudaError_t prepare_update2d(int Q);
 cudaError_t launch_update2d(const Update2DArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_init_levels(const Update2DArgs& a, int n_cells, cudaStream_t s);
+cudaError_t launch_cap_levels(const Update2DArgs& a, int cap, cudaStream_t s);
 cudaError_t launch_init2d(int ent, const Tables& tab, const EntParams& ent_p, const ipm_problem& prob, double* uhat,
                           double* lam, cudaStream_t s);
 cudaError_t launch_bc_copy1d(double* uhat, double* lam, int nx, int Nm, int bc_left, int bc_right,

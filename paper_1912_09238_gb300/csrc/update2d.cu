@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
       tot = warp_sum(tot);
       const double S = top / tot;
       lev_new = S < a.delta_lo ? lev - 1 : (S > a.delta_hi ? lev + 1 : lev);
-      lev_new = min(max(lev_new, 0), a.n_levels - 1);
+      lev_new = min(max(lev_new, 0), min(a.n_levels - 1, a.sc->level_cap));
       n_new = a.lev_n[lev_new];
     }
     __syncthreads();
@@ -214,6 +214,31 @@ __global__ void k_init_levels(Update2DArgs a, int n_cells) {
     a.lam[(size_t)c * NM + r] = 0.0;
   }
   if (lane == 0) a.level[c] = lev;
+}
+
+// Lower every interior level above cap to cap and zero the moments and duals beyond it (Algorithm 4:
+// the maximal level of a retardation stage). One warp per interior cell.
+__global__ void k_cap_levels(Update2DArgs a, int cap) {
+  constexpr int M = 4;
+  const int N = a.tab.N, NM = N * M, nx = a.mesh.nx, ny = a.mesh.ny;
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (w >= nx * ny) return;
+  const int c = cell2d(w % nx, w / nx, nx);
+  const int lev = a.level[c];
+  if (lev <= cap) return;
+  const int n = a.lev_n[cap];
+  for (int r = n * M + lane; r < NM; r += 32) {
+    a.uhat[(size_t)c * NM + r] = 0.0;
+    a.lam[(size_t)c * NM + r] = 0.0;
+  }
+  if (lane == 0) a.level[c] = cap;
+}
+
+cudaError_t launch_cap_levels(const Update2DArgs& a, int cap, cudaStream_t s) {
+  const int n = a.mesh.nx * a.mesh.ny;
+  k_cap_levels<<<(n + 7) / 8, 256, 0, s>>>(a, cap);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_init_levels(const Update2DArgs& a, int n_cells, cudaStream_t s) {

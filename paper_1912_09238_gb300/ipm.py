@@ -107,6 +107,9 @@ SIGNATURES = [
     ("ipm_get_nodal_states", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
     ("ipm_get_levels", ctypes.c_int, [_vp, _P(ctypes.c_int), ctypes.c_size_t]),
     ("ipm_get_tuning", ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_float), _P(ctypes.c_float)]),
+    ("ipm_set_max_level", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("ipm_oneshot_retarded", ctypes.c_int, [_vp, _P(ctypes.c_int), _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                            _P(ipm_stats)]),
     ("ipm_set_moments_device", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("ipm_get_moments_device", ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     ("ipm_dual_solve", ctypes.c_int, [_vp, _P(ipm_stats)]),
@@ -290,6 +293,18 @@ class Context:
     def get_nodal_states(self):
         d = self.dims
         return self._get("ipm_get_nodal_states", (d.n_cells, d.m, d.Q))
+
+    def set_max_level(self, level):
+        _check("ipm_set_max_level", lib().ipm_set_max_level(self.h, level), self.h)
+
+    def oneshot_retarded(self, max_levels, tolerances, tol, max_steps):
+        """Algorithm 4; returns the ipm_stats of the last step."""
+        lv = (ctypes.c_int * len(max_levels))(*max_levels)
+        tl = (ctypes.c_double * max(1, len(tolerances)))(*tolerances)
+        s = ipm_stats()
+        _check("ipm_oneshot_retarded", lib().ipm_oneshot_retarded(self.h, lv, tl, len(max_levels), tol, max_steps,
+                                                                  ctypes.byref(s)), self.h)
+        return s
 
     def tuning(self):
         """(kernel variant 1 = CTA per cell / 2 = warp per cell, ms of the CTA trial, ms of the warp trial)."""

@@ -58,3 +58,19 @@ def test_adaptive_rejects_1d_and_bad_ranges():
         gpu_context(workloads.variant(workloads.BURGERS_1D, nx=10), adapt_min_degree=2)
     with pytest.raises(ipm.IpmError):
         gpu_context(KH, adapt_min_degree=5)       # above the basis degree
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_retarded_adaptive_oneshot_matches_the_oracle(precision):
+    """Algorithm 4 on a coarse ramp mesh: stages, levels, steps and moments as the oracle."""
+    w = workloads.variant(workloads.RAMP_2D, nx=10, ny=5, M=4, nq=5)
+    prob = oracle_problem_2d(w)
+    lv = ad.Levels(degrees=(2, 3, 4), delta_lo=1e-10, delta_hi=1e-8)
+    st, hist = ad.oneshot_retarded(prob, lv, caps=(0, 2), tolerances=(2e-3,), tol=1e-9, max_steps=40)
+    ctx = gpu_context(w, precision=precision, adapt_min_degree=2, delta_lo=1e-10, delta_hi=1e-8)
+    s = ctx.oneshot_retarded([0, 2], [2e-3], 1e-9, 40)
+    assert s.failed_cells == 0
+    assert s.steps == st.n
+    assert np.array_equal(_grid(ctx.get_levels(), w)[1:-1, 1:-1], st.level[1:-1, 1:-1])
+    tol = 1e-10 if precision == "fp64" else 1e-6
+    assert rel_err(_grid(ctx.get_moments(), w)[1:-1, 1:-1], st.uhat[1:-1, 1:-1]) < tol

@@ -76,3 +76,35 @@ def test_levels_change_and_moments_beyond_the_level_stay_zero_and_means_are_cons
         tot0 = np.sum(A[..., None] * old.uhat[1:-1, 1:-1, 0, :], axis=(0, 1))
         assert np.abs(tot - tot0).max() < 1e-9
     assert len(seen) >= 2
+
+
+def test_retardation_caps_levels_then_releases_them():
+    """Algorithm 4 on a coarse ramp: the cap holds every level at the coarsest degree until the residual
+    passes the stage tolerance; afterwards finer levels appear; the residual keeps falling."""
+    w = workloads.variant(workloads.RAMP_2D, nx=10, ny=5, M=4, nq=5, sides=("dirichlet", "outflow", "slip", "dirichlet"))
+    prob = oracle_problem_2d(w)
+    lv = ad.Levels(degrees=(2, 3, 4), delta_lo=1e-10, delta_hi=1e-8)
+    st, hist = ad.oneshot_retarded(prob, lv, caps=(0, 2), tolerances=(2e-3,), tol=1e-9, max_steps=60)
+    stages = [h[2] for h in hist]
+    assert stages[0] == 0 and stages[-1] == 1
+    first1 = stages.index(1)
+    assert hist[first1 - 1][1] < 2e-3 <= max(h[1] for h in hist[:first1 - 1] or [(0, 1.0, 0)])
+    assert st.level[1:-1, 1:-1].max() > 0                   # finer degrees once released
+    assert hist[-1][1] < hist[0][1]
+
+
+def test_oneshot_step_with_cap_zero_is_the_fixed_low_degree_oneshot():
+    w = workloads.variant(workloads.RAMP_2D, nx=8, ny=4, M=4, nq=5)
+    prob = oracle_problem_2d(w)
+    lv = ad.Levels(degrees=(2, 3, 4), delta_lo=2e-5, delta_hi=2e-4)
+    nl, _ = ad.level_sizes(prob.space, lv)
+    a = ad.cap_levels(ad.initial_state(prob, lv), 0, nl)
+    w2 = workloads.variant(w, M=2)
+    prob2 = oracle_problem_2d(w2)
+    f = s2.initial_state(prob2)
+    assert np.abs(a.uhat[..., :nl[0], :] - f.uhat).max() < 1e-14
+    for _ in range(3):
+        a = ad.oneshot_step(prob, a, lv, 0)
+        f = s2.oneshot_step(prob2, f)
+        assert np.abs(a.uhat[..., :nl[0], :] - f.uhat).max() < 1e-12
+        assert np.all(a.uhat[..., nl[0]:, :] == 0.0)
