@@ -291,6 +291,8 @@ def run_gpu(args):
         line["serving"] = serving_bench(args)
     if rank == 0 and not args.no_workloads:
         line["workloads"] = workloads_bench(args)
+    if rank == 0 and not args.no_workloads:
+        line["frozen_hessian"] = frozen_hessian_bench(args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -380,6 +382,36 @@ def workloads_bench(args):
     out["kh2d_adaptive"] = {"workload": f"2-D shear layer, 512 x 512 periodic, 3 uniform dims, adaptive total degree "
                             f"2-6 (10-84 x 4 moments), 7^3 = 343 nodes, first {args.kh_steps} of the 200 steps",
                             "unit": UNIT, **r}
+    return out
+
+
+def frozen_hessian_bench(args):
+    """The Sod workload with frozen Hessians (ipm_options.hessian_reuse 2: Cholesky factors kept per
+    cell across solves, reused while they converge): both precision paths, 5 warm-up + 30 timed steps."""
+    from paper_1912_09238_gb300 import workloads
+    from tests._cases import gpu_context
+    import torch
+    out = {"workload": "Sod (as the headline) with hessian_reuse = 2, reuse_ratio 0.5", "unit": UNIT}
+    stream = torch.cuda.current_stream()
+    for prec in ("mixed", "fp64"):
+        ctx = gpu_context(workloads.SOD_1D, precision=prec, hessian_reuse=2)
+        ctx.set_stream(stream.cuda_stream)
+        for _ in range(5):
+            ctx.step(sync=False)
+        it = fa = 0
+        n, secs, _ = 30, 0.0, None
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(n):
+            a.record(stream)
+            ctx.step(sync=False)
+            b.record(stream)
+            s = ctx.sync_stats()
+            secs += a.elapsed_time(b) / 1e3
+            it += s.newton_iters
+            fa += s.factorizations
+        out[prec] = {"value": workloads.SOD_1D["nx"] * n / secs, "ms_per_step": 1e3 * secs / n,
+                     "newton_updates_per_step": it / n, "factorizations_per_step": fa / n}
+        ctx.close()
     return out
 
 

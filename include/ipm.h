@@ -155,6 +155,15 @@ typedef struct {
    * duals beyond a cell's degree are zero (graded ordering: a lower degree is a prefix). */
   int adapt_min_degree;
   double delta_lo, delta_hi;
+  /* Frozen Hessians (the paper's outlook, Sec. 8: quasi-Newton / frozen Hessians): 0 = Newton (the
+   * paper's method); 1 = after the first update of a solve, keep using the last Cholesky factor while the
+   * previous step was a full step (alpha = 1) and reduced the stopping criterion by at least reuse_ratio,
+   * else refactorise; 2 = like 1, and the newest factor of every cell is kept between solves (device
+   * memory n_cells * (N*m(N*m+1)/2 + N*m) doubles, refused with IPM_EINVAL above a quarter of the free
+   * memory) and used for the first update of the next solve. The converged duals meet the same FP64
+   * criterion (Eq. tauCrit) as Newton's. Runs on the CTA-per-cell Newton kernel. */
+  int hessian_reuse;
+  double reuse_ratio;
   /* Newton kernel: 0 = autotune (time each applicable variant on the initial state at ipm_init and
    * keep the fastest; the decision is remembered for the process, per problem shape, so equal shapes
    * always run the same variant), 1 = one CTA per cell, 2 = one warp per cell (cells with N*m <= 64,
@@ -185,6 +194,8 @@ typedef struct {
   int64_t steps;            /* steps taken since ipm_init */
   int32_t tc_timeouts;      /* mixed path: bounded tensor-core / bulk-copy waits that ran out (0 normally;
                                the affected cells report IPM_ETIMEOUT) */
+  int64_t factorizations;   /* Cholesky factorisations of the last solve (equals newton_iters without
+                               frozen Hessians) */
 } ipm_stats;
 
 typedef struct ipm_ctx ipm_ctx;

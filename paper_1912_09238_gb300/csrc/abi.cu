@@ -32,6 +32,9 @@ struct ipm_ctx {
   int n_levels = 0;                 // adaptive: levels adapt_min_degree .. total_degree
   int lev_n[8] = {0}, lev_prev[8] = {0};
   int* d_level = nullptr;
+  double* d_factors = nullptr;      // hessian_reuse 2: kept Cholesky factors per cell
+  int* d_factor_valid = nullptr;
+  size_t factor_stride = 0;
   double *d_area = nullptr, *d_xf = nullptr, *d_yf = nullptr;
   int device = 0;
   cudaStream_t own_stream = nullptr;
@@ -142,6 +145,11 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.max_halvings = c->opt.max_halvings;
   a.track_speed = 1;
   a.h_dump = nullptr;
+  a.hessian_reuse = c->opt.hessian_reuse;
+  a.reuse_ratio = c->opt.reuse_ratio;
+  a.factor_store = c->d_factors;
+  a.factor_stride = c->factor_stride;
+  a.factor_valid = c->d_factor_valid;
   a.level = c->n_levels ? c->d_level : nullptr;
   for (int k = 0; k < 8; ++k) a.lev_n[k] = c->lev_n[k];
   a.mx.phi_img = c->d_phi_img;
@@ -352,7 +360,8 @@ static void free_ctx(ipm_ctx* c) {
   if (c->oneshot_exec) cudaGraphExecDestroy(c->oneshot_exec);
   void* ptrs[] = {c->d_Phi, c->d_PhiT, c->d_w, c->d_nodes, c->d_pairs, c->d_uhat, c->d_lam, c->d_unode,
                   c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc,
-                  c->d_phiT32, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf, c->d_level};
+                  c->d_phiT32, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf, c->d_level,
+                  c->d_factors, c->d_factor_valid};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -400,6 +409,8 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   if (opt.precision != IPM_PREC_FP64 && opt.precision != IPM_PREC_MIXED)
     return fail(nullptr, IPM_EINVAL, "ipm_init: unknown precision");
   if (opt.newton_kernel < 0 || opt.newton_kernel > 2) return fail(nullptr, IPM_EINVAL, "ipm_init: unknown Newton kernel");
+  if (opt.hessian_reuse < 0 || opt.hessian_reuse > 2 || !(opt.reuse_ratio > 0.0 && opt.reuse_ratio < 1.0))
+    return fail(nullptr, IPM_EINVAL, "ipm_init: hessian_reuse must be 0..2 with 0 < reuse_ratio < 1");
   c->prob = *problem;
   c->basis = *basis;
   c->quad = *quad;
@@ -426,6 +437,13 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   c->n_cells = c->is2d ? (problem->nx + 2) * (problem->ny + 2) : problem->nx + 2;
   c->dx = (problem->x_hi - problem->x_lo) / problem->nx;
   if (c->is2d) build_mesh2d(*problem, c->mesh2d);
+  if (opt.hessian_reuse == 2) {
+    c->factor_stride = (size_t)c->NM * (c->NM + 1) / 2 + c->NM;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess ||
+        (size_t)c->n_cells * c->factor_stride * sizeof(double) > free_b / 4)
+      return fail(nullptr, IPM_EINVAL, "ipm_init: kept factors (hessian_reuse 2) need more than a quarter of the free memory");
+  }
   if (opt.adapt_min_degree > 0) {
     if (!c->is2d) return fail(nullptr, IPM_EINVAL, "ipm_init: adaptivity is built for 2-D problems");
     const int L = basis->total_degree - opt.adapt_min_degree + 1;
@@ -494,7 +512,7 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     c->newton_grid = std::max(1, std::min(c->n_interior, bps * prop.multiProcessorCount));
   }
   // warp-per-cell variant for small cells: as many warps (cells) per CTA as shared memory allows
-  if (c->NM <= 64 && c->n_levels == 0) {
+  if (c->NM <= 64 && c->n_levels == 0 && opt.hessian_reuse == 0) {
     const size_t slice = newton_warp_slice(c->N, c->m, c->Q);
     for (int wps = 8; wps >= 2; wps /= 2) {
       if (wps * slice * sizeof(double) > budget) continue;
@@ -521,6 +539,7 @@ static size_t ctx_footprint(const ipm_ctx* c) {
   if (c->mixed) b += N * Q * 4 + (size_t)c->mx.chunks * c->mx.b_chunk_bytes;
   if (c->is2d) b += (c->mesh2d.area.size() + c->mesh2d.xf.size() + c->mesh2d.yf.size()) * 8;
   if (c->n_levels) b += nc * 4;
+  if (c->factor_stride) b += nc * (c->factor_stride * 8 + 4);
   return b;
 }
 
@@ -537,6 +556,8 @@ void ipm_default_options(ipm_options* o) {
   o->adapt_min_degree = 0;
   o->delta_lo = 2e-5;
   o->delta_hi = 2e-4;
+  o->hessian_reuse = 0;
+  o->reuse_ratio = 0.5;
   o->newton_kernel = 0;
 }
 
@@ -623,6 +644,11 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   CK(cudaMalloc(&c->d_order, (size_t)c->n_interior * sizeof(int)), "cudaMalloc order");
   CK(cudaMalloc(&c->d_sc, sizeof(StepScalars)), "cudaMalloc scalars");
   if (!c->h_in_smem) CK(cudaMalloc(&c->d_hwork, (size_t)c->newton_grid * c->hwork_stride * sizeof(double)), "cudaMalloc hwork");
+  if (c->factor_stride) {
+    CK(cudaMalloc(&c->d_factors, (size_t)c->n_cells * c->factor_stride * sizeof(double)), "cudaMalloc factors");
+    CK(cudaMalloc(&c->d_factor_valid, (size_t)c->n_cells * sizeof(int)), "cudaMalloc factor flags");
+    if (st == IPM_OK) CK(cudaMemsetAsync(c->d_factor_valid, 0, (size_t)c->n_cells * sizeof(int), c->stream), "memset factor flags");
+  }
   if (st != IPM_OK) {
     free_ctx(c);
     return st;
@@ -840,6 +866,7 @@ static void fill_stats(const StepScalars& h, ipm_stats* s) {
   s->residual = h.residual;
   s->steps = h.steps;
   s->tc_timeouts = h.tc_timeouts;
+  s->factorizations = (int64_t)h.last_factorizations;
 }
 
 ipm_status ipm_sync_stats(ipm_ctx* c, ipm_stats* s) {

@@ -241,6 +241,8 @@ struct StepScalars {
   int first_status;
   int tc_timeouts;               // bounded tensor-core / bulk-copy waits that ran out (mixed path)
   int level_cap;                 // adaptive meshes: highest level the update may assign (Algorithm 4 stages)
+  unsigned long long factorizations;       // Cholesky factorisations since the last reduction
+  unsigned long long last_factorizations;  // ... of the last solve (frozen-Hessian statistics)
 };
 
 // Mixed-precision Hessian (tensor cores): tiling of H_ab = Phi^T diag(w J_ab) Phi as MMAs with
@@ -276,6 +278,11 @@ struct NewtonArgs {
   int track_speed;       // 1: fold the nodal signal speeds of the result into sc->smax_bits
   double* h_dump;        // non-null: assemble the Hessian at the current duals, store it packed
                          // [work item][NM(NM+1)/2] and stop (no Newton update)
+  int hessian_reuse;     // 0: Newton; 1: reuse the factor within a solve; 2: also across solves
+  double reuse_ratio;    // reuse while the residual falls at least by this factor per full step
+  double* factor_store;  // hessian_reuse 2: [cell][NM(NM+1)/2 + NM] kept factor and reciprocal pivots
+  size_t factor_stride;
+  int* factor_valid;     // [cell]
   const int* level;      // adaptive meshes: refinement level per cell (nullptr: every cell at tab.N)
   int lev_n[8];          // moments per level (graded prefixes of the table's basis)
   MixedTiles mx;         // mixed path only

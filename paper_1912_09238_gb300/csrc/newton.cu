@@ -306,6 +306,38 @@ __device__ bool cholesky_aug(double* A, int n, double* s_P, double* s_dinv, int*
   return true;
 }
 
+// Forward substitution L y = b in place on x (x holds b on entry), blocks of NB from the top: one
+// warp solves the diagonal block (lane i holds entry kb + i), then all threads update the rows below.
+// Used when a stored factor is reused (the factorisation itself folds the forward solve in).
+__device__ void forward_substitute(const double* A, int n, const double* s_dinv, double* x) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int kb = 0; kb < n; kb += NB) {
+    const int kw = min(NB, n - kb);
+    if (tid < 32) {
+      double v = lane < kw ? x[kb + lane] : 0.0;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        if (k < kw) {
+          const double yk = __shfl_sync(0xffffffffu, v, k) * s_dinv[kb + k];
+          if (lane == k) v = yk;
+          if (lane > k && lane < kw) v = fma(-A[rowoff(kb + lane) + kb + k], yk, v);
+        }
+      }
+      if (lane < kw) x[kb + lane] = v;
+    }
+    __syncthreads();
+    for (int r = kb + kw + tid; r < n; r += NT) {
+      const size_t ro = rowoff(r) + kb;
+      double v = x[r];
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+        if (k < kw) v = fma(-A[ro + k], x[kb + k], v);
+      x[r] = v;
+    }
+    __syncthreads();
+  }
+}
+
 // Back substitution L^T x = b in place on x (x holds b on entry), blocks of NB from the bottom: one
 // warp solves the diagonal block (lane i holds entry kb + i), then all threads update the entries above.
 __device__ void back_substitute(const double* A, int n, const double* s_dinv, double* x) {
@@ -545,6 +577,18 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
     __syncthreads();
 
     int it = 0, st = ST_OK;
+    // frozen Hessians (hessian_reuse > 0): the Cholesky factor of an earlier iterate is kept and reused
+    // while the Newton steps it gives converge fast enough
+    bool have_factor = false;
+    int nfact = 0;
+    double res_prev = 0.0, alpha_prev = 0.0;
+    if (a.hessian_reuse == 2 && a.factor_valid[cell]) {
+      const double* fs = a.factor_store + (size_t)cell * a.factor_stride;
+      const size_t nph = (size_t)NM * (NM + 1) / 2;
+      for (size_t r = tid; r < nph; r += NT) s_H[r] = fs[r];
+      for (int r = tid; r < NM; r += NT) s_dinv[r] = fs[nph + r];
+      have_factor = true;
+    }
     for (;;) {
       // (a1) reconstruction
       for (int q = tid; q < Q; q += NT) {
@@ -625,6 +669,16 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
         }
       }
 
+      const bool reuse = have_factor && a.hessian_reuse > 0 && !a.h_dump &&
+                         (it == 0 ? a.hessian_reuse == 2 : (alpha_prev == 1.0 && res <= a.reuse_ratio * res_prev));
+      res_prev = res;
+      if (reuse) {
+        // chord step with the kept factor: L L^T Delta = -g
+        for (int r = tid; r < NM; r += NT) s_d[r] = -s_g[r];
+        __syncthreads();
+        forward_substitute(s_H, NM, s_dinv, s_d);
+        back_substitute(s_H, NM, s_dinv, s_d);
+      } else {
       // (b) Hessian, packed lower triangle, row index r = i*M + a
       if (MIXED) {
         if (!hessian_tc<M>(a, N, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, tcs, &s_abort)) {
@@ -648,9 +702,12 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       for (int r = tid; r < NM; r += NT) s_H[rowoff(NM) + r] = s_g[r];
       __syncthreads();
       if (!cholesky_aug(s_H, NM, s_P, s_dinv, &s_flag)) { st = ST_NOTSPD; break; }
+      have_factor = true;
+      ++nfact;
       for (int r = tid; r < NM; r += NT) s_d[r] = -s_H[rowoff(NM) + r];
       __syncthreads();
       back_substitute(s_H, NM, s_dinv, s_d);
+      }
       // direction at the nodes, slope, Delta . u_hat
       for (int q = tid; q < Q; q += NT) {
         double acc[M];
@@ -694,6 +751,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
         alpha *= 0.5;
       }
       if (!accepted) { st = ST_LINESEARCH; break; }
+      alpha_prev = alpha;
       for (int r = tid; r < NM; r += NT) s_lam[r] = fma(alpha, s_d[r], s_lam[r]);
       __syncthreads();
       ++it;
@@ -706,6 +764,15 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
     if (tid == 0) {
       a.iters[cell] = it;
       a.status[cell] = st;
+      if (nfact) atomicAdd(&a.sc->factorizations, (unsigned long long)nfact);
+    }
+    if (a.hessian_reuse == 2 && nfact > 0 && st == ST_OK) {
+      // keep the newest factor for the next solve of this cell
+      double* fs = a.factor_store + (size_t)cell * a.factor_stride;
+      const size_t nph = (size_t)NM * (NM + 1) / 2;
+      for (size_t r = tid; r < nph; r += NT) fs[r] = s_H[r];
+      for (int r = tid; r < NM; r += NT) fs[nph + r] = s_dinv[r];
+      if (tid == 0) a.factor_valid[cell] = 1;
     }
     if (a.track_speed) {
       double smax = 0.0;
