@@ -165,9 +165,9 @@ typedef struct {
   int hessian_reuse;
   double reuse_ratio;
   /* Newton kernel: 0 = autotune (time each applicable variant on the initial state at ipm_init and
-   * keep the fastest; the decision is remembered for the process, per problem shape, so equal shapes
-   * always run the same variant), 1 = one CTA per cell, 2 = one warp per cell (cells with N*m <= 64,
-   * fixed degree) */
+   * keep the fastest; the decision is remembered for the process, per problem shape (kind, entropy,
+   * N, m, Q, precision, power-of-two bucket of the interior cell count), so equal shapes always run
+   * the same variant), 1 = one CTA per cell, 2 = one warp per cell (cells with N*m <= 64, fixed degree) */
   int newton_kernel;
 } ipm_options;
 

@@ -263,9 +263,9 @@ static cudaError_t enqueue_step(ipm_ctx* c, int one_step, cudaStream_t s) {
 // problem of the same shape reuses the first decision, so its results do not depend on the load the
 // GPU happened to carry when it was tuned (and serving does not re-tune every request).
 struct TuneKey {
-  int kind, entk, N, m, Q, mixed, n_interior;
+  int kind, entk, N, m, Q, mixed, size_bucket;
   bool operator<(const TuneKey& o) const {
-    return std::tie(kind, entk, N, m, Q, mixed, n_interior) < std::tie(o.kind, o.entk, o.N, o.m, o.Q, o.mixed, o.n_interior);
+    return std::tie(kind, entk, N, m, Q, mixed, size_bucket) < std::tie(o.kind, o.entk, o.N, o.m, o.Q, o.mixed, o.size_bucket);
   }
 };
 struct TuneVal {
@@ -278,7 +278,10 @@ static std::map<TuneKey, TuneVal> g_tune;
 // Time one Newton solve of the interior on the initial state with each applicable kernel variant
 // (the duals are restored after every trial) and keep the fastest. Ties go to the CTA kernel.
 static ipm_status autotune_newton(ipm_ctx* c) {
-  const TuneKey key{c->prob.kind, c->entk, c->N, c->m, c->Q, c->mixed ? 1 : 0, c->n_interior};
+  // the interior size enters as its power-of-two bucket: meshes of similar size share a decision
+  int size_bucket = 0;
+  while ((1 << (size_bucket + 1)) <= c->n_interior) ++size_bucket;
+  const TuneKey key{c->prob.kind, c->entk, c->N, c->m, c->Q, c->mixed ? 1 : 0, size_bucket};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
