@@ -338,22 +338,24 @@ def workloads_bench(args):
     import torch
     out = {}
     stream = torch.cuda.current_stream()
+    only = getattr(args, "only", None)
     # 1-D Burgers (200 cells, N = 6, Q = 10), Algorithm 1 to t_end = 0.11
     w = workloads.BURGERS_1D
     r = {}
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "fp64") if only in (None, "burgers") else ():
         ctx = gpu_context(w, precision=prec)
         ctx.set_stream(stream.cuda_stream)
         n, secs, s = _timed_steps(ctx, 176)
         r[prec] = {"value": w["nx"] * n / secs, "steps": n, "t": s.t, "seconds": secs}
         ctx.close()
-    out["burgers1d"] = {"workload": "1-D Burgers IPM, 200 cells, N = 6, Q = 10, barrier entropy, to t_end = 0.11",
-                        "unit": UNIT, **r}
+    if r:
+        out["burgers1d"] = {"workload": "1-D Burgers IPM, 200 cells, N = 6, Q = 10, barrier entropy, to t_end = 0.11",
+                            "unit": UNIT, **r}
     # 2-D ramp, One-Shot towards residual 1e-8
     w = workloads.RAMP_2D
     cells = w["nx"] * w["ny"]
     r = {}
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "fp64") if only in (None, "ramp") else ():
         ctx = gpu_context(w, precision=prec)
         ctx.set_stream(stream.cuda_stream)
         cap = args.ramp_steps if prec == "mixed" else min(args.ramp_steps, 200)
@@ -363,15 +365,16 @@ def workloads_bench(args):
                    "newton_kernel": {1: "cta_per_cell", 2: "warp_per_cell"}[tune[0]],
                    "autotune_ms": {"cta_per_cell": tune[1], "warp_per_cell": tune[2]}}
         ctx.close()
-    out["ramp2d_oneshot"] = {"workload": "2-D steady Euler, 15-degree ramp, 256 x 128 cells, 2 uniform dims, "
-                             "total degree 4 (15 x 4 moments), 5 x 5 nodes, One-Shot IPM (Algorithm 2); mixed "
-                             "runs towards residual 1e-8 (capped), FP64 times the first 200 steps",
-                             "unit": UNIT, **r}
+    if r:
+        out["ramp2d_oneshot"] = {"workload": "2-D steady Euler, 15-degree ramp, 256 x 128 cells, 2 uniform dims, "
+                                 "total degree 4 (15 x 4 moments), 5 x 5 nodes, One-Shot IPM (Algorithm 2); mixed "
+                                 "runs towards residual 1e-8 (capped), FP64 times the first 200 steps",
+                                 "unit": UNIT, **r}
     # 2-D shear layer, adaptive degree 2..6, 7^3 nodes
     w = workloads.variant(workloads.KH_2D, M=6, nq=7)
     cells = w["nx"] * w["ny"]
     r = {}
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "fp64") if only in (None, "kh") else ():
         ctx = gpu_context(w, precision=prec, adapt_min_degree=2, delta_lo=2e-5, delta_hi=2e-4)
         ctx.set_stream(stream.cuda_stream)
         n, secs, s = _timed_steps(ctx, args.kh_steps)
@@ -379,9 +382,10 @@ def workloads_bench(args):
         r[prec] = {"value": cells * n / secs, "steps": n, "seconds": secs,
                    "cells_per_degree": {str(2 + k): int(v) for k, v in enumerate(np.bincount(lev.ravel(), minlength=5))}}
         ctx.close()
-    out["kh2d_adaptive"] = {"workload": f"2-D shear layer, 512 x 512 periodic, 3 uniform dims, adaptive total degree "
-                            f"2-6 (10-84 x 4 moments), 7^3 = 343 nodes, first {args.kh_steps} of the 200 steps",
-                            "unit": UNIT, **r}
+    if r:
+        out["kh2d_adaptive"] = {"workload": f"2-D shear layer, 512 x 512 periodic, 3 uniform dims, adaptive total degree "
+                                f"2-6 (10-84 x 4 moments), 7^3 = 343 nodes, first {args.kh_steps} of the 200 steps",
+                                "unit": UNIT, **r}
     return out
 
 
@@ -581,6 +585,8 @@ def main():
     ap.add_argument("--no-workloads", action="store_true", help="skip the Burgers / ramp / shear-layer runs")
     ap.add_argument("--ramp-steps", type=int, default=1000, help="One-Shot step cap of the ramp workload")
     ap.add_argument("--kh-steps", type=int, default=10, help="steps of the adaptive shear-layer workload")
+    ap.add_argument("--only", choices=["burgers", "ramp", "kh"], default=None,
+                    help="run only this workload's timing (no JSON bench line; for profiling)")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-steps", type=int, default=10)
     ap.add_argument("--serving-slots", type=int, default=32)
@@ -593,6 +599,13 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.only:
+        import torch
+        torch.cuda.set_device(0)
+        torch.cuda.set_stream(torch.cuda.Stream())
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(workloads_bench(args)), flush=True)
     else:
         run_gpu(args)
 

@@ -189,11 +189,16 @@ __global__ void __launch_bounds__(256) k_newton_warp(NewtonArgs a, int slice) {
         }
         for (int r = k + 1 + lane; r <= NM; r += 32) s_H[rowoff_w(r) + k] *= id;
         __syncwarp();
-        for (int r = k + 1 + lane; r <= NM; r += 32) {
-          const size_t ro = rowoff_w(r);
-          const double lrk = s_H[ro + k];
-          const int jmax = r < NM ? r : NM - 1;
-          for (int j = k + 1; j <= jmax; ++j) s_H[ro + j] = fma(-lrk, s_H[rowoff_w(j) + k], s_H[ro + j]);
+        // trailing update on an 8 x 4 lane grid (rows x columns), so that the lanes share the
+        // triangle evenly (a whole row per lane would leave most lanes idle on the short rows)
+        {
+          const int ly = lane >> 2, lx = lane & 3;
+          for (int r = k + 1 + ly; r <= NM; r += 8) {
+            const size_t ro = rowoff_w(r);
+            const double lrk = s_H[ro + k];
+            const int jmax = r < NM ? r : NM - 1;
+            for (int j = k + 1 + lx; j <= jmax; j += 4) s_H[ro + j] = fma(-lrk, s_H[rowoff_w(j) + k], s_H[ro + j]);
+          }
         }
         __syncwarp();
       }

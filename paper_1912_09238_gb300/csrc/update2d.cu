@@ -246,10 +246,132 @@ cudaError_t launch_init_levels(const Update2DArgs& a, int n_cells, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t prepare_update2d(int Q) { return raise_smem_limit(k_update2d, (size_t)4 * Q * sizeof(double)); }
+// The same update with one warp per cell (8 cells per CTA) for small node counts: lanes over nodes
+// for the fluxes, lanes over moments for the projection, no block barriers.
+constexpr int UPD_WARPS = 8;
+
+__global__ void __launch_bounds__(256) k_update2d_warp(Update2DArgs a) {
+  extern __shared__ __align__(16) double s_all[];
+  constexpr int M = 4;
+  const int N = a.tab.N, Q = a.tab.Q, NM = N * M;
+  const int nx = a.mesh.nx, ny = a.mesh.ny;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* s_v = s_all + (size_t)warp * M * Q;
+  double dt = a.dt_override;
+  if (!(dt > 0.0)) {
+    const double smax = __longlong_as_double((long long)a.sc->smax_bits);
+    dt = a.cfl * a.mesh.h_min / smax;
+    if (a.clip && a.t_end > 0.0 && a.sc->t + dt > a.t_end) dt = a.t_end - a.sc->t;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.sc->dt = dt > 0.0 ? dt : 0.0;
+  if (!(dt > 0.0)) return;
+  const double* __restrict__ w = a.tab.w;
+  const double* __restrict__ PhiT = a.tab.PhiT;
+  const int MQ = M * Q;
+  const double g = a.gamma;
+  for (int cidx = blockIdx.x * UPD_WARPS + warp; cidx < nx * ny; cidx += gridDim.x * UPD_WARPS) {
+    const int i = cidx % nx, j = cidx / nx;
+    const int c = cell2d(i, j, nx);
+    const double area = a.mesh.area[(size_t)j * nx + i];
+    const double* xl = a.mesh.xf + ((size_t)j * (nx + 1) + i) * 3;
+    const double* xr = xl + 3;
+    const double* yb = a.mesh.yf + ((size_t)j * nx + i) * 3;
+    const double* yt = a.mesh.yf + ((size_t)(j + 1) * nx + i) * 3;
+    const int nl = i > 0 ? cell2d(i - 1, j, nx) : outside(a.bc[0], cell2d(nx - 1, j, nx), cell2d(-1, j, nx));
+    const int nr = i < nx - 1 ? cell2d(i + 1, j, nx) : outside(a.bc[1], cell2d(0, j, nx), cell2d(nx, j, nx));
+    const int nb = j > 0 ? cell2d(i, j - 1, nx) : outside(a.bc[2], cell2d(i, ny - 1, nx), cell2d(i, -1, nx));
+    const int nt = j < ny - 1 ? cell2d(i, j + 1, nx) : outside(a.bc[3], cell2d(i, 0, nx), cell2d(i, ny, nx));
+    const double r = dt / area;
+    for (int q = lane; q < Q; q += 32) {
+      double uc[M], un[M], f[M], acc[M];
+      const double* ucg = a.unode + (size_t)c * MQ;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        uc[k] = ucg[k * Q + q];
+        acc[k] = 0.0;
+      }
+      const int nbr[4] = {nl, nr, nb, nt};
+      const double* fg[4] = {xl, xr, yb, yt};
+#pragma unroll
+      for (int fa = 0; fa < 4; ++fa) {
+        const double nxn = fg[fa][0], nyn = fg[fa][1], L = fg[fa][2];
+        const int o = nbr[fa];
+        if (o >= 0) {
+          const double* ug = a.unode + (size_t)o * MQ;
+#pragma unroll
+          for (int k = 0; k < M; ++k) un[k] = ug[k * Q + q];
+        } else if (o == -1) {
+#pragma unroll
+          for (int k = 0; k < M; ++k) un[k] = uc[k];
+        } else {
+          reflect(uc, nxn, nyn, un);
+        }
+        const bool ahead = (fa & 1) != 0;
+        if (ahead) rusanov2d(uc, un, nxn, nyn, g, f);
+        else rusanov2d(un, uc, nxn, nyn, g, f);
+        const double sL = ahead ? L : -L;
+#pragma unroll
+        for (int k = 0; k < M; ++k) acc[k] = fma(sL, f[k], acc[k]);
+      }
+      const double wq = w[q];
+#pragma unroll
+      for (int k = 0; k < M; ++k) s_v[k * Q + q] = wq * fma(-r, acc[k], uc[k]);
+    }
+    __syncwarp();
+    double* out = a.uhat + (size_t)c * NM;
+    const double old00 = out[0];
+    int n_new = N;
+    int lev_new = 0;
+    if (a.level) {
+      const int lev = a.level[c];
+      const int n_lev = a.lev_n[lev], n_prv = a.lev_prev[lev];
+      double top = 0.0, tot = 0.0;
+      for (int ii = lane; ii < n_lev; ii += 32) {
+        const double v = out[ii * M];
+        tot = fma(v, v, tot);
+        if (ii >= n_prv) top = fma(v, v, top);
+      }
+      top = warp_sum(top);
+      tot = warp_sum(tot);
+      const double S = top / tot;
+      lev_new = S < a.delta_lo ? lev - 1 : (S > a.delta_hi ? lev + 1 : lev);
+      lev_new = min(max(lev_new, 0), min(a.n_levels - 1, a.sc->level_cap));
+      n_new = a.lev_n[lev_new];
+    }
+    __syncwarp();
+    for (int rr = lane; rr < NM; rr += 32) {
+      const int ii = rr / M, k = rr - ii * M;
+      double v = 0.0;
+      if (ii < n_new) {
+        for (int q = 0; q < Q; ++q) v = fma(PhiT[(size_t)ii * Q + q], s_v[k * Q + q], v);
+      } else {
+        a.lam[(size_t)c * NM + rr] = 0.0;
+      }
+      out[rr] = v;
+    }
+    __syncwarp();
+    if (lane == 0 && a.cell_resid) a.cell_resid[c] = area * fabs(out[0] - old00);
+    if (lane == 0 && a.level) a.level[c] = lev_new;
+    __syncwarp();
+  }
+}
+
+// the warp variant when a warp's slice of node values is small; else one CTA per cell
+static bool update2d_use_warp(int Q) { return Q <= 64; }
+
+cudaError_t prepare_update2d(int Q) {
+  if (update2d_use_warp(Q)) return raise_smem_limit(k_update2d_warp, (size_t)UPD_WARPS * 4 * Q * sizeof(double));
+  return raise_smem_limit(k_update2d, (size_t)4 * Q * sizeof(double));
+}
 
 cudaError_t launch_update2d(const Update2DArgs& a, int grid, cudaStream_t s) {
-  k_update2d<<<grid, T2, (size_t)4 * a.tab.Q * sizeof(double), s>>>(a);
+  if (update2d_use_warp(a.tab.Q)) {
+    const int cells = a.mesh.nx * a.mesh.ny;
+    const int g = std::max(1, std::min((cells + UPD_WARPS - 1) / UPD_WARPS, 65535));
+    k_update2d_warp<<<g, 32 * UPD_WARPS, (size_t)UPD_WARPS * 4 * a.tab.Q * sizeof(double), s>>>(a);
+  } else {
+    k_update2d<<<grid, T2, (size_t)4 * a.tab.Q * sizeof(double), s>>>(a);
+  }
   return cudaGetLastError();
 }
 
