@@ -7,7 +7,8 @@
 One step = one call of ipm_step: the Newton solve of the dual problem in every cell, the CFL time
 step, the kinetic-flux moment update (one captured CUDA graph). The headline is the mixed-precision
 path (Hessian on the tensor cores, everything else FP64); the plain FP64 GPU path is timed on the
-same workload in the same run and reported beside it (--precision fp64 makes FP64 the headline).
+same workload in the same run and reported beside it (--precision fp64 makes FP64 the headline),
+and so is the FP32-factorisation mode (key "mixed_f32_factor").
 Prints one JSON line (rank 0).
 --impl reference times the CPU oracle on the host cores instead (each step a bounded sample).
 With torchrun (N > 1) every rank runs an independent replica of the workload on its own GPU
@@ -32,7 +33,7 @@ FP64_PEAK_TFLOPS = 1.25      # nominal dense FP64 of a GB300 (probe: 1.19 measur
 KERNELS_PER_STEP = 4         # k_order, k_newton, k_update1d, k_finalize (one CUDA graph per step)
 # dram__bytes_read.sum + dram__bytes_write.sum of one mixed-path k_newton launch on this workload,
 # from an ncu capture of the current kernel (a warm step); None for the FP64 kernel (no capture yet)
-NEWTON_TRAFFIC_BYTES = {"mixed": 6.02e6, "fp64": None}
+NEWTON_TRAFFIC_BYTES = {"mixed": 6.02e6, "fp64": None, "mixed_f32f": None}
 L2_FLUSH_BYTES = 512 << 20   # > 4x the 126 MiB L2
 WINDOW = dict(nx=200, x_lo=0.45, x_hi=0.55)   # same dx as the 2000-cell mesh, around the interface
 
@@ -193,7 +194,7 @@ def measure(args, precision, flush, stream, barrier, ws):
            "fp64_flops_per_launch": sum(flops) / len(flops),
            "fp64_tflops": (sum(flops) / len(flops)) / newton_s / 1e12,
            "newton_iters_per_step": statistics.mean(iters), "clocks": cl, "cells": cells, "dims": d}
-    if precision == "mixed":
+    if precision != "fp64":
         tcf = statistics.mean(hessian_tc_flops(d.N, d.m, d.Q, it) for it in iters)
         out["tensor_flops_per_launch"] = tcf
     return out, ctx
@@ -234,6 +235,12 @@ def run_gpu(args):
         # equal error: both paths ran the same steps from the same initial data
         a, b = ctx.get_moments(), rctx.get_moments()
         ref["max_rel_diff_moments_vs_mixed"] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+        # the FP32-factorisation mode on the same steps, against the FP64 path's moments
+        f32, fctx = measure(args, "mixed_f32f", flush, stream, barrier, ws)
+        c = fctx.get_moments()
+        f32["max_rel_diff_moments_vs_fp64"] = float(np.max(np.abs(c - b)) / np.max(np.abs(b)))
+        f32["fp32_fallbacks"] = fctx.sync_stats().fp32_fallbacks
+        fctx.close()
         rctx.close()
 
     roofline = {"bound": "alu", "kernel": "k_newton (fused dual solve: reconstruction, closure, gradient, "
@@ -287,6 +294,16 @@ def run_gpu(args):
                             "fp64_tflops": round(ref["fp64_tflops"], 4),
                             "max_rel_diff_moments_vs_mixed": ref["max_rel_diff_moments_vs_mixed"],
                             "speedup_mixed_over_fp64": main["value"] / ref["value"]}
+        line["mixed_f32_factor"] = {
+            "value": f32["value"], "unit": UNIT, "ms_per_step": f32["ms_per_step"],
+            "p50_step_ms": f32["p50_step_ms"], "p99_step_ms": f32["p99_step_ms"],
+            "newton_ms_mean": f32["newton_ms_mean"], "newton_iters_per_step": f32["newton_iters_per_step"],
+            "max_rel_diff_moments_vs_fp64": f32["max_rel_diff_moments_vs_fp64"],
+            "fp32_fallbacks": f32["fp32_fallbacks"], "speedup_over_fp64": f32["value"] / ref["value"],
+            "what": "precision mixed_f32f: tensor-core Hessian as in the headline, Cholesky factorisation and "
+                    "triangular solves in FP32 (FP64 refactorisation on a non-positive FP32 pivot); gradient, "
+                    "stopping test, line search and update in FP64. Not the headline: the headline keeps the "
+                    "factorisation in FP64."}
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_bench(args)
     if rank == 0 and not args.no_workloads:
@@ -578,7 +595,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_f32f"], default="mixed")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the plain FP64 GPU path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")

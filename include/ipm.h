@@ -97,8 +97,15 @@ typedef enum {
 
 typedef enum {
   IPM_PREC_FP64 = 0,   /* every operation in float64 */
-  IPM_PREC_MIXED = 1   /* Hessian contraction on the tensor cores (BF16 split products, FP32
+  IPM_PREC_MIXED = 1,  /* Hessian contraction on the tensor cores (BF16 split products, FP32
                           accumulate); gradient, Cholesky, Newton step and update in float64 */
+  IPM_PREC_MIXED_F32_FACTOR = 2  /* as IPM_PREC_MIXED, but the Cholesky factorisation and the
+                          triangular solves of the Newton direction run in FP32 on the CUDA cores
+                          (the split-BF16 Hessian is accurate to ~3e-5 already, the FP32 factor to
+                          ~n * 6e-8 relative); a cell whose FP32 factorisation meets a non-positive
+                          pivot is refactorised in FP64. Gradient, stopping test (Eq. tauCrit), line
+                          search and update stay float64, so the converged duals meet the same FP64
+                          criterion. CTA-per-cell kernel only; not with frozen Hessians. */
 } ipm_precision;
 
 /* Problem description. Primitive states are (u) for Burgers and (rho, v_1[, v_2], p) for Euler;
@@ -196,6 +203,7 @@ typedef struct {
                                the affected cells report IPM_ETIMEOUT) */
   int64_t factorizations;   /* Cholesky factorisations of the last solve (equals newton_iters without
                                frozen Hessians) */
+  int32_t fp32_fallbacks;   /* IPM_PREC_MIXED_F32_FACTOR: FP32 factorisations redone in FP64 (cumulative) */
 } ipm_stats;
 
 typedef struct ipm_ctx ipm_ctx;

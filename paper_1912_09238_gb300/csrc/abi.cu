@@ -48,7 +48,8 @@ struct ipm_ctx {
   StepScalars* d_sc = nullptr;
   int n_fixed_ghosts = 0;
   // launch configuration
-  bool mixed = false;          // precision IPM_PREC_MIXED: tensor-core Hessian
+  bool mixed = false;          // precision IPM_PREC_MIXED or _MIXED_F32_FACTOR: tensor-core Hessian
+  int newton_mode = 0;         // 0 FP64, 1 mixed, 2 mixed with an FP32 factorisation
   MixedLayout mx;
   NewtonSmem sm;
   float* d_phiT32 = nullptr;
@@ -226,7 +227,7 @@ static cudaError_t launch_newton_ctx(const ipm_ctx* c, const NewtonArgs& a, int 
     return launch_newton_warp(c->entk, c->phys, c->m, c->mixed, a, grid, c->warp_warps, c->warp_slice, s);
   }
   return launch_newton_phys(c->entk, c->phys, c->m, a, std::max(1, std::min(c->newton_grid, n_work)), c->newton_smem,
-                            c->h_in_smem, c->mixed, s);
+                            c->h_in_smem, c->newton_mode, s);
 }
 
 // enqueue: queue reset, Newton over the interior
@@ -409,8 +410,10 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     return fail(nullptr, IPM_EINVAL, "ipm_init: bad mesh or cfl");
   if ((problem->bc_left == IPM_BC_PERIODIC) != (problem->bc_right == IPM_BC_PERIODIC))
     return fail(nullptr, IPM_EINVAL, "ipm_init: periodic must be set on both ends");
-  if (opt.precision != IPM_PREC_FP64 && opt.precision != IPM_PREC_MIXED)
+  if (opt.precision != IPM_PREC_FP64 && opt.precision != IPM_PREC_MIXED && opt.precision != IPM_PREC_MIXED_F32_FACTOR)
     return fail(nullptr, IPM_EINVAL, "ipm_init: unknown precision");
+  if (opt.precision == IPM_PREC_MIXED_F32_FACTOR && opt.hessian_reuse != 0)
+    return fail(nullptr, IPM_EINVAL, "ipm_init: frozen Hessians keep FP64 factors; use them with IPM_PREC_FP64 or _MIXED");
   if (opt.newton_kernel < 0 || opt.newton_kernel > 2) return fail(nullptr, IPM_EINVAL, "ipm_init: unknown Newton kernel");
   if (opt.hessian_reuse < 0 || opt.hessian_reuse > 2 || !(opt.reuse_ratio > 0.0 && opt.reuse_ratio < 1.0))
     return fail(nullptr, IPM_EINVAL, "ipm_init: hessian_reuse must be 0..2 with 0 < reuse_ratio < 1");
@@ -480,7 +483,8 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   }
   // launch configuration of the Newton kernel: packed H in shared memory when it fits
   const size_t budget = (size_t)prop.sharedMemPerBlockOptin;
-  c->mixed = opt.precision == IPM_PREC_MIXED;
+  c->mixed = opt.precision != IPM_PREC_FP64;
+  c->newton_mode = opt.precision == IPM_PREC_MIXED_F32_FACTOR ? 2 : (c->mixed ? 1 : 0);
   if (c->mixed) {
     c->h_in_smem = true;
     c->mx = mixed_layout(c->N, c->m, c->Q, budget, true);
@@ -506,7 +510,7 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     // persistent grid: resident CTAs per SM (occupancy API) times the SM count; on the mixed path
     // the CTAs of one SM must also share its 512 tensor-memory columns
     int bps = 0;
-    e = prepare_newton(c->entk, c->phys, c->m, c->newton_smem, c->h_in_smem, c->mixed, &bps);
+    e = prepare_newton(c->entk, c->phys, c->m, c->newton_smem, c->h_in_smem, c->newton_mode, &bps);
     if (e == cudaSuccess) e = c->is2d ? prepare_update2d(c->Q) : prepare_update1d(c->phys, c->m, c->Q);
     if (e != cudaSuccess || bps < 1) {
         return fail(nullptr, IPM_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
@@ -515,7 +519,7 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     c->newton_grid = std::max(1, std::min(c->n_interior, bps * prop.multiProcessorCount));
   }
   // warp-per-cell variant for small cells: as many warps (cells) per CTA as shared memory allows
-  if (c->NM <= 64 && c->n_levels == 0 && opt.hessian_reuse == 0) {
+  if (c->NM <= 64 && c->n_levels == 0 && opt.hessian_reuse == 0 && c->newton_mode != 2) {
     const size_t slice = newton_warp_slice(c->N, c->m, c->Q);
     for (int wps = 8; wps >= 2; wps /= 2) {
       if (wps * slice * sizeof(double) > budget) continue;
@@ -870,6 +874,7 @@ static void fill_stats(const StepScalars& h, ipm_stats* s) {
   s->steps = h.steps;
   s->tc_timeouts = h.tc_timeouts;
   s->factorizations = (int64_t)h.last_factorizations;
+  s->fp32_fallbacks = h.fp32_fallbacks;
 }
 
 ipm_status ipm_sync_stats(ipm_ctx* c, ipm_stats* s) {
@@ -901,7 +906,8 @@ ipm_status ipm_assemble_hessian(ipm_ctx* c, double* h, size_t count) {
   a.track_speed = 0;
   cudaError_t e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), c->stream);
   if (e == cudaSuccess)
-    e = launch_newton_phys(c->entk, c->phys, c->m, a, c->newton_grid, c->newton_smem, c->h_in_smem, c->mixed, c->stream);
+    e = launch_newton_phys(c->entk, c->phys, c->m, a, c->newton_grid, c->newton_smem, c->h_in_smem, c->newton_mode,
+                           c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

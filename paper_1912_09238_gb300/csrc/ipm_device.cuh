@@ -243,6 +243,7 @@ struct StepScalars {
   int level_cap;                 // adaptive meshes: highest level the update may assign (Algorithm 4 stages)
   unsigned long long factorizations;       // Cholesky factorisations since the last reduction
   unsigned long long last_factorizations;  // ... of the last solve (frozen-Hessian statistics)
+  int fp32_fallbacks;                      // FP32-factor mode: factorisations redone in FP64 (cumulative)
 };
 
 // Mixed-precision Hessian (tensor cores): tiling of H_ab = Phi^T diag(w J_ab) Phi as MMAs with

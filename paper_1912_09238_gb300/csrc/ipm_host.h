@@ -70,9 +70,10 @@ cudaError_t raise_smem_limit(K k, size_t need) {
 NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* mx);
 MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem);
 int newton_threads();
+// mode: 0 FP64, 1 mixed (tensor-core Hessian, FP64 factorisation), 2 mixed with an FP32 factorisation
 cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, int grid, size_t smem, bool h_in_smem,
-                               bool mixed, cudaStream_t s);
-cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, bool mixed, int* blocks_per_sm);
+                               int mode, cudaStream_t s);
+cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, int mode, int* blocks_per_sm);
 // warp-per-cell Newton kernel for small cells (newton_warp.cu)
 size_t newton_warp_slice(int N, int m, int Q);
 cudaError_t prepare_newton_warp(int ent, int phys, int m, bool mixed, int warps, int slice, int* blocks_per_sm);

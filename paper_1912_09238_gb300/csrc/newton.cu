@@ -73,8 +73,8 @@ __device__ __forceinline__ void unpack_ab(int ab, int& a, int& b) {
 
 // Store the value H_ab[i][j] (a <= b) of the block form into the packed lower triangle of H
 // (row index i*M + a). Each lower entry is written by exactly one (ab, i, j).
-template <int M>
-__device__ __forceinline__ void store_block_entry(double* s_H, int a, int b, int i, int j, double v) {
+template <int M, typename T>
+__device__ __forceinline__ void store_block_entry(T* s_H, int a, int b, int i, int j, T v) {
   if (a == b) {
     if (i >= j) {
       const size_t r = (size_t)i * M + a, c = (size_t)j * M + a;
@@ -141,13 +141,17 @@ __device__ __forceinline__ size_t rowoff(int r) { return (size_t)r * (r + 1) / 2
 // cell index of work item w on the interior of an (nx+2)-wide mesh with one ghost layer, starting at row gy
 __device__ __forceinline__ int work_cell(int w, int nx, int gy) { return (w / nx + gy) * (nx + 2) + (w % nx + 1); }
 
+// element-type helpers of the factorisation (T = double, or float for the FP32-factor mode)
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
 // A[r][c] -= sum_k P[r][k] P[c][k] for rows r0..r0+3 (<= n) and columns c0, c0+1 (< n, <= r).
 // KW = NB: full panel (no guards on k); KW = 0: kw columns.
-template <int KW>
-__device__ __forceinline__ void trailing_tile(double* A, const double* s_P, int n, int r0, int c0, int kw) {
-  double acc[4][2];
+template <int KW, typename T>
+__device__ __forceinline__ void trailing_tile(T* A, const T* s_P, int n, int r0, int c0, int kw) {
+  T acc[4][2];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.0;
+  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = (T)0;
   bool rv[4], cv[2];
 #pragma unroll
   for (int i = 0; i < 4; ++i) rv[i] = r0 + i <= n;
@@ -156,11 +160,11 @@ __device__ __forceinline__ void trailing_tile(double* A, const double* s_P, int 
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
     if (KW == NB || k < kw) {
-      double p[4], q[2];
+      T p[4], q[2];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) p[i] = rv[i] ? s_P[(r0 + i) * PSTR + k] : 0.0;
+      for (int i = 0; i < 4; ++i) p[i] = rv[i] ? s_P[(r0 + i) * PSTR + k] : (T)0;
 #pragma unroll
-      for (int j = 0; j < 2; ++j) q[j] = cv[j] ? s_P[(c0 + j) * PSTR + k] : 0.0;
+      for (int j = 0; j < 2; ++j) q[j] = cv[j] ? s_P[(c0 + j) * PSTR + k] : (T)0;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -177,25 +181,26 @@ __device__ __forceinline__ void trailing_tile(double* A, const double* s_P, int 
 // Factorise the NB x NB diagonal block at rows/columns kb..kb+kw-1 (already updated by all earlier
 // panels); called by one full warp, lane i owning row kb + i in registers. Writes L into A and into
 // the panel buffer P, the reciprocal pivots into s_dinv; sets *s_flag on a bad pivot.
-__device__ __forceinline__ void panel_diag(double* A, int kb, int kw, double* P, double* s_dinv, int* s_flag) {
+template <typename T>
+__device__ __forceinline__ void panel_diag(T* A, int kb, int kw, T* P, T* s_dinv, int* s_flag) {
   const int lane = threadIdx.x & 31;
-  double row[NB];
+  T row[NB];
   const bool mine = lane < kw;
 #pragma unroll
-  for (int j = 0; j < NB; ++j) row[j] = (mine && j <= lane) ? A[rowoff(kb + lane) + kb + j] : 0.0;
+  for (int j = 0; j < NB; ++j) row[j] = (mine && j <= lane) ? A[rowoff(kb + lane) + kb + j] : (T)0;
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
     if (k < kw) {
-      const double dkk = __shfl_sync(0xffffffffu, row[k], k);
-      ok = ok && dkk > 0.0 && isfinite(dkk);
-      const double id = rsqrt(fmax(dkk, 1e-300));
+      const T dkk = __shfl_sync(0xffffffffu, row[k], k);
+      ok = ok && dkk > (T)0 && isfinite(dkk);
+      const T id = rsqrt_t(dkk > (T)0 ? dkk : (T)1);
       if (lane == k) row[k] = dkk * id;
       if (lane > k) row[k] *= id;
 #pragma unroll
       for (int j = k + 1; j < NB; ++j) {
         if (j < kw) {
-          const double ljk = __shfl_sync(0xffffffffu, row[k], j);
+          const T ljk = __shfl_sync(0xffffffffu, row[k], j);
           if (lane >= j) row[j] = fma(-row[k], ljk, row[j]);
         }
       }
@@ -215,15 +220,16 @@ __device__ __forceinline__ void panel_diag(double* A, int kb, int kw, double* P,
 }
 
 // Rows r = kb+kw .. n of the panel: L[r][kb..kb+kw) = A[r][kb..kb+kw) L_bb^-T, by threads t0, t0+stride, ...
-__device__ __forceinline__ void panel_trsm(double* A, int n, int kb, int kw, double* P, const double* s_dinv, int t0,
+template <typename T>
+__device__ __forceinline__ void panel_trsm(T* A, int n, int kb, int kw, T* P, const T* s_dinv, int t0,
                                            int stride) {
   for (int r = kb + kw + t0; r <= n; r += stride) {
     const size_t ro = rowoff(r) + kb;
-    double x[NB];
+    T x[NB];
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
       if (k < kw) {
-        double v = A[ro + k];
+        T v = A[ro + k];
 #pragma unroll
         for (int j = 0; j < k; ++j) v = fma(-x[j], P[(kb + k) * PSTR + j], v);
         x[k] = v * s_dinv[kb + k];
@@ -241,7 +247,8 @@ __device__ __forceinline__ void panel_trsm(double* A, int n, int kb, int kw, dou
 
 // Rank-kw update with panel P of rows s1..n and columns s1..min(r, n-1), tiles of 4 rows x 2 columns,
 // by threads t0, t0+stride, ...
-__device__ __forceinline__ void trailing_update(double* A, int n, const double* P, int kw, int s1, int t0, int stride) {
+template <typename T>
+__device__ __forceinline__ void trailing_update(T* A, int n, const T* P, int kw, int s1, int t0, int stride) {
   const int TR = (n + 4 - s1) / 4;                // row tiles (rows s1..n)
   const int ntiles = TR * (TR + 1);               // row tile ti has 2 ti + 2 column tiles
   for (int t = t0; t < ntiles; t += stride) {
@@ -260,7 +267,8 @@ __device__ __forceinline__ void trailing_update(double* A, int n, const double* 
 // (B) warp 0 factorises panel p+1 (diagonal block, then its rows below) while warps 1.. apply
 // panel p to the rest of the trailing matrix. The latency-bound diagonal block thus overlaps the
 // FP64-throughput-bound trailing update.
-__device__ bool cholesky_aug(double* A, int n, double* s_P, double* s_dinv, int* s_flag) {
+template <typename T>
+__device__ bool cholesky_aug(T* A, int n, T* s_P, T* s_dinv, int* s_flag) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int pbuf = (n + 1) * PSTR;
   if (tid == 0) *s_flag = 0;
@@ -277,15 +285,15 @@ __device__ bool cholesky_aug(double* A, int n, double* s_P, double* s_dinv, int*
   for (int kb = 0; kb < n; kb += NB, ++p) {
     const int kw = min(NB, n - kb), s0 = kb + kw;
     if (s0 >= n) break;                            // only the gradient row is left: nothing to update
-    const double* P = s_P + (p & 1) * pbuf;
-    double* Pn = s_P + ((p + 1) & 1) * pbuf;
+    const T* P = s_P + (p & 1) * pbuf;
+    T* Pn = s_P + ((p + 1) & 1) * pbuf;
     const int kw1 = min(NB, n - s0);
     // (A) columns s0 .. s0+kw1-1 of rows s0..n
     const int rows = n + 1 - s0;
     for (int item = tid; item < rows * kw1; item += NT) {
       const int r = s0 + item / kw1, c = s0 + item % kw1;
       if (c > r) continue;
-      double acc = 0.0;
+      T acc = (T)0;
 #pragma unroll
       for (int k = 0; k < NB; ++k)
         if (k < kw) acc = fma(P[r * PSTR + k], P[c * PSTR + k], acc);
@@ -309,16 +317,17 @@ __device__ bool cholesky_aug(double* A, int n, double* s_P, double* s_dinv, int*
 // Forward substitution L y = b in place on x (x holds b on entry), blocks of NB from the top: one
 // warp solves the diagonal block (lane i holds entry kb + i), then all threads update the rows below.
 // Used when a stored factor is reused (the factorisation itself folds the forward solve in).
-__device__ void forward_substitute(const double* A, int n, const double* s_dinv, double* x) {
+template <typename T>
+__device__ void forward_substitute(const T* A, int n, const T* s_dinv, T* x) {
   const int tid = threadIdx.x, lane = tid & 31;
   for (int kb = 0; kb < n; kb += NB) {
     const int kw = min(NB, n - kb);
     if (tid < 32) {
-      double v = lane < kw ? x[kb + lane] : 0.0;
+      T v = lane < kw ? x[kb + lane] : (T)0;
 #pragma unroll
       for (int k = 0; k < NB; ++k) {
         if (k < kw) {
-          const double yk = __shfl_sync(0xffffffffu, v, k) * s_dinv[kb + k];
+          const T yk = __shfl_sync(0xffffffffu, v, k) * s_dinv[kb + k];
           if (lane == k) v = yk;
           if (lane > k && lane < kw) v = fma(-A[rowoff(kb + lane) + kb + k], yk, v);
         }
@@ -328,7 +337,7 @@ __device__ void forward_substitute(const double* A, int n, const double* s_dinv,
     __syncthreads();
     for (int r = kb + kw + tid; r < n; r += NT) {
       const size_t ro = rowoff(r) + kb;
-      double v = x[r];
+      T v = x[r];
 #pragma unroll
       for (int k = 0; k < NB; ++k)
         if (k < kw) v = fma(-A[ro + k], x[kb + k], v);
@@ -340,16 +349,17 @@ __device__ void forward_substitute(const double* A, int n, const double* s_dinv,
 
 // Back substitution L^T x = b in place on x (x holds b on entry), blocks of NB from the bottom: one
 // warp solves the diagonal block (lane i holds entry kb + i), then all threads update the entries above.
-__device__ void back_substitute(const double* A, int n, const double* s_dinv, double* x) {
+template <typename T>
+__device__ void back_substitute(const T* A, int n, const T* s_dinv, T* x) {
   const int tid = threadIdx.x, lane = tid & 31;
   for (int kb = ((n - 1) / NB) * NB; kb >= 0; kb -= NB) {
     const int kw = min(NB, n - kb);
     if (tid < 32) {
-      double v = lane < kw ? x[kb + lane] : 0.0;
+      T v = lane < kw ? x[kb + lane] : (T)0;
 #pragma unroll
       for (int k = NB - 1; k >= 0; --k) {
         if (k < kw) {
-          const double xk = __shfl_sync(0xffffffffu, v, k) * s_dinv[kb + k];
+          const T xk = __shfl_sync(0xffffffffu, v, k) * s_dinv[kb + k];
           if (lane == k) v = xk;
           if (lane < k) v = fma(-A[rowoff(kb + k) + kb + lane], xk, v);
         }
@@ -358,7 +368,7 @@ __device__ void back_substitute(const double* A, int n, const double* s_dinv, do
     }
     __syncthreads();
     for (int r = tid; r < kb; r += NT) {
-      double v = x[r];
+      T v = x[r];
 #pragma unroll
       for (int k = 0; k < NB; ++k)
         if (k < kw) v = fma(-A[rowoff(kb + k) + r], x[kb + k], v);
@@ -388,8 +398,8 @@ __device__ __forceinline__ bool tc_wait(TcState& t, int k) {
 // (b), mixed: split-BF16 products on the tensor cores, FP32 accumulate in tensor memory, then
 // widened into the packed FP64 H. s_wJf holds w_k J_k,ab as float [B][Q]. Returns false when a
 // bounded wait ran out (the CTA must stop).
-template <int M>
-__device__ bool hessian_tc(const NewtonArgs& a, int N, const float* s_wJf, double* s_H, uint8_t* sA, uint8_t* sB,
+template <int M, typename T>
+__device__ bool hessian_tc(const NewtonArgs& a, int N, const float* s_wJf, T* s_H, uint8_t* sA, uint8_t* sB,
                            TcState& t, int* s_abort) {
   constexpr int B = packed_count(M);
   const MixedTiles& mx = a.mx;
@@ -498,7 +508,7 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, const float* s_wJf, doubl
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int j = col0 + e;
-            if (j < N) store_block_entry<M>(s_H, aa, bb, i, j, (double)__uint_as_float(r[e]));
+            if (j < N) store_block_entry<M, T>(s_H, aa, bb, i, j, (T)__uint_as_float(r[e]));
           }
         }
       }
@@ -509,7 +519,7 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, const float* s_wJf, doubl
   return true;
 }
 
-template <int ENT, int PHYS, int M, bool H_SMEM, bool MIXED>
+template <int ENT, int PHYS, int M, bool H_SMEM, bool MIXED, bool F32F>
 __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
   constexpr int B = packed_count(M);
   extern __shared__ __align__(128) double smem[];
@@ -672,7 +682,40 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       const bool reuse = have_factor && a.hessian_reuse > 0 && !a.h_dump &&
                          (it == 0 ? a.hessian_reuse == 2 : (alpha_prev == 1.0 && res <= a.reuse_ratio * res_prev));
       res_prev = res;
-      if (reuse) {
+      bool solved = false;
+      if (F32F && !reuse && !a.h_dump) {
+        // FP32 factorisation of the split-BF16 Hessian: the tensor-core accumulators are FP32 already;
+        // the FP32 solve gives the Newton direction to about the Hessian's own accuracy. A failed
+        // pivot falls through to the FP64 assembly and factorisation below.
+        float* Hf = reinterpret_cast<float*>(s_H);
+        float* Pf = reinterpret_cast<float*>(s_P);
+        float* dinvf = reinterpret_cast<float*>(s_dinv);
+        if (!hessian_tc<M, float>(a, N, reinterpret_cast<const float*>(s_wJ), Hf, sA, sB, tcs, &s_abort)) {
+          if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
+          st = ST_TIMEOUT;
+          stop = true;
+          break;
+        }
+        __syncthreads();
+        for (int r = tid; r < NM; r += NT) Hf[rowoff(NM) + r] = (float)s_g[r];
+        __syncthreads();
+        if (cholesky_aug<float>(Hf, NM, Pf, dinvf, &s_flag)) {
+          float* xf = Pf;                                   // the panel buffers are free again
+          for (int r = tid; r < NM; r += NT) xf[r] = -Hf[rowoff(NM) + r];
+          __syncthreads();
+          back_substitute<float>(Hf, NM, dinvf, xf);
+          for (int r = tid; r < NM; r += NT) s_d[r] = (double)xf[r];
+          __syncthreads();
+          ++nfact;
+          solved = true;
+          have_factor = false;                              // the FP64 factor (if any) was overwritten
+        } else if (tid == 0) {
+          atomicAdd(&a.sc->fp32_fallbacks, 1);
+        }
+        __syncthreads();
+      }
+      if (solved) {
+      } else if (reuse) {
         // chord step with the kept factor: L L^T Delta = -g
         for (int r = tid; r < NM; r += NT) s_d[r] = -s_g[r];
         __syncthreads();
@@ -681,7 +724,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       } else {
       // (b) Hessian, packed lower triangle, row index r = i*M + a
       if (MIXED) {
-        if (!hessian_tc<M>(a, N, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, tcs, &s_abort)) {
+        if (!hessian_tc<M, double>(a, N, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, tcs, &s_abort)) {
           if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
           st = ST_TIMEOUT;
           stop = true;
@@ -867,10 +910,10 @@ MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem
 
 // prepare = 1: raise the kernel's dynamic shared-memory limit (outside any stream capture);
 // prepare = 0: launch.
-template <int ENT, int PHYS, int M, bool MIXED>
+template <int ENT, int PHYS, int M, bool MIXED, bool F32F>
 static cudaError_t launch_t(const NewtonArgs* a, int grid, size_t smem, bool h_in_smem, cudaStream_t s, int prepare,
                             int* blocks_per_sm) {
-  auto k = h_in_smem ? k_newton<ENT, PHYS, M, true, MIXED> : k_newton<ENT, PHYS, M, false, MIXED>;
+  auto k = h_in_smem ? k_newton<ENT, PHYS, M, true, MIXED, F32F> : k_newton<ENT, PHYS, M, false, MIXED, F32F>;
   if (prepare) {
     cudaError_t e = raise_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
@@ -898,20 +941,23 @@ static cudaError_t dispatch(int ent, int phys, int m, F&& f) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, bool mixed, int* blocks_per_sm) {
+// mode: 0 FP64, 1 mixed (tensor-core Hessian, FP64 factorisation), 2 mixed with an FP32 factorisation
+cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, int mode, int* blocks_per_sm) {
   return dispatch(ent, phys, m, [&](auto E, auto P, auto MM) {
     constexpr int e_ = decltype(E)::value, p_ = decltype(P)::value, m_ = decltype(MM)::value;
-    return mixed ? launch_t<e_, p_, m_, true>(nullptr, 0, smem, h_in_smem, nullptr, 1, blocks_per_sm)
-                 : launch_t<e_, p_, m_, false>(nullptr, 0, smem, h_in_smem, nullptr, 1, blocks_per_sm);
+    if (mode == 2) return launch_t<e_, p_, m_, true, true>(nullptr, 0, smem, h_in_smem, nullptr, 1, blocks_per_sm);
+    return mode == 1 ? launch_t<e_, p_, m_, true, false>(nullptr, 0, smem, h_in_smem, nullptr, 1, blocks_per_sm)
+                     : launch_t<e_, p_, m_, false, false>(nullptr, 0, smem, h_in_smem, nullptr, 1, blocks_per_sm);
   });
 }
 
 cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, int grid, size_t smem, bool h_in_smem,
-                               bool mixed, cudaStream_t s) {
+                               int mode, cudaStream_t s) {
   return dispatch(ent, phys, m, [&](auto E, auto P, auto MM) {
     constexpr int e_ = decltype(E)::value, p_ = decltype(P)::value, m_ = decltype(MM)::value;
-    return mixed ? launch_t<e_, p_, m_, true>(&a, grid, smem, h_in_smem, s, 0, nullptr)
-                 : launch_t<e_, p_, m_, false>(&a, grid, smem, h_in_smem, s, 0, nullptr);
+    if (mode == 2) return launch_t<e_, p_, m_, true, true>(&a, grid, smem, h_in_smem, s, 0, nullptr);
+    return mode == 1 ? launch_t<e_, p_, m_, true, false>(&a, grid, smem, h_in_smem, s, 0, nullptr)
+                     : launch_t<e_, p_, m_, false, false>(&a, grid, smem, h_in_smem, s, 0, nullptr);
   });
 }
 

@@ -107,7 +107,7 @@ extern "C" ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, con
   const NewtonSmem sm = h_in_smem ? sm_full : sm_lean;
   const size_t smem = sm.bytes;
   int bps = 0;
-  e = prepare_newton(entk, phys, m, smem, h_in_smem, false, &bps);
+  e = prepare_newton(entk, phys, m, smem, h_in_smem, 0, &bps);
   if (e != cudaSuccess || bps < 1) return noalloc_fail(IPM_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
 
   // carve the scratch: scalars | Phi | PhiT | w | nodes | pairs | cell list | Hessian slots
@@ -186,7 +186,7 @@ extern "C" ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, con
   a.track_speed = 0;
   a.h_dump = nullptr;
   a.off_h = sm.off_h;
-  e = launch_newton_phys(entk, phys, m, a, grid, smem, h_in_smem, false, s);
+  e = launch_newton_phys(entk, phys, m, a, grid, smem, h_in_smem, 0, s);
   if (e == cudaSuccess) e = launch_finalize(a.sc, d_iters, d_status, nullptr, n_cells, 0, n_cells, 0, s);
   if (e != cudaSuccess) return noalloc_fail(IPM_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   if (stats) {

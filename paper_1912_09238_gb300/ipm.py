@@ -18,7 +18,7 @@ BC = {"outflow": 0, "periodic": 1, "dirichlet": 2, "slip": 3}
 MESH = {"cartesian": 0, "ramp": 1}
 IC = {"riemann": 0, "freestream": 1, "shear": 2}
 ENTROPY = {"quadratic": 0, "barrier": 1, "euler": 2}
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "mixed_f32f": 2}
 
 
 class ipm_problem(ctypes.Structure):
@@ -63,7 +63,8 @@ class ipm_stats(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int64), ("max_iters", ctypes.c_int32), ("failed_cells", ctypes.c_int32),
                 ("first_failed_cell", ctypes.c_int32), ("first_status", ctypes.c_int32),
                 ("dt", ctypes.c_double), ("t", ctypes.c_double), ("residual", ctypes.c_double),
-                ("steps", ctypes.c_int64), ("tc_timeouts", ctypes.c_int32), ("factorizations", ctypes.c_int64)]
+                ("steps", ctypes.c_int64), ("tc_timeouts", ctypes.c_int32), ("factorizations", ctypes.c_int64),
+                ("fp32_fallbacks", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
