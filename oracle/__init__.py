@@ -23,6 +23,8 @@ What it computes, module by module (each function cites the passage it follows):
                   for 1-D problems, the steady residual (Eq. residualSteady).
 * ``scheme2d`` -- the same on structured 2-D quadrilateral meshes (Sec. 7 Euler system).
 * ``adaptive`` -- the smoothness indicator (Eq. errorIndicator) and Algorithm 3.
+* ``collocation`` -- Stochastic Collocation (Sec. 2, Sec. 7): the deterministic scheme with the
+                  same flux run once per quadrature node, each node on its own time steps.
 
 Everything is float64 numpy. Vectorisation over cells (and over quadrature nodes) is the
 only liberty taken: every cell still runs its own iteration with its own stopping test;

@@ -140,15 +140,19 @@ def time_step(prob: Problem1D, U: np.ndarray, t: float) -> float:
     return dt
 
 
-def moment_update(prob: Problem1D, lam: np.ndarray, dt: float) -> np.ndarray:
-    """c(lambda_{j-1}, lambda_j, lambda_{j+1}) for j = 1..nx (Eq. momentUpQuadrature): (nx, N, m)."""
-    U = nodal_states(prob, lam)                                  # (nx+2, Q, m)
+def nodal_update(prob: Problem1D, U: np.ndarray, dt: float) -> np.ndarray:
+    """The finite-volume update of nodal states U (nx+2, Q, m), node by node, for j = 1..nx:
+    u_k^(j) - dt/dx (g(u_k^(j), u_k^(j+1)) - g(u_k^(j-1), u_k^(j))): (nx, Q, m)."""
     if prob.flux == "rusanov":
         G = rusanov(prob.phys, U[:-1], U[1:], np.array([1.0]))
     else:
         G = lax_friedrichs(prob.phys, U[:-1], U[1:], prob.dx, dt)   # faces j+1/2, j = 0..nx: (nx+1, Q, m)
-    inner = U[1:-1] - (dt / prob.dx) * (G[1:] - G[:-1])
-    return prob.space.project(inner)
+    return U[1:-1] - (dt / prob.dx) * (G[1:] - G[:-1])
+
+
+def moment_update(prob: Problem1D, lam: np.ndarray, dt: float) -> np.ndarray:
+    """c(lambda_{j-1}, lambda_j, lambda_{j+1}) for j = 1..nx (Eq. momentUpQuadrature): (nx, N, m)."""
+    return prob.space.project(nodal_update(prob, nodal_states(prob, lam), dt))
 
 
 def ipm_step(prob: Problem1D, st: State1D) -> State1D:

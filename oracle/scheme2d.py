@@ -305,9 +305,13 @@ def _outside(prob, side, U, inner, ghost, n):
 
 def moment_update(prob: Problem2D, lam: np.ndarray, dt: float) -> np.ndarray:
     """c(...) for every interior cell: (ny, nx, N, m)."""
+    return prob.space.project(nodal_update(prob, nodal_states(prob, lam), dt))
+
+
+def nodal_update(prob: Problem2D, U: np.ndarray, dt: float) -> np.ndarray:
+    """The finite-volume update of nodal states U (ny+2, nx+2, Q, m), node by node, for every interior
+    cell: u_k^(c) - dt/A_c sum_faces L_f s_f g(u_k^(in), u_k^(out); n_f): (ny, nx, Q, m)."""
     mesh = prob.mesh
-    ny, nx = mesh.ny, mesh.nx
-    U = nodal_states(prob, lam)                            # (ny+2, nx+2, Q, m)
     left, right, bottom, top = prob.sides
     if left == "periodic":
         U = U.copy()
@@ -326,8 +330,7 @@ def moment_update(prob: Problem2D, lam: np.ndarray, dt: float) -> np.ndarray:
     ahead_y = np.concatenate([C, _outside(prob, top, U, C[-1:], U[-1:, 1:-1], nyf[-1:])], axis=0)
     Gy = rusanov(prob.phys, behind_y, ahead_y, nyf[:, :, None, :]) * lyf[:, :, None, None]   # (ny+1, nx, Q, m)
     div = (Gx[:, 1:] - Gx[:, :-1]) + (Gy[1:] - Gy[:-1])
-    inner = C - (dt / mesh.area())[..., None, None] * div
-    return prob.space.project(inner)
+    return C - (dt / mesh.area())[..., None, None] * div
 
 
 def time_step(prob: Problem2D, U: np.ndarray, t: float, clip: bool = True) -> float:
