@@ -310,6 +310,8 @@ def run_gpu(args):
         line["workloads"] = workloads_bench(args)
     if rank == 0 and not args.no_workloads:
         line["frozen_hessian"] = frozen_hessian_bench(args)
+    if rank == 0 and not args.no_workloads:
+        line["collocation"] = collocation_bench(args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -403,6 +405,72 @@ def workloads_bench(args):
         out["kh2d_adaptive"] = {"workload": f"2-D shear layer, 512 x 512 periodic, 3 uniform dims, adaptive total degree "
                                 f"2-6 (10-84 x 4 moments), 7^3 = 343 nodes, first {args.kh_steps} of the 200 steps",
                                 "unit": UNIT, **r}
+    return out
+
+
+def burgers_exact_mean_var(nx, x_lo, x_hi, t, samples=4001, sub=32):
+    """E and Var over xi ~ U[-1, 1] of the cell averages of the exact Burgers solution of the 1-D Burgers
+    workload: u = 12 left of the shock x_s(xi) = 0.5 + 0.2 xi + 6.5 t (Rankine-Hugoniot speed
+    (12 + 1)/2), 1 right of it; midpoint rules in xi and inside each cell."""
+    import numpy as np
+    dx = (x_hi - x_lo) / nx
+    xi = -1.0 + (np.arange(samples) + 0.5) * 2.0 / samples
+    xs = 0.5 + 0.2 * xi + 6.5 * t
+    x = x_lo + (np.arange(nx)[:, None] + (np.arange(sub)[None, :] + 0.5) / sub) * dx       # (nx, sub)
+    frac = np.mean(x[:, :, None] < xs[None, None, :], axis=1)                              # (nx, samples)
+    u = 1.0 + 11.0 * frac
+    return u.mean(axis=1), u.var(axis=1)
+
+
+def collocation_bench(args):
+    """Stochastic Collocation (ipm_sc_*) next to IPM on the GPU (the paper's IPM-versus-SC comparison).
+    Burgers to t_end = 0.11 on 200 and 1600 cells: IPM (FP64) with (N, Q) = (3, 5), (6, 10), (10, 20)
+    against SC with Q = 5, 10, 20, 40 Gauss nodes; relative L2 errors of E[u] and Var[u] against the exact
+    Rankine-Hugoniot solution's cell averages, and the device time of each full run. Sod (2000 cells, 216
+    nodes): the SC run to t_end = 0.14 (its time and node-cell-steps/s); the IPM Sod numbers are the
+    headline's."""
+    import numpy as np
+    from paper_1912_09238_gb300 import workloads
+    from tests._cases import gpu_collocation, gpu_context
+    import torch
+    out = {}
+    stream = torch.cuda.current_stream()
+    for nx in (200, 1600):
+        w = workloads.variant(workloads.BURGERS_1D, nx=nx)
+        E_ref, V_ref = burgers_exact_mean_var(nx, w["x_lo"], w["x_hi"], w["t_end"])
+        dx = (w["x_hi"] - w["x_lo"]) / nx
+        err = lambda a, b: float(np.sqrt(np.sum(dx * (a - b) ** 2) / np.sum(dx * b ** 2)))
+        rows = []
+        for N, Q in ((3, 5), (6, 10), (10, 20)):
+            ctx = gpu_context(workloads.variant(w, M=N - 1, nq=Q), precision="fp64")
+            ctx.set_stream(stream.cuda_stream)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            s = ctx.run()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            u = ctx.get_moments()[1:-1, :, 0]
+            rows.append({"method": "IPM (FP64)", "N": N, "Q": Q, "steps": int(s.steps), "ms": ev0.elapsed_time(ev1),
+                         "E_rel_l2": err(u[:, 0], E_ref), "Var_rel_l2": err(np.sum(u[:, 1:] ** 2, axis=1), V_ref)})
+            ctx.close()
+        for Q in (5, 10, 20, 40):
+            g = gpu_collocation(workloads.variant(w, M=Q - 1, nq=Q))
+            st = g.run()
+            u = g.get_moments()[1:-1, :, 0]        # N = Q moments: their squares sum to the nodal variance
+            rows.append({"method": "SC", "Q": Q, "steps": int(st.max_node_steps), "ms": st.elapsed_ms,
+                         "E_rel_l2": err(u[:, 0], E_ref), "Var_rel_l2": err(np.sum(u[:, 1:] ** 2, axis=1), V_ref)})
+            g.close()
+        out[f"burgers1d_{nx}"] = {"workload": f"1-D Burgers, {nx} cells, t_end 0.11; errors against the exact "
+                                              "solution's cell averages (the first-order LF error included)",
+                                  "runs": rows}
+    w = workloads.SOD_1D
+    g = gpu_collocation(w)
+    st = g.run()
+    steps, _, _ = g.node_info()
+    out["sod1d"] = {"workload": "1-D Sod, 2000 cells, 216 Gauss nodes (6^3), to t_end 0.14", "ms": st.elapsed_ms,
+                    "node_steps_min_max": [int(steps.min()), int(steps.max())],
+                    "node_cell_steps_per_s": float(steps.sum()) * w["nx"] / (st.elapsed_ms / 1e3)}
+    g.close()
     return out
 
 
@@ -602,7 +670,7 @@ def main():
     ap.add_argument("--no-workloads", action="store_true", help="skip the Burgers / ramp / shear-layer runs")
     ap.add_argument("--ramp-steps", type=int, default=1000, help="One-Shot step cap of the ramp workload")
     ap.add_argument("--kh-steps", type=int, default=10, help="steps of the adaptive shear-layer workload")
-    ap.add_argument("--only", choices=["burgers", "ramp", "kh"], default=None,
+    ap.add_argument("--only", choices=["burgers", "ramp", "kh", "collocation"], default=None,
                     help="run only this workload's timing (no JSON bench line; for profiling)")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-steps", type=int, default=10)
@@ -622,7 +690,7 @@ def main():
         torch.cuda.set_stream(torch.cuda.Stream())
         import __graft_entry__
         __graft_entry__.build()
-        print(json.dumps(workloads_bench(args)), flush=True)
+        print(json.dumps(collocation_bench(args) if args.only == "collocation" else workloads_bench(args)), flush=True)
     else:
         run_gpu(args)
 

@@ -403,6 +403,56 @@ void ipm_server_destroy(ipm_server* srv);
 ipm_status ipm_tables(int p, int total_degree, int n_per_dim, int N_cap, int Q_cap,
                       int* indices, double* nodes, double* weights, double* phi, int* N_out, int* Q_out);
 
+/* ---- Stochastic Collocation (SC): the non-intrusive baseline (Sec. 2, the collocation paragraph;
+ * Sec. 7, the IPM-versus-SC comparisons) -------------------------------------------------------------
+ * Every node xi_k of the tensor Gauss rule of (basis, quad) runs the deterministic finite-volume
+ * scheme of the IPM update, with the same numerical flux (global Lax-Friedrichs in 1-D, Rusanov on 2-D
+ * meshes) and the same boundary handling, on its own state u(x, t, xi_k), starting from the exact
+ * nodal cell averages of the initial data. Each node is a black box: its own time step
+ * dt_k = cfl * h / max wave speed of node k (interior and Dirichlet ghosts; h = dx in 1-D), with the
+ * 1-D viscosity dx / (2 dt_k) of that step, and its own step count. Unsteady problems (t_end > 0)
+ * stop each node at t_end (last step clipped); steady problems (t_end == 0) iterate each node until
+ * its residual sum_c A_c |rho_c^{n+1} - rho_c^n| (A_c = dx in 1-D) is below steady_tol. The moments
+ * are u_hat_i = sum_k w_k u(xi_k) phi_i(xi_k) (layout [cell][moment][variable] as everywhere).
+ * The library has no entropy or dual state here: SC needs neither. */
+typedef struct ipm_sc ipm_sc;
+
+typedef struct {
+  int64_t steps;            /* lockstep steps launched since ipm_sc_init (finished nodes are carried through) */
+  int64_t max_node_steps;   /* most steps any node has taken */
+  int32_t active_nodes;     /* nodes still running */
+  double t_min, t_max;      /* smallest and largest node time */
+  double residual_max;      /* largest last steady residual over the nodes (0 before the first step) */
+  double elapsed_ms;        /* device time of this call's launches (CUDA events on the object's stream) */
+} ipm_sc_stats;
+
+/* Allocate the nodal states (two buffers of cells * nodes * variables float64) and set the initial
+ * data. steady_tol is used (and must be > 0) when problem->t_end == 0. IPM_EINVAL for a problem
+ * ipm_init would reject; IPM_ENOMEM / IPM_ECUDA as ipm_init. */
+ipm_status ipm_sc_init(const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad,
+                       double steady_tol, ipm_sc** out);
+
+/* One step of every running node; stats may be NULL. */
+ipm_status ipm_sc_step(ipm_sc* sc, ipm_sc_stats* stats);
+
+/* Step until every node has finished or max_steps lockstep steps have been launched in total
+ * (steps are launched in captured graphs of 16; a node that finishes inside a graph is carried
+ * through unchanged). stats may be NULL. */
+ipm_status ipm_sc_run(ipm_sc* sc, int64_t max_steps, ipm_sc_stats* stats);
+
+/* Nodal states [cell][node][variable] (count = cells * nodes * variables, ghosts included). */
+ipm_status ipm_sc_get_nodal(ipm_sc* sc, double* host, size_t count);
+
+/* SC moments [cell][moment][variable] (count = cells * N * variables). */
+ipm_status ipm_sc_get_moments(ipm_sc* sc, double* host, size_t count);
+
+/* Per node (count = node count; any output may be NULL): steps taken, time reached, last residual. */
+ipm_status ipm_sc_get_node_info(ipm_sc* sc, int64_t* steps, double* t, double* residual, size_t count);
+
+ipm_status ipm_sc_get_dims(const ipm_sc* sc, int* n_cells, int* n_nodes, int* n_moments, int* n_vars);
+const char* ipm_sc_last_error(const ipm_sc* sc);   /* NULL: the last failure without a handle */
+void ipm_sc_destroy(ipm_sc* sc);                   /* NULL is accepted */
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,9 +65,12 @@ def initial_nodal_1d(prob: s1.Problem1D) -> np.ndarray:
     return U
 
 
-def run_1d(prob: s1.Problem1D, steady_tol: float = 0.0, max_steps: int = 10 ** 9) -> SCResult:
-    """SC of a 1-D problem: every node of prob.space run on its own (see the module docstring)."""
+def run_1d(prob: s1.Problem1D, steady_tol: float = 0.0, max_steps: int = 10 ** 9, nodes=None) -> SCResult:
+    """SC of a 1-D problem: every node of prob.space run on its own (see the module docstring). nodes:
+    indices of the nodes to run (default all); the result holds those nodes in that order."""
     U0 = initial_nodal_1d(prob)
+    if nodes is not None:
+        U0 = U0[:, list(nodes)]
     Q = U0.shape[1]
 
     def step(u, dt):
@@ -92,9 +95,12 @@ def initial_nodal_2d(prob: s2.Problem2D) -> np.ndarray:
     return prob.ic.cell_states(prob.phys, prob.mesh, prob.space.nodes, ny + 2, nx + 2)
 
 
-def run_2d(prob: s2.Problem2D, steady_tol: float = 0.0, max_steps: int = 10 ** 9) -> SCResult:
-    """SC of a 2-D problem: every node of prob.space run on its own (see the module docstring)."""
+def run_2d(prob: s2.Problem2D, steady_tol: float = 0.0, max_steps: int = 10 ** 9, nodes=None) -> SCResult:
+    """SC of a 2-D problem: every node of prob.space run on its own (see the module docstring). nodes:
+    indices of the nodes to run (default all); the result holds those nodes in that order."""
     U0 = initial_nodal_2d(prob)
+    if nodes is not None:
+        U0 = U0[:, :, list(nodes)]
     Q = U0.shape[2]
     area = prob.mesh.area()
 

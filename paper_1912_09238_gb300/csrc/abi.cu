@@ -380,36 +380,45 @@ static cudaError_t upload(T** dst, const std::vector<T>& src) {
   return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
+namespace ipm {
+// Checks of a problem, its basis and its quadrature shared by every entry point that takes them;
+// nullptr when they are valid, else what is wrong.
+const char* check_problem(const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad) {
+  if (basis->p < 1 || basis->p > 3 || basis->total_degree < 0 || quad->n_per_dim < 1)
+    return "basis needs 1 <= p <= 3, M >= 0, n_per_dim >= 1";
+  if (problem->kind != IPM_BURGERS_1D && problem->kind != IPM_EULER_1D && problem->kind != IPM_EULER_2D)
+    return "unknown problem kind";
+  if (problem->kind == IPM_EULER_2D) {
+    if (problem->ny < 1 || !(problem->y_hi > problem->y_lo))
+      return "2-D mesh needs ny >= 1 and y_hi > y_lo";
+    if ((problem->bc_bottom == IPM_BC_PERIODIC) != (problem->bc_top == IPM_BC_PERIODIC))
+      return "periodic must be set on both the bottom and the top";
+    const int sides[4] = {problem->bc_left, problem->bc_right, problem->bc_bottom, problem->bc_top};
+    for (int k = 0; k < 4; ++k)
+      if (sides[k] < IPM_BC_OUTFLOW || sides[k] > IPM_BC_SLIP_WALL) return "bad side";
+    if (problem->mesh_kind != IPM_MESH_CARTESIAN && problem->mesh_kind != IPM_MESH_RAMP)
+      return "unknown mesh kind";
+    if (problem->mesh_kind == IPM_MESH_RAMP && !(std::fabs(problem->ramp_deg) < 60.0))
+      return "ramp angle must be below 60 degrees";
+    if (problem->ic_kind != IPM_IC_RIEMANN && problem->ic_kind != IPM_IC_FREESTREAM && problem->ic_kind != IPM_IC_SHEAR)
+      return "unknown initial data";
+    if (problem->ic_kind != IPM_IC_FREESTREAM && problem->mesh_kind != IPM_MESH_CARTESIAN)
+      return "Riemann and shear data need a Cartesian mesh";
+  } else if (problem->bc_left == IPM_BC_SLIP_WALL || problem->bc_right == IPM_BC_SLIP_WALL) {
+    return "slip walls are 2-D only";
+  }
+  if (problem->nx < 1 || !(problem->x_hi > problem->x_lo) || !(problem->cfl > 0))
+    return "bad mesh or cfl";
+  if ((problem->bc_left == IPM_BC_PERIODIC) != (problem->bc_right == IPM_BC_PERIODIC))
+    return "periodic must be set on both ends";
+  return nullptr;
+}
+}  // namespace ipm
+
 // Validate the problem and fill every size, table and launch parameter of c (no device allocation).
 static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad,
                            const ipm_entropy* entropy, const ipm_options& opt) {
-  if (basis->p < 1 || basis->p > 3 || basis->total_degree < 0 || quad->n_per_dim < 1)
-    return fail(nullptr, IPM_EINVAL, "ipm_init: basis needs 1 <= p <= 3, M >= 0, n_per_dim >= 1");
-  if (problem->kind != IPM_BURGERS_1D && problem->kind != IPM_EULER_1D && problem->kind != IPM_EULER_2D)
-    return fail(nullptr, IPM_EINVAL, "ipm_init: unknown problem kind");
-  if (problem->kind == IPM_EULER_2D) {
-    if (problem->ny < 1 || !(problem->y_hi > problem->y_lo))
-      return fail(nullptr, IPM_EINVAL, "ipm_init: 2-D mesh needs ny >= 1 and y_hi > y_lo");
-    if ((problem->bc_bottom == IPM_BC_PERIODIC) != (problem->bc_top == IPM_BC_PERIODIC))
-      return fail(nullptr, IPM_EINVAL, "ipm_init: periodic must be set on both the bottom and the top");
-    const int sides[4] = {problem->bc_left, problem->bc_right, problem->bc_bottom, problem->bc_top};
-    for (int k = 0; k < 4; ++k)
-      if (sides[k] < IPM_BC_OUTFLOW || sides[k] > IPM_BC_SLIP_WALL) return fail(nullptr, IPM_EINVAL, "ipm_init: bad side");
-    if (problem->mesh_kind != IPM_MESH_CARTESIAN && problem->mesh_kind != IPM_MESH_RAMP)
-      return fail(nullptr, IPM_EINVAL, "ipm_init: unknown mesh kind");
-    if (problem->mesh_kind == IPM_MESH_RAMP && !(std::fabs(problem->ramp_deg) < 60.0))
-      return fail(nullptr, IPM_EINVAL, "ipm_init: ramp angle must be below 60 degrees");
-    if (problem->ic_kind != IPM_IC_RIEMANN && problem->ic_kind != IPM_IC_FREESTREAM && problem->ic_kind != IPM_IC_SHEAR)
-      return fail(nullptr, IPM_EINVAL, "ipm_init: unknown initial data");
-    if (problem->ic_kind != IPM_IC_FREESTREAM && problem->mesh_kind != IPM_MESH_CARTESIAN)
-      return fail(nullptr, IPM_EINVAL, "ipm_init: Riemann and shear data need a Cartesian mesh");
-  } else if (problem->bc_left == IPM_BC_SLIP_WALL || problem->bc_right == IPM_BC_SLIP_WALL) {
-    return fail(nullptr, IPM_EINVAL, "ipm_init: slip walls are 2-D only");
-  }
-  if (problem->nx < 1 || !(problem->x_hi > problem->x_lo) || !(problem->cfl > 0))
-    return fail(nullptr, IPM_EINVAL, "ipm_init: bad mesh or cfl");
-  if ((problem->bc_left == IPM_BC_PERIODIC) != (problem->bc_right == IPM_BC_PERIODIC))
-    return fail(nullptr, IPM_EINVAL, "ipm_init: periodic must be set on both ends");
+  if (const char* why = check_problem(problem, basis, quad)) return fail(nullptr, IPM_EINVAL, std::string("ipm_init: ") + why);
   if (opt.precision != IPM_PREC_FP64 && opt.precision != IPM_PREC_MIXED && opt.precision != IPM_PREC_MIXED_F32_FACTOR)
     return fail(nullptr, IPM_EINVAL, "ipm_init: unknown precision");
   if (opt.precision == IPM_PREC_MIXED_F32_FACTOR && opt.hessian_reuse != 0)

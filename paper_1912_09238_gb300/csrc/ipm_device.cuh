@@ -18,6 +18,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/ipm.h"
+
 namespace ipm {
 
 enum EntKind { ENT_QUADRATIC = 0, ENT_BARRIER = 1, ENT_EULER = 2 };
@@ -355,6 +357,80 @@ __device__ __forceinline__ double node_speed<PHYS_EULER2D, 4>(const double* u, d
   const double v1 = u[1] / u[0], v2 = u[2] / u[0];
   const double p = (g - 1.0) * (u[3] - 0.5 * (u[1] * v1 + u[2] * v2));
   return fmax(fabs(v1), fabs(v2)) + sqrt(g * p / u[0]);
+}
+
+// cell index of the left (side < 0) or right neighbour of interior cell j of a 1-D mesh, resolved
+// through the boundary condition: outflow reads the cell itself, periodic the opposite end,
+// Dirichlet the fixed ghost
+__device__ __forceinline__ int neighbour(int j, int nx, int side, int bc) {
+  // side -1: left neighbour of j, +1: right neighbour
+  if (side < 0) {
+    if (j > 1) return j - 1;
+    return bc == IPM_BC_OUTFLOW ? 1 : (bc == IPM_BC_PERIODIC ? nx : 0);
+  }
+  if (j < nx) return j + 1;
+  return bc == IPM_BC_OUTFLOW ? nx : (bc == IPM_BC_PERIODIC ? 1 : nx + 1);
+}
+
+// physical flux of the 1-D systems (App. A Burgers; Sec. 7.1 Euler)
+template <int PHYS, int M>
+struct Flux1D;
+template <>
+struct Flux1D<PHYS_BURGERS, 1> {
+  __device__ static void f(const double* u, double, double* out) { out[0] = 0.5 * u[0] * u[0]; }
+};
+template <>
+struct Flux1D<PHYS_EULER1D, 3> {
+  __device__ static void f(const double* u, double g, double* out) {
+    const double v = u[1] / u[0];
+    const double p = (g - 1.0) * (u[2] - 0.5 * u[1] * v);
+    out[0] = u[1];
+    out[1] = fma(u[1], v, p);
+    out[2] = (u[2] + p) * v;
+  }
+};
+
+// F(u).n and |v.n| + c for the 2-D Euler system
+__device__ __forceinline__ double euler2d_normal_flux(const double* u, double nx, double ny, double g, double* f) {
+  const double rho = u[0], ir = 1.0 / rho;
+  const double v1 = u[1] * ir, v2 = u[2] * ir;
+  const double p = (g - 1.0) * (u[3] - 0.5 * (u[1] * v1 + u[2] * v2));
+  const double vn = v1 * nx + v2 * ny;
+  f[0] = rho * vn;
+  f[1] = fma(u[1], vn, p * nx);
+  f[2] = fma(u[2], vn, p * ny);
+  f[3] = (u[3] + p) * vn;
+  return fabs(vn) + sqrt(g * p * ir);
+}
+
+// Rusanov flux from a (behind) to b (ahead) across unit normal n
+__device__ __forceinline__ void rusanov2d(const double* ua, const double* ub, double nx, double ny, double g,
+                                          double* out) {
+  double fa[4], fb[4];
+  const double sa = euler2d_normal_flux(ua, nx, ny, g, fa);
+  const double sb = euler2d_normal_flux(ub, nx, ny, g, fb);
+  const double s = fmax(sa, sb);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out[c] = 0.5 * (fa[c] + fb[c]) - 0.5 * s * (ub[c] - ua[c]);
+}
+
+__device__ __forceinline__ void reflect(const double* u, double nx, double ny, double* out) {
+  const double mn = u[1] * nx + u[2] * ny;
+  out[0] = u[0];
+  out[1] = u[1] - 2.0 * mn * nx;
+  out[2] = u[2] - 2.0 * mn * ny;
+  out[3] = u[3];
+}
+
+__device__ __forceinline__ int cell2d(int i, int j, int nx) { return (j + 1) * (nx + 2) + (i + 1); }
+
+// state beyond a boundary face: the neighbour cell index, or -1 for the cell itself (outflow),
+// or -2 for the reflected state (slip wall)
+__device__ __forceinline__ int outside(int bc, int wrap_cell, int ghost_cell) {
+  if (bc == IPM_BC_PERIODIC) return wrap_cell;
+  if (bc == IPM_BC_DIRICHLET) return ghost_cell;
+  if (bc == IPM_BC_SLIP_WALL) return -2;
+  return -1;
 }
 
 __device__ inline double warp_sum(double v) {

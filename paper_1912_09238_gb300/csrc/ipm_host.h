@@ -30,6 +30,7 @@ struct Mesh2DHost {
 };
 
 void set_global_error(const std::string& msg);
+const char* check_problem(const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad);
 void build_mesh2d(const ipm_problem& pr, Mesh2DHost& m);
 void gauss_legendre_1d(int n, std::vector<double>& x, std::vector<double>& w);
 void build_tables(int p, int M, int nq, HostTables& t);

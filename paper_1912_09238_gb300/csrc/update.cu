@@ -9,39 +9,13 @@
 // dt = CFL dx / max speed (the maximum the Newton kernel folded into StepScalars), clipped to t_end.
 // Ghost neighbours are resolved through the boundary condition: outflow reads the cell itself,
 // periodic the opposite end, Dirichlet the fixed ghost.
+#include "ic.cuh"
 #include "ipm_host.h"
 
 namespace ipm {
 
 constexpr int UT = 256;
 constexpr int UWARPS = UT / 32;
-
-template <int PHYS, int M>
-struct Flux1D;
-template <>
-struct Flux1D<PHYS_BURGERS, 1> {
-  __device__ static void f(const double* u, double, double* out) { out[0] = 0.5 * u[0] * u[0]; }
-};
-template <>
-struct Flux1D<PHYS_EULER1D, 3> {
-  __device__ static void f(const double* u, double g, double* out) {
-    const double v = u[1] / u[0];
-    const double p = (g - 1.0) * (u[2] - 0.5 * u[1] * v);
-    out[0] = u[1];
-    out[1] = fma(u[1], v, p);
-    out[2] = (u[2] + p) * v;
-  }
-};
-
-__device__ __forceinline__ int neighbour(int j, int nx, int side, int bc) {
-  // side -1: left neighbour of j, +1: right neighbour
-  if (side < 0) {
-    if (j > 1) return j - 1;
-    return bc == IPM_BC_OUTFLOW ? 1 : (bc == IPM_BC_PERIODIC ? nx : 0);
-  }
-  if (j < nx) return j + 1;
-  return bc == IPM_BC_OUTFLOW ? nx : (bc == IPM_BC_PERIODIC ? 1 : nx + 1);
-}
 
 __device__ __forceinline__ double step_dt(const Update1DArgs& a) {
   if (a.dt_override > 0.0) return a.dt_override;
@@ -158,31 +132,11 @@ cudaError_t launch_update1d(int phys, int m, const Update1DArgs& a, int grid, cu
 struct InitArgs {
   Tables tab;
   EntParams ent;
-  double x_lo, dx, gamma;
-  double x0, dx0[3];
-  double left[4], dleft[4][3], right[4], dright[4][3];
+  IC1D ic;
   double* uhat;
   double* lam;
   int n_cells;
 };
-
-template <int ENT, int M>
-__device__ void primitive_to_conserved(const double* prim, double gamma, double* u) {
-  if (M == 1) {
-    u[0] = prim[0];
-  } else {
-    constexpr int D = M - 2;
-    const double rho = prim[0], p = prim[D + 1];
-    double vsq = 0.0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      u[1 + d] = rho * prim[1 + d];
-      vsq = fma(prim[1 + d], prim[1 + d], vsq);
-    }
-    u[0] = rho;
-    u[M - 1] = p / (gamma - 1.0) + 0.5 * rho * vsq;
-  }
-}
 
 template <int ENT, int M>
 __global__ void __launch_bounds__(UT) k_init1d(InitArgs a) {
@@ -192,27 +146,11 @@ __global__ void __launch_bounds__(UT) k_init1d(InitArgs a) {
   double* s_e = sm + M * Q;    // [M][Q] w * grad s(ubar)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int j = blockIdx.x; j < a.n_cells; j += gridDim.x) {
-    const double x_left = a.x_lo + (j - 1) * a.dx;
     for (int q = tid; q < Q; q += UT) {
       double xi[3] = {0.0, 0.0, 0.0};
       for (int d = 0; d < P; ++d) xi[d] = a.tab.nodes[(size_t)q * P + d];
-      double x0 = a.x0, pl[4], pr[4];
-      for (int d = 0; d < P; ++d) x0 = fma(a.dx0[d], xi[d], x0);
-      const int nprim = (M == 1) ? 1 : M;
-      for (int v = 0; v < nprim; ++v) {
-        pl[v] = a.left[v];
-        pr[v] = a.right[v];
-        for (int d = 0; d < P; ++d) {
-          pl[v] = fma(a.dleft[v][d], xi[d], pl[v]);
-          pr[v] = fma(a.dright[v][d], xi[d], pr[v]);
-        }
-      }
-      double UL[M], UR[M], ub[M], ge[M];
-      primitive_to_conserved<ENT, M>(pl, a.gamma, UL);
-      primitive_to_conserved<ENT, M>(pr, a.gamma, UR);
-      const double frac = fmin(fmax((x0 - x_left) / a.dx, 0.0), 1.0);
-#pragma unroll
-      for (int c = 0; c < M; ++c) ub[c] = frac * UL[c] + (1.0 - frac) * UR[c];
+      double ub[M], ge[M];
+      ic1d_average<M>(a.ic, j, xi, P, ub);
       entropy_gradient<ENT, M>(ub, a.ent, ge);
       const double wq = a.tab.w[q];
 #pragma unroll
@@ -252,19 +190,7 @@ cudaError_t launch_init1d(int ent, int m, const Tables& tab, const EntParams& en
   InitArgs a;
   a.tab = tab;
   a.ent = ent_p;
-  a.x_lo = prob.x_lo;
-  a.dx = (prob.x_hi - prob.x_lo) / prob.nx;
-  a.gamma = prob.gamma;
-  a.x0 = prob.ic_x0;
-  for (int d = 0; d < 3; ++d) a.dx0[d] = prob.ic_dx0[d];
-  for (int v = 0; v < 4; ++v) {
-    a.left[v] = prob.ic_left[v];
-    a.right[v] = prob.ic_right[v];
-    for (int d = 0; d < 3; ++d) {
-      a.dleft[v][d] = prob.ic_dleft[v][d];
-      a.dright[v][d] = prob.ic_dright[v][d];
-    }
-  }
+  a.ic = ic1d_params(prob);
   a.uhat = uhat;
   a.lam = lam;
   a.n_cells = n_cells;

@@ -13,55 +13,13 @@
 // clipped to t_end on Algorithm-1 steps.
 #include <cmath>
 
+#include "ic.cuh"
 #include "ipm_host.h"
 
 namespace ipm {
 
 constexpr int T2 = 256;
 constexpr int W2 = T2 / 32;
-
-// F(u).n and |v.n| + c for the 2-D Euler system
-__device__ __forceinline__ double euler2d_normal_flux(const double* u, double nx, double ny, double g, double* f) {
-  const double rho = u[0], ir = 1.0 / rho;
-  const double v1 = u[1] * ir, v2 = u[2] * ir;
-  const double p = (g - 1.0) * (u[3] - 0.5 * (u[1] * v1 + u[2] * v2));
-  const double vn = v1 * nx + v2 * ny;
-  f[0] = rho * vn;
-  f[1] = fma(u[1], vn, p * nx);
-  f[2] = fma(u[2], vn, p * ny);
-  f[3] = (u[3] + p) * vn;
-  return fabs(vn) + sqrt(g * p * ir);
-}
-
-// Rusanov flux from a (behind) to b (ahead) across unit normal n
-__device__ __forceinline__ void rusanov2d(const double* ua, const double* ub, double nx, double ny, double g,
-                                          double* out) {
-  double fa[4], fb[4];
-  const double sa = euler2d_normal_flux(ua, nx, ny, g, fa);
-  const double sb = euler2d_normal_flux(ub, nx, ny, g, fb);
-  const double s = fmax(sa, sb);
-#pragma unroll
-  for (int c = 0; c < 4; ++c) out[c] = 0.5 * (fa[c] + fb[c]) - 0.5 * s * (ub[c] - ua[c]);
-}
-
-__device__ __forceinline__ void reflect(const double* u, double nx, double ny, double* out) {
-  const double mn = u[1] * nx + u[2] * ny;
-  out[0] = u[0];
-  out[1] = u[1] - 2.0 * mn * nx;
-  out[2] = u[2] - 2.0 * mn * ny;
-  out[3] = u[3];
-}
-
-__device__ __forceinline__ int cell2d(int i, int j, int nx) { return (j + 1) * (nx + 2) + (i + 1); }
-
-// state beyond a boundary face: the neighbour cell index, or -1 for the cell itself (outflow),
-// or -2 for the reflected state (slip wall)
-__device__ __forceinline__ int outside(int bc, int wrap_cell, int ghost_cell) {
-  if (bc == IPM_BC_PERIODIC) return wrap_cell;
-  if (bc == IPM_BC_DIRICHLET) return ghost_cell;
-  if (bc == IPM_BC_SLIP_WALL) return -2;
-  return -1;
-}
 
 __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
   extern __shared__ __align__(16) double s_v[];     // [4][Q] w * integrand
@@ -382,27 +340,10 @@ cudaError_t launch_update2d(const Update2DArgs& a, int grid, cudaStream_t s) {
 struct Init2DArgs {
   Tables tab;
   EntParams ent;
-  int nx, ny, ic_kind;
-  double x_lo, dx, y_lo, dy, gamma;
-  double x0;
-  double left[4], dleft[4][3], right[4], dright[4][3];
-  double param[4], dparam[4][3];
+  IC2D ic;
   double* uhat;
   double* lam;
 };
-
-__device__ __forceinline__ double affine3(double v0, const double* d, const double* xi, int P) {
-  double v = v0;
-  for (int k = 0; k < P; ++k) v = fma(d[k], xi[k], v);
-  return v;
-}
-
-__device__ __forceinline__ void prim4_to_cons(double rho, double v1, double v2, double p, double g, double* u) {
-  u[0] = rho;
-  u[1] = rho * v1;
-  u[2] = rho * v2;
-  u[3] = p / (g - 1.0) + 0.5 * rho * (v1 * v1 + v2 * v2);
-}
 
 template <int ENT>
 __global__ void __launch_bounds__(T2) k_init2d(Init2DArgs a) {
@@ -412,51 +353,14 @@ __global__ void __launch_bounds__(T2) k_init2d(Init2DArgs a) {
   double* s_u = sm;            // [M][Q] w * ubar
   double* s_e = sm + M * Q;    // [M][Q] w * grad s(ubar)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nx = a.nx, ny = a.ny, n_cells = (nx + 2) * (ny + 2);
+  const int nx = a.ic.nx, ny = a.ic.ny, n_cells = (nx + 2) * (ny + 2);
   for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
     const int ii = c % (nx + 2), jj = c / (nx + 2);              // ghost-inclusive column and row
     for (int q = tid; q < Q; q += T2) {
       double xi[3] = {0.0, 0.0, 0.0};
       for (int d = 0; d < P; ++d) xi[d] = a.tab.nodes[(size_t)q * P + d];
       double ub[M], ge[M];
-      if (a.ic_kind == IPM_IC_FREESTREAM) {
-        const double rho = a.param[0], p = a.param[1];
-        const double mach = affine3(a.param[2], a.dparam[2], xi, P);
-        const double th = affine3(a.param[3], a.dparam[3], xi, P) * (M_PI / 180.0);
-        const double cs = sqrt(a.gamma * p / rho);
-        prim4_to_cons(rho, mach * cs * cos(th), mach * cs * sin(th), p, a.gamma, ub);
-      } else if (a.ic_kind == IPM_IC_SHEAR) {
-        // ghosts repeat the periodic interior
-        const int iw = ii == 0 ? nx : (ii == nx + 1 ? 1 : ii);
-        const int jw = jj == 0 ? ny : (jj == ny + 1 ? 1 : jj);
-        const double ylo = a.y_lo + (jw - 1) * a.dy, yhi = ylo + a.dy;
-        const double xc = a.x_lo + (iw - 0.5) * a.dx;
-        const double amp = affine3(a.param[0], a.dparam[0], xi, P);
-        const double ph = affine3(a.param[1], a.dparam[1], xi, P);
-        const double hw = affine3(a.param[2], a.dparam[2], xi, P);
-        const double ym = a.y_lo + 0.5 * a.dy * ny;
-        const double f = fmax(fmin(yhi, ym + hw) - fmax(ylo, ym - hw), 0.0) / a.dy;
-        const double v2 = amp * sin(a.param[3] * (xc + ph));
-        const double rin = a.left[0], vin = a.left[1], rout = a.right[0], vout = a.right[1], p = a.left[3];
-        const double rho = f * rin + (1.0 - f) * rout;
-        ub[0] = rho;
-        ub[1] = f * rin * vin + (1.0 - f) * rout * vout;
-        ub[2] = rho * v2;
-        ub[3] = p / (a.gamma - 1.0) + 0.5 * f * rin * (vin * vin + v2 * v2) + 0.5 * (1.0 - f) * rout * (vout * vout + v2 * v2);
-      } else {
-        // x-Riemann: exact cell average in x of the two states
-        double pl[4], pr[4], UL[M], UR[M];
-        for (int v = 0; v < 4; ++v) {
-          pl[v] = affine3(a.left[v], a.dleft[v], xi, P);
-          pr[v] = affine3(a.right[v], a.dright[v], xi, P);
-        }
-        prim4_to_cons(pl[0], pl[1], pl[2], pl[3], a.gamma, UL);
-        prim4_to_cons(pr[0], pr[1], pr[2], pr[3], a.gamma, UR);
-        const double x_left = a.x_lo + (ii - 1) * a.dx;
-        const double frac = fmin(fmax((a.x0 - x_left) / a.dx, 0.0), 1.0);
-#pragma unroll
-        for (int k = 0; k < M; ++k) ub[k] = frac * UL[k] + (1.0 - frac) * UR[k];
-      }
+      ic2d_average(a.ic, ii, jj, xi, P, ub);
       entropy_gradient<ENT, M>(ub, a.ent, ge);
       const double wq = a.tab.w[q];
 #pragma unroll
@@ -496,25 +400,7 @@ cudaError_t launch_init2d(int ent, const Tables& tab, const EntParams& ent_p, co
   Init2DArgs a;
   a.tab = tab;
   a.ent = ent_p;
-  a.nx = prob.nx;
-  a.ny = prob.ny;
-  a.ic_kind = prob.ic_kind;
-  a.x_lo = prob.x_lo;
-  a.dx = (prob.x_hi - prob.x_lo) / prob.nx;
-  a.y_lo = prob.y_lo;
-  a.dy = (prob.y_hi - prob.y_lo) / prob.ny;
-  a.gamma = prob.gamma;
-  a.x0 = prob.ic_x0;
-  for (int v = 0; v < 4; ++v) {
-    a.left[v] = prob.ic_left[v];
-    a.right[v] = prob.ic_right[v];
-    a.param[v] = prob.ic_param[v];
-    for (int d = 0; d < 3; ++d) {
-      a.dleft[v][d] = prob.ic_dleft[v][d];
-      a.dright[v][d] = prob.ic_dright[v][d];
-      a.dparam[v][d] = prob.ic_dparam[v][d];
-    }
-  }
+  a.ic = ic2d_params(prob);
   a.uhat = uhat;
   a.lam = lam;
   const int n_cells = (prob.nx + 2) * (prob.ny + 2);

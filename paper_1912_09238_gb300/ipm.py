@@ -81,6 +81,15 @@ class ipm_result(ctypes.Structure):
                 ("error", ctypes.c_char * 192)]
 
 
+class ipm_sc_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("max_node_steps", ctypes.c_int64), ("active_nodes", ctypes.c_int32),
+                ("t_min", ctypes.c_double), ("t_max", ctypes.c_double), ("residual_max", ctypes.c_double),
+                ("elapsed_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class IpmError(RuntimeError):
     def __init__(self, call, status, msg):
         super().__init__(f"{call} -> {STATUS_NAMES.get(status, status)}: {msg}")
@@ -133,6 +142,15 @@ SIGNATURES = [
     ("ipm_server_destroy", None, [_vp]),
     ("ipm_tables", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   _P(ctypes.c_int), _dp, _dp, _dp, _P(ctypes.c_int), _P(ctypes.c_int)]),
+    ("ipm_sc_init", ctypes.c_int, [_P(ipm_problem), _P(ipm_basis), _P(ipm_quadrature), ctypes.c_double, _P(_vp)]),
+    ("ipm_sc_step", ctypes.c_int, [_vp, _P(ipm_sc_stats)]),
+    ("ipm_sc_run", ctypes.c_int, [_vp, ctypes.c_int64, _P(ipm_sc_stats)]),
+    ("ipm_sc_get_nodal", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
+    ("ipm_sc_get_moments", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
+    ("ipm_sc_get_node_info", ctypes.c_int, [_vp, _P(ctypes.c_int64), _dp, _dp, ctypes.c_size_t]),
+    ("ipm_sc_get_dims", ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int), _P(ctypes.c_int)]),
+    ("ipm_sc_last_error", ctypes.c_char_p, [_vp]),
+    ("ipm_sc_destroy", None, [_vp]),
 ]
 
 
@@ -424,3 +442,72 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class Collocation:
+    """Stochastic Collocation on the GPU (ipm_sc_*): one deterministic run per quadrature node with the
+    IPM update's flux, each node on its own time steps; see include/ipm.h."""
+
+    def __init__(self, problem, p, total_degree, n_per_dim, steady_tol=0.0):
+        import numpy as np  # noqa: F401
+        self.h = None
+        h = _vp()
+        b = ipm_basis(p=p, total_degree=total_degree)
+        q = ipm_quadrature(n_per_dim=n_per_dim)
+        st = lib().ipm_sc_init(ctypes.byref(problem), ctypes.byref(b), ctypes.byref(q), float(steady_tol),
+                               ctypes.byref(h))
+        if st != IPM_OK:
+            msg = lib().ipm_sc_last_error(None)
+            raise IpmError("ipm_sc_init", st, msg.decode() if msg else "")
+        self.h = h
+        c, n, N, m = (ctypes.c_int() for _ in range(4))
+        lib().ipm_sc_get_dims(self.h, ctypes.byref(c), ctypes.byref(n), ctypes.byref(N), ctypes.byref(m))
+        self.n_cells, self.Q, self.N, self.m = c.value, n.value, N.value, m.value
+
+    def _check(self, call, st):
+        if st != IPM_OK:
+            msg = lib().ipm_sc_last_error(self.h)
+            raise IpmError(call, st, msg.decode() if msg else "")
+
+    def close(self):
+        if self.h:
+            lib().ipm_sc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self):
+        s = ipm_sc_stats()
+        self._check("ipm_sc_step", lib().ipm_sc_step(self.h, ctypes.byref(s)))
+        return s
+
+    def run(self, max_steps=2 ** 62):
+        s = ipm_sc_stats()
+        self._check("ipm_sc_run", lib().ipm_sc_run(self.h, int(max_steps), ctypes.byref(s)))
+        return s
+
+    def get_nodal(self):
+        import numpy as np
+        a = np.empty((self.n_cells, self.Q, self.m))
+        self._check("ipm_sc_get_nodal", lib().ipm_sc_get_nodal(self.h, _dptr(a), a.size))
+        return a
+
+    def get_moments(self):
+        import numpy as np
+        a = np.empty((self.n_cells, self.N, self.m))
+        self._check("ipm_sc_get_moments", lib().ipm_sc_get_moments(self.h, _dptr(a), a.size))
+        return a
+
+    def node_info(self):
+        """(steps, t, residual) per node."""
+        import numpy as np
+        n = np.empty(self.Q, dtype=np.int64)
+        t = np.empty(self.Q)
+        r = np.empty(self.Q)
+        self._check("ipm_sc_get_node_info", lib().ipm_sc_get_node_info(
+            self.h, n.ctypes.data_as(_P(ctypes.c_int64)), _dptr(t), _dptr(r), self.Q))
+        return n, t, r

@@ -68,6 +68,26 @@ def oracle_problem_2d(w, tau=None):
                         t_end=w["t_end"], newton=dual.NewtonOptions(tau=tau if tau is not None else w.get("newton_tol", 1e-10)))
 
 
+def gpu_problem(w):
+    """The ipm_problem of a workload dictionary."""
+    from paper_1912_09238_gb300 import ipm
+    if w["kind"] == "euler2d":
+        return ipm.make_problem_2d(w["nx"], w["ny"], w["x_lo"], w["x_hi"], w["y_lo"], w["y_hi"], sides=w["sides"],
+                                   mesh=w["mesh"], ramp_x0=w["ramp_x0"], ramp_deg=w["ramp_deg"], cfl=w["cfl"],
+                                   t_end=w["t_end"], gamma=w["gamma"], ic=w["ic"], param=w["param"],
+                                   dparam=w.get("dparam"), x0=w.get("x0", 0.5), left=w.get("left", (0, 0, 0, 0)),
+                                   dleft=w.get("dleft"), right=w.get("right", (0, 0, 0, 0)), dright=w.get("dright"))
+    return ipm.make_problem(w["kind"], w["nx"], w["x_lo"], w["x_hi"], bc=w["bc"], cfl=w["cfl"], t_end=w["t_end"],
+                            gamma=w["gamma"], x0=w["x0"], dx0=w["dx0"], left=w["left"], dleft=w.get("dleft"),
+                            right=w["right"], dright=w.get("dright"))
+
+
+def gpu_collocation(w, steady_tol=0.0):
+    """Stochastic Collocation of a workload on the GPU (ipm_sc_*), on the workload's quadrature."""
+    from paper_1912_09238_gb300 import ipm
+    return ipm.Collocation(gpu_problem(w), w["p"], w["M"], w["nq"], steady_tol)
+
+
 def gpu_context(w, precision="fp64", tau=None, **opt):
     from paper_1912_09238_gb300 import ipm
     if w["kind"] == "euler2d":
