@@ -20,6 +20,15 @@ products of every level), so the nodal states of all cells live on the same node
   from u_hat^n; moment update c (Eq. adaptiveFVUpdate) with every stencil cell evaluated with its
   own level's duals and the result projected onto level l^{n+1}; the duals of the next solve are
   lambda^{n+1} padded with zeros or truncated to l^{n+1}.
+* Quadrature per level (Levels.quad_levels; Sec. 5 uses nested rules, Sec. 7 Clenshaw-Curtis levels):
+  level l integrates with the nested tensor Clenshaw-Curtis rule of level quad_levels[l] (a prefix of
+  the finest rule's nodes, with its own weights; prob.space is then a basis.NestedCCSpace). The dual
+  problem of level l uses that rule (Eq. dualIterationFunctionAd, <.>_{Q_l}); the update of a cell
+  whose new level is l integrates over Q_l with every stencil cell's ansatz evaluated at those nodes
+  (the paper: a coarser neighbour is evaluated at the finer nodes); the time step takes the wave
+  speed of each interior cell at the nodes of its new level and of each Dirichlet ghost at the nodes
+  of its own level; the initial moments and duals are projected with the rule of the initial level.
+  Without quad_levels every level shares the one rule of prob.space.
 
 Pinned by: tests/test_oracle_adaptive.py (indicator against its integral definition on the nodes,
 level rules, a single level reproducing the fixed-degree scheme, pad/truncate bookkeeping,
@@ -55,6 +64,23 @@ class Levels:
     degrees: tuple          # consecutive total degrees, coarsest first
     delta_lo: float
     delta_hi: float
+    quad_levels: tuple = None   # Clenshaw-Curtis level of every refinement level (nested rules), or None
+
+
+def level_space(prob, lv: Levels, l: int):
+    """Basis and quadrature of refinement level l: the first N_l basis functions with the shared rule,
+    or with the level's nested Clenshaw-Curtis rule."""
+    nl, _ = level_sizes(prob.space, lv)
+    if lv.quad_levels is None:
+        return SubSpace(prob.space, nl[l])
+    return prob.space.level(lv.quad_levels[l], nl[l])
+
+
+def level_nodes(prob, lv: Levels):
+    """Q_l of every refinement level."""
+    if lv.quad_levels is None:
+        return [prob.space.Q] * len(lv.degrees)
+    return [prob.space.level_q(k) for k in lv.quad_levels]
 
 
 def indicator(uhat0, n_l, n_prev):
@@ -116,18 +142,62 @@ def initial_state(prob: s2.Problem2D, lv: Levels) -> AdaptiveState:
     for _ in range(len(nl)):
         S = _indicator_levels(st.uhat, level, nl, nprev)
         level = np.where((S < lo) & (level > 0), level - 1, level)
-    out = AdaptiveState(uhat=truncate(st.uhat, level, nl), lam=truncate(st.lam, level, nl), level=level)
+    if lv.quad_levels is None:
+        out = AdaptiveState(uhat=truncate(st.uhat, level, nl), lam=truncate(st.lam, level, nl), level=level)
+    else:
+        # the initial level's own rule: u_j^0 = <u_IC phi_l>_{Q_l} (Algorithm 3, first loop)
+        ny, nx = prob.mesh.ny, prob.mesh.nx
+        ubar = prob.ic.cell_states(prob.phys, prob.mesh, prob.space.nodes, ny + 2, nx + 2)
+        gs = prob.ent.grad_s(ubar)
+        uhat, lam = np.zeros_like(st.uhat), np.zeros_like(st.lam)
+        for l, n in enumerate(nl):
+            sel = np.nonzero(level == l)
+            V = level_space(prob, lv, l)
+            uhat[sel[0], sel[1], :n] = V.project(ubar[sel][:, :V.Q])
+            lam[sel[0], sel[1], :n] = V.project(gs[sel][:, :V.Q])
+        out = AdaptiveState(uhat=uhat, lam=lam, level=level)
     d = s2._dirichlet_mask(prob)
     for l, n in enumerate(nl):
         sel = np.nonzero(d & (level == l))
         if sel[0].size:
-            li, _, stat, _ = dualmod.dual_solve(SubSpace(prob.space, n), prob.ent, out.lam[sel][:, :n],
+            li, _, stat, _ = dualmod.dual_solve(level_space(prob, lv, l), prob.ent, out.lam[sel][:, :n],
                                                 out.uhat[sel][:, :n], prob.newton)
             assert np.all(stat == 0)
             lam_sel = out.lam[sel]
             lam_sel[:, :n] = li
             out.lam[sel] = lam_sel
     return out
+
+
+def _time_step_and_update(prob, lv: Levels, st: AdaptiveState, lam, level, clip):
+    """dt of the step and the new moments (Eq. adaptiveFVUpdate) of the interior cells at their new
+    levels (level: new levels of the interior, the ghosts' own levels)."""
+    nl, _ = level_sizes(prob.space, lv)
+    U = s2.nodal_states(prob, lam)                  # every cell's ansatz at all nodes of prob.space
+    uhat = st.uhat.copy()
+    if lv.quad_levels is None:
+        dt = s2.time_step(prob, U, st.t, clip=clip)
+        uhat[1:-1, 1:-1] = truncate(s2.moment_update(prob, lam, dt), level[1:-1, 1:-1], nl)
+        return dt, uhat
+    # wave speeds at the nodes of each cell's (new) level; interior and Dirichlet ghosts
+    qn = np.asarray(level_nodes(prob, lv))[level]                    # (ny+2, nx+2)
+    cells = s2._dirichlet_mask(prob)
+    cells[1:-1, 1:-1] = True
+    speed = prob.phys.speed(U)                                       # (ny+2, nx+2, Q)
+    at = np.arange(U.shape[-2])[None, None, :] < qn[..., None]
+    smax = float(np.max(np.where(at & cells[..., None], speed, 0.0)))
+    dt = prob.cfl * prob.mesh.h_min() / smax
+    if clip and prob.t_end > 0 and st.t + dt > prob.t_end:
+        dt = prob.t_end - st.t
+    inner = s2.nodal_update(prob, U, dt)                             # (ny, nx, Q, m), every node
+    new = np.zeros(uhat[1:-1, 1:-1].shape)
+    for l, n in enumerate(nl):
+        sel = np.nonzero(level[1:-1, 1:-1] == l)
+        if sel[0].size:
+            V = level_space(prob, lv, l)
+            new[sel[0], sel[1], :n] = V.project(inner[sel][:, :V.Q])
+    uhat[1:-1, 1:-1] = new
+    return dt, uhat
 
 
 def ipm_step(prob: s2.Problem2D, st: AdaptiveState, lv: Levels) -> AdaptiveState:
@@ -142,7 +212,7 @@ def ipm_step(prob: s2.Problem2D, st: AdaptiveState, lv: Levels) -> AdaptiveState
         sel = np.nonzero(inner_level == l)
         if sel[0].size == 0:
             continue
-        sub = SubSpace(prob.space, n)
+        sub = level_space(prob, lv, l)
         jj, ii = sel[0] + 1, sel[1] + 1
         li, itl, sl, _ = dualmod.dual_solve(sub, prob.ent, st.lam[jj, ii, :n], st.uhat[jj, ii, :n], prob.newton)
         lam[jj, ii, :n] = li
@@ -151,10 +221,7 @@ def ipm_step(prob: s2.Problem2D, st: AdaptiveState, lv: Levels) -> AdaptiveState
     level = st.level.copy()
     level[1:-1, 1:-1], _ = new_levels(st.uhat[1:-1, 1:-1], inner_level, nl, nprev, lv)
     # periodic ghosts mirror the levels of the cells they copy (they are never read by the update)
-    U = s2.nodal_states(prob, lam)
-    dt = s2.time_step(prob, U, st.t)
-    uhat = st.uhat.copy()
-    uhat[1:-1, 1:-1] = truncate(s2.moment_update(prob, lam, dt), level[1:-1, 1:-1], nl)
+    dt, uhat = _time_step_and_update(prob, lv, st, lam, level, clip=True)
     lam_next = lam.copy()
     lam_next[1:-1, 1:-1] = truncate(lam[1:-1, 1:-1], level[1:-1, 1:-1], nl)
     res = s2.steady_residual(prob, uhat, st.uhat)
@@ -188,7 +255,7 @@ def oneshot_step(prob: s2.Problem2D, st: AdaptiveState, lv: Levels, cap: int) ->
         sel = np.nonzero(inner_level == l)
         if sel[0].size == 0:
             continue
-        sub = SubSpace(prob.space, n)
+        sub = level_space(prob, lv, l)
         jj, ii = sel[0] + 1, sel[1] + 1
         li, itl, sl, _ = dualmod.dual_solve(sub, prob.ent, st.lam[jj, ii, :n], st.uhat[jj, ii, :n], prob.newton,
                                             one_step=True)
@@ -198,10 +265,7 @@ def oneshot_step(prob: s2.Problem2D, st: AdaptiveState, lv: Levels, cap: int) ->
     level = st.level.copy()
     new, _ = new_levels(st.uhat[1:-1, 1:-1], inner_level, nl, nprev, lv)
     level[1:-1, 1:-1] = np.minimum(new, cap)
-    U = s2.nodal_states(prob, lam)
-    dt = s2.time_step(prob, U, st.t, clip=False)
-    uhat = st.uhat.copy()
-    uhat[1:-1, 1:-1] = truncate(s2.moment_update(prob, lam, dt), level[1:-1, 1:-1], nl)
+    dt, uhat = _time_step_and_update(prob, lv, st, lam, level, clip=False)
     lam_next = lam.copy()
     lam_next[1:-1, 1:-1] = truncate(lam[1:-1, 1:-1], level[1:-1, 1:-1], nl)
     res = s2.steady_residual(prob, uhat, st.uhat)

@@ -108,3 +108,71 @@ def test_oneshot_step_with_cap_zero_is_the_fixed_low_degree_oneshot():
         f = s2.oneshot_step(prob2, f)
         assert np.abs(a.uhat[..., :nl[0], :] - f.uhat).max() < 1e-12
         assert np.all(a.uhat[..., nl[0]:, :] == 0.0)
+
+
+# ---------- quadrature per refinement level (nested Clenshaw-Curtis rules, Sec. 5 and Sec. 7) ----------
+def _kh_cc(nx=8, M=2, kmax=3, p=2):
+    """The shear layer with two uncertain dims (band half-width 0.25 + 0.05 xi_1, phase 0.1 xi_2) in a
+    nested Clenshaw-Curtis space of level kmax."""
+    w = workloads.variant(workloads.KH_2D, nx=nx, ny=nx, M=M, nq=3, dparam=((0.005, 0.0, 0.0), (0.0, 0.1, 0.0),
+                                                                          (0.05, 0.0, 0.0), (0.0, 0.0, 0.0)), p=p)
+    prob = oracle_problem_2d(w)
+    prob.space = basis.NestedCCSpace(p, M, kmax)
+    return w, prob
+
+
+def test_single_level_with_its_own_rule_is_the_fixed_rule_scheme():
+    """One refinement level on the level-2 rule, inside a level-3 nested space, equals the fixed-degree
+    scheme whose space is the level-2 rule itself."""
+    _, prob = _kh_cc(kmax=3)
+    lv = ad.Levels(degrees=(2,), delta_lo=2e-5, delta_hi=2e-4, quad_levels=(2,))
+    _, ref = _kh_cc(kmax=2)
+    a = ad.initial_state(prob, lv)
+    f = s2.initial_state(ref)
+    assert np.abs(a.uhat - f.uhat).max() < 1e-14
+    for _ in range(2):
+        a = ad.ipm_step(prob, a, lv)
+        f = s2.ipm_step(ref, f)
+        assert np.abs(a.uhat - f.uhat).max() < 1e-12
+        assert abs(a.last_dt - f.last_dt) <= 1e-15 * f.last_dt
+
+
+def test_levels_sharing_one_rule_equal_the_shared_rule_scheme():
+    """Two refinement levels that both use the finest rule of the space give the shared-rule scheme."""
+    _, prob = _kh_cc(M=3, kmax=2)
+    lv_q = ad.Levels(degrees=(2, 3), delta_lo=2e-5, delta_hi=2e-4, quad_levels=(2, 2))
+    lv_s = ad.Levels(degrees=(2, 3), delta_lo=2e-5, delta_hi=2e-4)
+    a, b = ad.initial_state(prob, lv_q), ad.initial_state(prob, lv_s)
+    assert np.array_equal(a.level, b.level) and np.abs(a.uhat - b.uhat).max() < 1e-14
+    for _ in range(2):
+        a, b = ad.ipm_step(prob, a, lv_q), ad.ipm_step(prob, b, lv_s)
+        assert np.array_equal(a.level, b.level)
+        assert np.abs(a.uhat - b.uhat).max() < 1e-12
+
+
+def test_per_level_rules_change_levels_keep_zeros_and_conserve_within_one_level():
+    _, prob = _kh_cc(nx=10, M=3, kmax=2)
+    lv = ad.Levels(degrees=(1, 2, 3), delta_lo=2e-5, delta_hi=2e-4, quad_levels=(1, 2, 2))
+    nl, _ = ad.level_sizes(prob.space, lv)
+    st = ad.initial_state(prob, lv)
+    seen = set()
+    for _ in range(3):
+        st = ad.ipm_step(prob, st, lv)
+        assert np.all(st.newton_status == 0)
+        lev = st.level[1:-1, 1:-1]
+        seen |= set(np.unique(lev).tolist())
+        n = np.asarray(nl)[lev]
+        beyond = np.arange(st.uhat.shape[-2])[None, None, :] >= n[..., None]
+        assert np.all(st.uhat[1:-1, 1:-1][beyond] == 0.0)
+    assert len(seen) >= 2
+    # every cell on one level (the coarsest, a 3-point rule per dimension): the fluxes telescope and the
+    # means are conserved up to the dual residuals
+    lv1 = ad.Levels(degrees=(1,), delta_lo=2e-5, delta_hi=2e-4, quad_levels=(1,))
+    st = ad.initial_state(prob, lv1)
+    A = prob.mesh.area()
+    for _ in range(3):
+        old = st
+        st = ad.ipm_step(prob, old, lv1)
+        tot = np.sum(A[..., None] * st.uhat[1:-1, 1:-1, 0, :], axis=(0, 1))
+        tot0 = np.sum(A[..., None] * old.uhat[1:-1, 1:-1, 0, :], axis=(0, 1))
+        assert np.abs(tot - tot0).max() < 1e-9

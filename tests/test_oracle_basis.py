@@ -66,3 +66,68 @@ def test_tensor_weights_are_products():
         a, b = divmod(k, 4)
         assert sp.nodes[k, 0] == x1[a] and sp.nodes[k, 1] == x1[b]
         assert abs(sp.w[k] - w1[a] * w1[b] / 4) < 1e-16
+
+
+# ---------- nested Clenshaw-Curtis rules (Sec. 5 nested quadrature; Sec. 7 levels and counts) ----------
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_clenshaw_curtis_weights_solve_the_moment_equations(k):
+    """Independent of the closed form: the weights that make the rule exact on P_0..P_n at the
+    Chebyshev points (a Legendre Vandermonde solve) are the closed-form weights; all are positive."""
+    x, w = basis.clenshaw_curtis_1d(k)
+    n = x.size
+    V = np.stack([np.polynomial.legendre.legval(x, np.eye(n)[d]) for d in range(n)])
+    rhs = np.zeros(n)
+    rhs[0] = 2.0
+    assert np.abs(np.linalg.solve(V, rhs) - w).max() < 1e-13
+    assert np.all(w > 0) and abs(w.sum() - 2.0) < 1e-14
+    # odd point count: exact one degree beyond the interpolation degree, by symmetry
+    assert abs(np.sum(w * x ** n) - (2.0 / (n + 1) if n % 2 == 0 else 0.0)) < 1e-14
+
+
+def test_clenshaw_curtis_rules_are_nested():
+    for k in range(5):
+        a, _ = basis.clenshaw_curtis_1d(k)
+        b, _ = basis.clenshaw_curtis_1d(k + 1)
+        assert all(np.min(np.abs(b - v)) == 0.0 for v in a)
+
+
+def test_paper_clenshaw_curtis_point_counts():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "clenshaw_curtis_points.txt")
+    rows = [tuple(int(t) for t in line.split()) for line in open(path) if line.strip() and not line.startswith("#")]
+    assert len(rows) == 6
+    for p, k, count in rows:
+        if p == 1:
+            assert basis.clenshaw_curtis_1d(k)[0].size == count
+        _, _, W = basis.nested_cc_tensor(p, k)
+        assert W[k].size == count
+
+
+@pytest.mark.parametrize("p,kmax", [(1, 3), (2, 3), (3, 2)])
+def test_nested_tensor_levels_are_prefixes_with_their_own_weights(p, kmax):
+    nodes, birth, W = basis.nested_cc_tensor(p, kmax)
+    assert np.all(np.diff(birth) >= 0)
+    for k in range(kmax + 1):
+        x, w = basis.clenshaw_curtis_1d(k)
+        Qk = W[k].size
+        assert Qk == x.size ** p
+        # the prefix is the level-k tensor grid, and its weights are the level-k tensor weights
+        grid = {tuple(t): np.prod([w[list(x).index(c)] for c in t]) / 2 ** p
+                for t in itertools.product(x, repeat=p)}
+        got = {tuple(v): wt for v, wt in zip(nodes[:Qk], W[k])}
+        assert set(got) == set(grid)
+        assert max(abs(got[t] - grid[t]) for t in grid) < 1e-15
+        # exact for tensor monomials of degree <= 2^k + 1 per dimension (degree 1 at level 0)
+        top = 1 if k == 0 else x.size
+        for e in itertools.product(range(top + 1), repeat=p):
+            exact = np.prod([(1.0 / (d + 1) if d % 2 == 0 else 0.0) for d in e])
+            assert abs(np.sum(W[k] * np.prod(nodes[:Qk] ** np.array(e), axis=1)) - exact) < 1e-14
+
+
+def test_nested_space_is_orthonormal_where_the_rule_is_exact():
+    sp = basis.NestedCCSpace(2, 4, 3)          # degree 8 per dimension needs 9 points: level 3
+    G = sp.Phi.T @ (sp.w[:, None] * sp.Phi)
+    assert np.abs(G - np.eye(sp.N)).max() < 1e-13
+    lv = sp.level(2, 6)                        # degree 2 (6 functions) on the level-2 rule (5 points)
+    G2 = lv.Phi.T @ (lv.w[:, None] * lv.Phi)
+    assert np.abs(G2 - np.eye(6)).max() < 1e-13
