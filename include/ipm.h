@@ -139,8 +139,26 @@ typedef struct {
   int total_degree;         /* M: moments N = C(M+p, p) */
 } ipm_basis;
 
+typedef enum {
+  IPM_QUAD_GAUSS = 0,       /* tensor Gauss-Legendre rule with n_per_dim^p nodes (every level shares it) */
+  IPM_QUAD_CC_NESTED = 1    /* nested tensor Clenshaw-Curtis rules, one per refinement level (Sec. 5: nested
+                               quadrature per level; Sec. 7: Clenshaw-Curtis levels with 2^k + 1 points) */
+} ipm_quad_kind;
+
 typedef struct {
-  int n_per_dim;            /* tensor Gauss-Legendre rule with n_per_dim^p nodes */
+  int n_per_dim;            /* IPM_QUAD_GAUSS: nodes per dimension */
+  int kind;                 /* ipm_quad_kind; 0 (a zero-initialised struct) is the Gauss rule */
+  int cc_level[8];          /* IPM_QUAD_CC_NESTED: Clenshaw-Curtis level k_l of refinement level l (adaptive
+                               contexts, l = 0 .. levels-1; fixed degree: cc_level[0]); the 1-D rule of level
+                               k has 2^k + 1 points (k = 0: the midpoint); k_l must not decrease with l, must
+                               give 2^k_l + 1 >= M_l + 1 points per dimension and be at most 6. All zero: the
+                               smallest k >= 1 with 2^k + 1 >= M_l + 2. The finest level's rule is the node
+                               set of the context: nodal arrays hold (2^k_max + 1)^p nodes, ordered so that
+                               every coarser level's nodes come first. A cell of level l solves its dual
+                               problem with the level-l rule (Eq. dualIterationFunctionAd); its moment update
+                               integrates with the rule of its new level, with every stencil cell's ansatz
+                               evaluated at those nodes (Eq. adaptiveFVUpdate); the time step takes each
+                               cell's wave speed at the nodes of its new level. */
 } ipm_quadrature;
 
 typedef struct {
@@ -395,6 +413,13 @@ ipm_status ipm_server_drain(ipm_server* srv, double timeout_s);
 
 /* Stop the worker: waiting requests are dropped, running ones finish first. NULL is accepted. */
 void ipm_server_destroy(ipm_server* srv);
+
+/* Host-only: the nested Clenshaw-Curtis tables of level kmax (IPM_QUAD_CC_NESTED): nodes Q*p doubles
+ * (Q = (2^kmax + 1)^p, coarser levels first), level_weights (kmax+1)*Q doubles (row k: the level-k
+ * weights of the first (2^k + 1)^p nodes, density folded in, zero beyond), phi Q*N doubles. Any output
+ * may be NULL; IPM_EINVAL for p outside 1..3, kmax outside 0..6 or too small capacities. */
+ipm_status ipm_tables_cc(int p, int total_degree, int kmax, int N_cap, int Q_cap, int* indices, double* nodes,
+                         double* level_weights, double* phi, int* N_out, int* Q_out);
 
 /* Host-only: the basis and quadrature tables the library uses (no GPU needed).
  * indices: N*p ints (graded order), nodes: Q*p doubles, weights: Q doubles (density folded in,

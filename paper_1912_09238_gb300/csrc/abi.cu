@@ -32,6 +32,14 @@ struct ipm_ctx {
   int n_levels = 0;                 // adaptive: levels adapt_min_degree .. total_degree
   int lev_n[8] = {0}, lev_prev[8] = {0};
   int* d_level = nullptr;
+  int* d_level_next = nullptr;      // adaptive: the new level of every cell, set before each Newton launch
+  // quadrature per level (IPM_QUAD_CC_NESTED on an adaptive mesh): nodes and weights [level][Q] of each
+  // level's rule; without it every level uses the table's rule
+  bool level_rules = false;
+  int lev_q[8] = {0};
+  std::vector<double> lev_w;
+  double* d_lev_w = nullptr;
+  int* d_q_eval = nullptr;          // nodes each cell's nodal states must cover (per-level rules)
   double* d_factors = nullptr;      // hessian_reuse 2: kept Cholesky factors per cell
   int* d_factor_valid = nullptr;
   size_t factor_stride = 0;
@@ -152,7 +160,13 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.factor_stride = c->factor_stride;
   a.factor_valid = c->d_factor_valid;
   a.level = c->n_levels ? c->d_level : nullptr;
-  for (int k = 0; k < 8; ++k) a.lev_n[k] = c->lev_n[k];
+  for (int k = 0; k < 8; ++k) {
+    a.lev_n[k] = c->lev_n[k];
+    a.lev_q[k] = c->lev_q[k];
+  }
+  a.lev_w = c->level_rules ? c->d_lev_w : nullptr;
+  a.level_next = c->n_levels ? c->d_level_next : nullptr;
+  a.q_eval = c->level_rules ? c->d_q_eval : nullptr;
   a.mx.phi_img = c->d_phi_img;
   a.mx.phiT32 = c->d_phiT32;
   a.mx.n_pad = c->mx.n_pad;
@@ -217,6 +231,10 @@ static Update2DArgs update2d_args(const ipm_ctx* c, double dt_override, bool res
   }
   u.delta_lo = std::min(c->opt.delta_lo, c->opt.delta_hi);
   u.delta_hi = std::max(c->opt.delta_lo, c->opt.delta_hi);
+  u.level_next = c->n_levels ? c->d_level_next : nullptr;
+  u.q_eval = c->level_rules ? c->d_q_eval : nullptr;
+  for (int k = 0; k < 8; ++k) u.lev_q[k] = c->lev_q[k];
+  u.lev_w = c->level_rules ? c->d_lev_w : nullptr;
   return u;
 }
 
@@ -232,7 +250,14 @@ static cudaError_t launch_newton_ctx(const ipm_ctx* c, const NewtonArgs& a, int 
 
 // enqueue: queue reset, Newton over the interior
 static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), s);
+  cudaError_t e = cudaSuccess;
+  if (c->n_levels) {
+    // the levels of this step's update (from the moments the dual problems are solved for): the Newton
+    // kernel evaluates each cell at the nodes its stencil's updates read and takes the wave speed there
+    e = launch_next_levels(update2d_args(c, 0.0, false, false), s);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), s);
   if (e == cudaSuccess) e = launch_order(c->d_iters, c->n_interior, c->prob.nx, c->is2d ? 1 : 0, c->d_order, s);
   if (e != cudaSuccess) return e;
   NewtonArgs a = newton_args(c, one_step);
@@ -365,7 +390,7 @@ static void free_ctx(ipm_ctx* c) {
   void* ptrs[] = {c->d_Phi, c->d_PhiT, c->d_w, c->d_nodes, c->d_pairs, c->d_uhat, c->d_lam, c->d_unode,
                   c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc,
                   c->d_phiT32, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf, c->d_level,
-                  c->d_factors, c->d_factor_valid};
+                  c->d_factors, c->d_factor_valid, c->d_level_next, c->d_lev_w, c->d_q_eval};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -384,8 +409,10 @@ namespace ipm {
 // Checks of a problem, its basis and its quadrature shared by every entry point that takes them;
 // nullptr when they are valid, else what is wrong.
 const char* check_problem(const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad) {
-  if (basis->p < 1 || basis->p > 3 || basis->total_degree < 0 || quad->n_per_dim < 1)
-    return "basis needs 1 <= p <= 3, M >= 0, n_per_dim >= 1";
+  if (basis->p < 1 || basis->p > 3 || basis->total_degree < 0)
+    return "basis needs 1 <= p <= 3, M >= 0";
+  if (quad->kind != IPM_QUAD_GAUSS && quad->kind != IPM_QUAD_CC_NESTED) return "unknown quadrature kind";
+  if (quad->kind == IPM_QUAD_GAUSS && quad->n_per_dim < 1) return "a Gauss rule needs n_per_dim >= 1";
   if (problem->kind != IPM_BURGERS_1D && problem->kind != IPM_EULER_1D && problem->kind != IPM_EULER_2D)
     return "unknown problem kind";
   if (problem->kind == IPM_EULER_2D) {
@@ -444,9 +471,33 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   if (c->entk == ENT_BARRIER && !(entropy->u_plus > entropy->u_minus)) {
     return fail(nullptr, IPM_EINVAL, "ipm_init: barrier needs u_plus > u_minus");
   }
-  build_tables(basis->p, basis->total_degree, quad->n_per_dim, c->tab);
+  const int L_adapt = opt.adapt_min_degree > 0 ? basis->total_degree - opt.adapt_min_degree + 1 : 0;
+  if (quad->kind == IPM_QUAD_CC_NESTED) {
+    // nested Clenshaw-Curtis rules: one per refinement level (or one for a fixed degree)
+    const int nl = L_adapt > 0 && L_adapt <= 8 ? L_adapt : 1;
+    const int M0 = L_adapt > 0 ? opt.adapt_min_degree : basis->total_degree;
+    int cc[8] = {0};
+    if (const char* why = cc_levels(quad, M0, nl, cc)) return fail(nullptr, IPM_EINVAL, std::string("ipm_init: ") + why);
+    int q1 = 1;
+    for (int d = 0; d < basis->p; ++d) q1 *= (cc[nl - 1] == 0 ? 1 : (1 << cc[nl - 1]) + 1);
+    if (q1 > 40000) return fail(nullptr, IPM_EINVAL, "ipm_init: the finest Clenshaw-Curtis rule has more than 40000 nodes");
+    std::vector<std::vector<double>> lw;
+    build_tables_cc(basis->p, basis->total_degree, cc[nl - 1], c->tab, lw);
+    if (L_adapt > 0) {
+      c->level_rules = true;
+      c->lev_w.assign((size_t)nl * c->tab.Q, 0.0);
+      for (int l = 0; l < nl; ++l) {
+        c->lev_q[l] = (int)lw[cc[l]].size();
+        std::copy(lw[cc[l]].begin(), lw[cc[l]].end(), c->lev_w.begin() + (size_t)l * c->tab.Q);
+      }
+    }
+  } else {
+    build_tables(basis->p, basis->total_degree, quad->n_per_dim, c->tab);
+  }
   c->N = c->tab.N;
   c->Q = c->tab.Q;
+  for (int l = 0; l < 8; ++l)
+    if (!c->level_rules) c->lev_q[l] = c->Q;
   c->NM = c->N * c->m;
   c->n_interior = c->is2d ? problem->nx * problem->ny : problem->nx;
   c->n_cells = c->is2d ? (problem->nx + 2) * (problem->ny + 2) : problem->nx + 2;
@@ -554,7 +605,8 @@ static size_t ctx_footprint(const ipm_ctx* c) {
   if (!c->h_in_smem) b += (size_t)c->newton_grid * c->hwork_stride * 8;
   if (c->mixed) b += N * Q * 4 + (size_t)c->mx.chunks * c->mx.b_chunk_bytes;
   if (c->is2d) b += (c->mesh2d.area.size() + c->mesh2d.xf.size() + c->mesh2d.yf.size()) * 8;
-  if (c->n_levels) b += nc * 4;
+  if (c->n_levels) b += 2 * nc * 4;
+  if (c->level_rules) b += nc * 4 + c->lev_w.size() * 8;
   if (c->factor_stride) b += nc * (c->factor_stride * 8 + 4);
   return b;
 }
@@ -594,6 +646,24 @@ ipm_status ipm_tables(int p, int total_degree, int n_per_dim, int N_cap, int Q_c
   if (indices) std::memcpy(indices, t.indices.data(), t.indices.size() * sizeof(int));
   if (nodes) std::memcpy(nodes, t.nodes.data(), t.nodes.size() * sizeof(double));
   if (weights) std::memcpy(weights, t.w.data(), t.w.size() * sizeof(double));
+  if (phi) std::memcpy(phi, t.Phi.data(), t.Phi.size() * sizeof(double));
+  return IPM_OK;
+}
+
+ipm_status ipm_tables_cc(int p, int total_degree, int kmax, int N_cap, int Q_cap, int* indices, double* nodes,
+                         double* level_weights, double* phi, int* N_out, int* Q_out) {
+  if (p < 1 || p > 3 || total_degree < 0 || kmax < 0 || kmax > 6) return fail(nullptr, IPM_EINVAL, "ipm_tables_cc: bad sizes");
+  HostTables t;
+  std::vector<std::vector<double>> lw;
+  build_tables_cc(p, total_degree, kmax, t, lw);
+  if (N_out) *N_out = t.N;
+  if (Q_out) *Q_out = t.Q;
+  if (t.N > N_cap || t.Q > Q_cap) return fail(nullptr, IPM_EINVAL, "ipm_tables_cc: capacity too small");
+  if (indices) std::memcpy(indices, t.indices.data(), t.indices.size() * sizeof(int));
+  if (nodes) std::memcpy(nodes, t.nodes.data(), t.nodes.size() * sizeof(double));
+  if (level_weights)
+    for (int k = 0; k <= kmax; ++k)
+      for (int q = 0; q < t.Q; ++q) level_weights[(size_t)k * t.Q + q] = q < (int)lw[k].size() ? lw[k][q] : 0.0;
   if (phi) std::memcpy(phi, t.Phi.data(), t.Phi.size() * sizeof(double));
   return IPM_OK;
 }
@@ -683,8 +753,22 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
       CK(launch_init2d(c->entk, dev_tables(c), ent_params(c), c->prob, c->d_uhat, c->d_lam, c->stream), "init kernel");
     if (c->n_levels) {
       CK(cudaMalloc(&c->d_level, (size_t)c->n_cells * sizeof(int)), "cudaMalloc levels");
+      CK(cudaMalloc(&c->d_level_next, (size_t)c->n_cells * sizeof(int)), "cudaMalloc next levels");
+      if (c->level_rules) {
+        CK(upload(&c->d_lev_w, c->lev_w), "upload level weights");
+        CK(upload(&c->d_q_eval, std::vector<int>((size_t)c->n_cells, c->Q)), "upload evaluation nodes");
+      }
       if (st == IPM_OK)
         CK(launch_init_levels(update2d_args(c, 0.0, false, false), c->n_cells, c->stream), "initial levels");
+      // with a rule per level, every cell's initial moments and duals come from its level's rule
+      if (st == IPM_OK && c->level_rules)
+        CK(launch_init2d(c->entk, dev_tables(c), ent_params(c), c->prob, c->d_uhat, c->d_lam, c->stream, c->d_level,
+                         c->lev_n, c->lev_q, c->d_lev_w),
+           "initial data at the level rules");
+      if (st == IPM_OK)
+        CK(cudaMemcpyAsync(c->d_level_next, c->d_level, (size_t)c->n_cells * sizeof(int), cudaMemcpyDeviceToDevice,
+                           c->stream),
+           "copy levels");
     }
   } else {
     CK(launch_init1d(c->entk, c->m, dev_tables(c), ent_params(c), c->prob, c->d_uhat, c->d_lam, c->n_cells, c->stream),

@@ -510,7 +510,19 @@ ipm_status ipm_sc_init(const ipm_problem* problem, const ipm_basis* basis, const
   s->is2d = problem->kind == IPM_EULER_2D;
   s->m = problem->kind == IPM_BURGERS_1D ? 1 : (s->is2d ? 4 : 3);
   s->phys = problem->kind == IPM_BURGERS_1D ? PHYS_BURGERS : (s->is2d ? PHYS_EULER2D : PHYS_EULER1D);
-  build_tables(basis->p, basis->total_degree, quad->n_per_dim, s->tab);
+  if (quad->kind == IPM_QUAD_CC_NESTED) {
+    // the Clenshaw-Curtis rule of cc_level[0] (or the default level for the basis degree), as the
+    // paper's collocation runs use
+    int k = 0;
+    if (const char* why = cc_levels(quad, basis->total_degree, 1, &k)) {
+      delete s;
+      return sc_fail(nullptr, IPM_EINVAL, std::string("ipm_sc_init: ") + why);
+    }
+    std::vector<std::vector<double>> lw;
+    build_tables_cc(basis->p, basis->total_degree, k, s->tab, lw);
+  } else {
+    build_tables(basis->p, basis->total_degree, quad->n_per_dim, s->tab);
+  }
   s->Q = s->tab.Q;
   s->N = s->tab.N;
   s->n_interior = s->is2d ? problem->nx * problem->ny : problem->nx;

@@ -288,6 +288,14 @@ struct NewtonArgs {
   int* factor_valid;     // [cell]
   const int* level;      // adaptive meshes: refinement level per cell (nullptr: every cell at tab.N)
   int lev_n[8];          // moments per level (graded prefixes of the table's basis)
+  // quadrature per level (nested Clenshaw-Curtis rules): nodes of each level's rule (a prefix of the
+  // table's nodes) and its weights [level][tab.Q]; lev_w == nullptr: every level uses tab.w over tab.Q
+  int lev_q[8];
+  const double* lev_w;
+  const int* level_next; // adaptive meshes: the level each cell takes in this step's update (wave speeds
+                         // are taken at that level's nodes), or nullptr
+  const int* q_eval;     // per-level rules: nodes at which each cell's nodal states are written (the
+                         // largest new level's rule over its stencil); the rest of its row is zeroed
   MixedTiles mx;         // mixed path only
   uint32_t off_h, off_a, off_b;  // shared-memory byte offsets: packed H, A staging, Phi chunks
 };
@@ -332,6 +340,10 @@ struct Update2DArgs {
   int n_levels;
   int lev_n[8], lev_prev[8];   // moments of each level and of the level's lower-degree part
   double delta_lo, delta_hi;
+  int* level_next;       // the new level of every cell, set before the Newton kernel (k_next_levels)
+  int* q_eval;           // per-level rules: nodes each cell's nodal states must cover (k_eval_q)
+  int lev_q[8];          // nodes of each level's rule (tab.Q for all with one shared rule)
+  const double* lev_w;   // per-level rules: weights [level][tab.Q], or nullptr
 };
 
 #ifdef __CUDACC__

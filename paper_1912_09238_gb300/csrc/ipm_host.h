@@ -34,6 +34,12 @@ const char* check_problem(const ipm_problem* problem, const ipm_basis* basis, co
 void build_mesh2d(const ipm_problem& pr, Mesh2DHost& m);
 void gauss_legendre_1d(int n, std::vector<double>& x, std::vector<double>& w);
 void build_tables(int p, int M, int nq, HostTables& t);
+void clenshaw_curtis_1d(int k, std::vector<double>& x, std::vector<double>& w);
+// nested tensor Clenshaw-Curtis tables of level kmax; level_w[k]: the level-k weights of the first nodes
+void build_tables_cc(int p, int M, int kmax, HostTables& t, std::vector<std::vector<double>>& level_w);
+// Clenshaw-Curtis level of every refinement level (n of them, total degrees M0, M0+1, ...) from a
+// quadrature description; nullptr when valid, else what is wrong
+const char* cc_levels(const ipm_quadrature* quad, int M0, int n, int* out);
 
 // Tiling of the mixed-precision Hessian (see MixedTiles) and its shared-memory needs.
 struct MixedLayout {
@@ -93,8 +99,14 @@ cudaError_t prepare_update2d(int Q);
 cudaError_t launch_update2d(const Update2DArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_init_levels(const Update2DArgs& a, int n_cells, cudaStream_t s);
 cudaError_t launch_cap_levels(const Update2DArgs& a, int cap, cudaStream_t s);
+// level != nullptr: project every cell at its level (lev_n moments) with its level's rule (lev_q nodes,
+// weights lev_w [level][tab.Q])
 cudaError_t launch_init2d(int ent, const Tables& tab, const EntParams& ent_p, const ipm_problem& prob, double* uhat,
-                          double* lam, cudaStream_t s);
+                          double* lam, cudaStream_t s, const int* level = nullptr, const int* lev_n = nullptr,
+                          const int* lev_q = nullptr, const double* lev_w = nullptr);
+// adaptive meshes: the new level of every interior cell (Eq. errorIndicator on u_hat^n, capped), and with
+// per-level rules the nodes each cell's nodal states must cover
+cudaError_t launch_next_levels(const Update2DArgs& a, cudaStream_t s);
 cudaError_t launch_bc_copy1d(double* uhat, double* lam, int nx, int Nm, int bc_left, int bc_right,
                              cudaStream_t s);
 

@@ -94,7 +94,7 @@ __device__ __forceinline__ void store_block_entry(T* s_H, int a, int b, int i, i
 
 // (b), FP64 on the CUDA cores: one thread per moment pair (i >= j), all B blocks at once.
 template <int M>
-__device__ __forceinline__ void hessian_fp64(const NewtonArgs& a, int N, const double* s_wJ, double* s_H) {
+__device__ __forceinline__ void hessian_fp64(const NewtonArgs& a, int N, int Qc, const double* s_wJ, double* s_H) {
   constexpr int B = packed_count(M);
   const int ldN = a.tab.N, Q = a.tab.Q, NP = N * (N + 1) / 2;
   const double* __restrict__ Phi = a.tab.Phi;
@@ -104,7 +104,7 @@ __device__ __forceinline__ void hessian_fp64(const NewtonArgs& a, int N, const d
     double acc[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) acc[b] = 0.0;
-    for (int q = 0; q < Q; ++q) {
+    for (int q = 0; q < Qc; ++q) {
       const double pq = Phi[(size_t)q * ldN + i] * Phi[(size_t)q * ldN + j];
 #pragma unroll
       for (int b = 0; b < B; ++b) acc[b] = fma(s_wJ[b * Q + q], pq, acc[b]);
@@ -399,7 +399,7 @@ __device__ __forceinline__ bool tc_wait(TcState& t, int k) {
 // widened into the packed FP64 H. s_wJf holds w_k J_k,ab as float [B][Q]. Returns false when a
 // bounded wait ran out (the CTA must stop).
 template <int M, typename T>
-__device__ bool hessian_tc(const NewtonArgs& a, int N, const float* s_wJf, T* s_H, uint8_t* sA, uint8_t* sB,
+__device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJf, T* s_H, uint8_t* sA, uint8_t* sB,
                            TcState& t, int* s_abort) {
   constexpr int B = packed_count(M);
   const MixedTiles& mx = a.mx;
@@ -416,6 +416,8 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, const float* s_wJf, T* s_
   const int tpp = min(mx.tpp, tiles);
   const uint32_t idesc = tc::idesc_bf16_f32(128, n_pad);
   const int groups = mx.kc / 8;
+  // K chunks of this cell's rule (a prefix of the table's nodes; the rest of the last chunk is zero in A)
+  const int chunks = (Qc + mx.kc - 1) / mx.kc;
 
   for (int t0 = 0; t0 < tiles; t0 += tpp) {
     const int nt = min(tpp, tiles - t0);
@@ -425,9 +427,9 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, const float* s_wJf, T* s_
       tc::bulk_g2s(sB, mx.phi_img, b_chunk, &t.bars[1]);
     }
     t.pend[1] = true;
-    for (int c = 0; c < mx.chunks; ++c) {
+    for (int c = 0; c < chunks; ++c) {
       const int buf = c & 1;
-      if (c + 1 < mx.chunks) {
+      if (c + 1 < chunks) {
         // the other buffer was last read by the MMAs of chunk c-1, which have completed
         if (tid == 0) {
           tc::mbar_arrive_expect_tx(&t.bars[1 + (buf ^ 1)], b_chunk);
@@ -449,8 +451,8 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, const float* s_wJf, T* s_
 #pragma unroll
           for (int e = 0; e < 8; e += 2) {
             const int q = q0 + g * 8 + e;
-            const float x0 = q < Q ? wj[q] * ph[q] : 0.f;
-            const float x1 = q + 1 < Q ? wj[q + 1] * ph[q + 1] : 0.f;
+            const float x0 = q < Qc ? wj[q] * ph[q] : 0.f;
+            const float x1 = q + 1 < Qc ? wj[q + 1] * ph[q + 1] : 0.f;
             const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
             const float2 hf = __bfloat1622float2(h);
             const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
@@ -538,8 +540,8 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
   double* s_Lam = s_d + NMX;      // [M][Q]
   double* s_dLam = s_Lam + M * Q; // [M][Q]
   double* s_u = s_dLam + M * Q;   // [M][Q]
-  double* s_wJ = s_u + M * Q;     // [B][Q]  (float [B][Q] on the mixed path)
-  double* s_red = s_wJ + B * Q;   // NWARPS * 8
+  double* s_wJ = s_u + M * Q;     // [B][Q]  (float [B][Q] on the mixed path, half the space)
+  double* s_red = s_wJ + (MIXED ? (B * Q + 1) / 2 : B * Q);   // NWARPS * 8
   double* s_wu = s_red + NWARPS * 8;  // [M][Q] w_k u_k
   double* s_dinv = s_wu + M * Q;      // [NM] reciprocal pivots
   double* s_P = s_dinv + NMX;         // [2][(NM + 1) * PSTR] Cholesky panels (current, next)
@@ -578,6 +580,10 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
     const int cell = a.cell_list ? a.cell_list[wk] : work_cell(wk, a.nx, a.gy);
     const int N = a.level ? a.lev_n[a.level[cell]] : NX;     // moments of this cell's level
     const int NM = N * M;
+    // this cell's quadrature: its level's rule (the first Qc of the table's nodes) or the shared rule
+    const int lev_c = a.level ? a.level[cell] : 0;
+    const int Qc = a.lev_w ? a.lev_q[lev_c] : Q;
+    const double* __restrict__ wc = a.lev_w ? a.lev_w + (size_t)lev_c * Q : w;
     double* lam_g = a.lam + (size_t)cell * NMX;
     const double* uh_g = a.uhat + (size_t)cell * NMX;
     for (int r = tid; r < NM; r += NT) {
@@ -601,7 +607,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
     }
     for (;;) {
       // (a1) reconstruction
-      for (int q = tid; q < Q; q += NT) {
+      for (int q = tid; q < Qc; q += NT) {
         double acc[M];
 #pragma unroll
         for (int c = 0; c < M; ++c) acc[c] = 0.0;
@@ -617,12 +623,12 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       __syncthreads();
       // (a2) closure, cost terms
       double red[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // sum w s*, sum w |s*|, #infeasible, lambda.uhat, sum |lambda uhat|
-      for (int q = tid; q < Q; q += NT) {
+      for (int q = tid; q < Qc; q += NT) {
         double L[M], u[M], J[B], ss;
 #pragma unroll
         for (int c = 0; c < M; ++c) L[c] = s_Lam[c * Q + q];
         const bool ok = Closure<ENT, M>::template eval<true>(L, a.ent, u, J, ss);
-        const double wq = w[q];
+        const double wq = wc[q];
 #pragma unroll
         for (int c = 0; c < M; ++c) {
           s_u[c * Q + q] = u[c];
@@ -654,7 +660,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
         const double* wu = s_wu + c * Q;
         double acc = 0.0;
 #pragma unroll 8
-        for (int q = 0; q < Q; ++q) acc = fma(Phi[(size_t)q * NX + i], wu[q], acc);
+        for (int q = 0; q < Qc; ++q) acc = fma(Phi[(size_t)q * NX + i], wu[q], acc);
         s_g[r] = acc - s_uh[r];
       }
       __syncthreads();
@@ -690,7 +696,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
         float* Hf = reinterpret_cast<float*>(s_H);
         float* Pf = reinterpret_cast<float*>(s_P);
         float* dinvf = reinterpret_cast<float*>(s_dinv);
-        if (!hessian_tc<M, float>(a, N, reinterpret_cast<const float*>(s_wJ), Hf, sA, sB, tcs, &s_abort)) {
+        if (!hessian_tc<M, float>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), Hf, sA, sB, tcs, &s_abort)) {
           if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
           st = ST_TIMEOUT;
           stop = true;
@@ -724,14 +730,14 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       } else {
       // (b) Hessian, packed lower triangle, row index r = i*M + a
       if (MIXED) {
-        if (!hessian_tc<M, double>(a, N, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, tcs, &s_abort)) {
+        if (!hessian_tc<M, double>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, tcs, &s_abort)) {
           if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
           st = ST_TIMEOUT;
           stop = true;
           break;
         }
       } else {
-        hessian_fp64<M>(a, N, s_wJ, s_H);
+        hessian_fp64<M>(a, N, Qc, s_wJ, s_H);
       }
       __syncthreads();
       if (a.h_dump) {
@@ -752,7 +758,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       back_substitute(s_H, NM, s_dinv, s_d);
       }
       // direction at the nodes, slope, Delta . u_hat
-      for (int q = tid; q < Q; q += NT) {
+      for (int q = tid; q < Qc; q += NT) {
         double acc[M];
 #pragma unroll
         for (int c = 0; c < M; ++c) acc[c] = 0.0;
@@ -777,12 +783,12 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       bool accepted = false;
       for (int h = 0; h <= a.max_halvings; ++h) {
         double rr[2] = {0.0, 0.0};
-        for (int q = tid; q < Q; q += NT) {
+        for (int q = tid; q < Qc; q += NT) {
           double L[M], ss;
 #pragma unroll
           for (int c = 0; c < M; ++c) L[c] = fma(alpha, s_dLam[c * Q + q], s_Lam[c * Q + q]);
           const bool ok = Closure<ENT, M>::feasible_sstar(L, a.ent, ss);
-          rr[0] = fma(w[q], ss, rr[0]);
+          rr[0] = fma(wc[q], ss, rr[0]);
           rr[1] += ok ? 0.0 : 1.0;
         }
         block_sum<2>(rr, s_red);
@@ -803,7 +809,28 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
     // results: duals, nodal states at the final duals, counters, signal speed
     for (int r = tid; r < NM; r += NT) lam_g[r] = s_lam[r];
     double* un = a.unode + (size_t)cell * M * Q;
-    for (int r = tid; r < M * Q; r += NT) un[r] = s_u[r];
+    if (a.q_eval) {
+      // per-level rules: the states at the nodes the stencil's updates read beyond this cell's own rule
+      // (the ansatz of the final duals evaluated there), zero beyond them
+      const int qe = a.q_eval[cell];
+      for (int q = Qc + tid; q < qe; q += NT) {
+        double L[M], u[M], ss;
+#pragma unroll
+        for (int c = 0; c < M; ++c) L[c] = 0.0;
+        for (int i = 0; i < N; ++i) {
+          const double ph = PhiT[(size_t)i * Q + q];
+#pragma unroll
+          for (int c = 0; c < M; ++c) L[c] = fma(ph, s_lam[i * M + c], L[c]);
+        }
+        Closure<ENT, M>::template eval<false>(L, a.ent, u, nullptr, ss);
+#pragma unroll
+        for (int c = 0; c < M; ++c) s_u[c * Q + q] = u[c];
+      }
+      __syncthreads();
+      for (int r = tid; r < M * Q; r += NT) un[r] = (r % Q) < qe ? s_u[r] : 0.0;
+    } else {
+      for (int r = tid; r < M * Q; r += NT) un[r] = s_u[r];
+    }
     if (tid == 0) {
       a.iters[cell] = it;
       a.status[cell] = st;
@@ -818,8 +845,10 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       if (tid == 0) a.factor_valid[cell] = 1;
     }
     if (a.track_speed) {
+      // wave speeds at the nodes of the rule this cell's update integrates with
+      const int qs = (a.lev_w && a.level_next) ? a.lev_q[a.level_next[cell]] : Q;
       double smax = 0.0;
-      for (int q = tid; q < Q; q += NT) {
+      for (int q = tid; q < qs; q += NT) {
         double u[M];
 #pragma unroll
         for (int c = 0; c < M; ++c) u[c] = s_u[c * Q + q];
@@ -864,8 +893,9 @@ NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* m
   NewtonSmem s;
   const size_t NM = (size_t)N * m;
   const size_t B = (size_t)m * (m + 1) / 2;
+  const size_t wj = mx ? (B * Q + 1) / 2 : B * Q;     // w J: float on the mixed path
   const size_t fixed =
-      (4 * NM + 4 * (size_t)m * Q + B * Q + NWARPS * 8 + NM + 2 * (NM + 1) * PSTR) * sizeof(double);
+      (4 * NM + 4 * (size_t)m * Q + wj + NWARPS * 8 + NM + 2 * (NM + 1) * PSTR) * sizeof(double);
   const size_t h_bytes = h_in_smem ? packed_aug_count((int)NM) * sizeof(double) : 0;
   s.off_h = (uint32_t)align128(fixed);
   if (!mx) {

@@ -52,6 +52,8 @@ extern "C" ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, con
     return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: n_cells must be in 1..IPM_NOALLOC_MAX_CELLS");
   if (basis->p < 1 || basis->p > 3 || basis->total_degree < 0 || quad->n_per_dim < 1)
     return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: basis needs 1 <= p <= 3, M >= 0, n_per_dim >= 1");
+  if (quad->kind != IPM_QUAD_GAUSS)
+    return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: tensor Gauss rules only");
   int m, phys;
   if (problem_kind == IPM_BURGERS_1D) {
     m = 1;

@@ -43,6 +43,18 @@ __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
   for (int cidx = blockIdx.x; cidx < nx * ny; cidx += gridDim.x) {
     const int i = cidx % nx, j = cidx / nx;
     const int c = cell2d(i, j, nx);
+    // adaptive meshes: the new level (k_next_levels) sets the moments kept and, with a rule per level,
+    // the nodes and weights of the update's quadrature (Eq. adaptiveFVUpdate)
+    int lev_new = 0, n_new = N, Qn = Q;
+    const double* wn = w;
+    if (a.level) {
+      lev_new = a.level_next[c];
+      n_new = a.lev_n[lev_new];
+      if (a.lev_w) {
+        Qn = a.lev_q[lev_new];
+        wn = a.lev_w + (size_t)lev_new * Q;
+      }
+    }
     const double area = a.mesh.area[(size_t)j * nx + i];
     const double* xl = a.mesh.xf + ((size_t)j * (nx + 1) + i) * 3;
     const double* xr = xl + 3;
@@ -53,7 +65,7 @@ __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
     const int nb = j > 0 ? cell2d(i, j - 1, nx) : outside(a.bc[2], cell2d(i, ny - 1, nx), cell2d(i, -1, nx));
     const int nt = j < ny - 1 ? cell2d(i, j + 1, nx) : outside(a.bc[3], cell2d(i, 0, nx), cell2d(i, ny, nx));
     const double r = dt / area;
-    for (int q = tid; q < Q; q += T2) {
+    for (int q = tid; q < Qn; q += T2) {
       double uc[M], un[M], f[M], acc[M];
       const double* ucg = a.unode + (size_t)c * MQ;
 #pragma unroll
@@ -85,35 +97,13 @@ __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
 #pragma unroll
         for (int k = 0; k < M; ++k) acc[k] = fma(sL, f[k], acc[k]);
       }
-      const double wq = w[q];
+      const double wq = wn[q];
 #pragma unroll
       for (int k = 0; k < M; ++k) s_v[k * Q + q] = wq * fma(-r, acc[k], uc[k]);
     }
     __syncthreads();
     double* out = a.uhat + (size_t)c * NM;
     const double old00 = out[0];
-    // adaptive meshes: the new level from the smoothness indicator of the density moments u_hat^n at
-    // the cell's level (Eq. errorIndicator): keep inside [delta_lo, delta_hi], one level down below,
-    // one level up above
-    int n_new = N;
-    int lev_new = 0;
-    if (a.level) {
-      const int lev = a.level[c];
-      const int n_lev = a.lev_n[lev], n_prv = a.lev_prev[lev];
-      double top = 0.0, tot = 0.0;
-      for (int ii = lane; ii < n_lev; ii += 32) {
-        const double v = out[ii * M];
-        tot = fma(v, v, tot);
-        if (ii >= n_prv) top = fma(v, v, top);
-      }
-      top = warp_sum(top);
-      tot = warp_sum(tot);
-      const double S = top / tot;
-      lev_new = S < a.delta_lo ? lev - 1 : (S > a.delta_hi ? lev + 1 : lev);
-      lev_new = min(max(lev_new, 0), min(a.n_levels - 1, a.sc->level_cap));
-      n_new = a.lev_n[lev_new];
-    }
-    __syncthreads();
     for (int ii = warp; ii < N; ii += W2) {
       if (ii >= n_new) {                                   // beyond the new level: moments and duals are zero
         if (lane < M) {
@@ -125,7 +115,7 @@ __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
       double s[M];
 #pragma unroll
       for (int k = 0; k < M; ++k) s[k] = 0.0;
-      for (int q = lane; q < Q; q += 32) {
+      for (int q = lane; q < Qn; q += 32) {
         const double ph = PhiT[(size_t)ii * Q + q];
 #pragma unroll
         for (int k = 0; k < M; ++k) s[k] = fma(ph, s_v[k * Q + q], s[k]);
@@ -141,6 +131,64 @@ __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
     if (tid == 0 && a.level) a.level[c] = lev_new;
     __syncthreads();
   }
+}
+
+// New refinement levels (Algorithm 3, DetermineRefinementLevel) from the smoothness indicator of the
+// density moments u_hat^n at each interior cell's level (Eq. errorIndicator): keep inside
+// [delta_lo, delta_hi], one level down below, one level up above, clamped to 0 .. min(levels - 1, cap).
+// One warp per interior cell.
+__global__ void k_next_levels(Update2DArgs a) {
+  constexpr int M = 4;
+  const int NM = a.tab.N * M, nx = a.mesh.nx, ny = a.mesh.ny;
+  const int lane = threadIdx.x & 31;
+  const int wk = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (wk >= nx * ny) return;
+  const int c = cell2d(wk % nx, wk / nx, nx);
+  const double* u = a.uhat + (size_t)c * NM;
+  const int lev = a.level[c];
+  const int n_lev = a.lev_n[lev], n_prv = a.lev_prev[lev];
+  double top = 0.0, tot = 0.0;
+  for (int ii = lane; ii < n_lev; ii += 32) {
+    const double v = u[ii * M];
+    tot = fma(v, v, tot);
+    if (ii >= n_prv) top = fma(v, v, top);
+  }
+  top = warp_sum(top);
+  tot = warp_sum(tot);
+  const double S = top / tot;
+  int lev_new = S < a.delta_lo ? lev - 1 : (S > a.delta_hi ? lev + 1 : lev);
+  lev_new = min(max(lev_new, 0), min(a.n_levels - 1, a.sc->level_cap));
+  if (lane == 0) a.level_next[c] = lev_new;
+}
+
+// Per-level rules: the nodes each interior cell's nodal states must cover, the largest rule among the new
+// levels of the cell and of the cells its faces read (the paper's coarser neighbour evaluated at the
+// finer nodes). Dirichlet ghosts keep all nodes. One thread per interior cell.
+__global__ void k_eval_q(Update2DArgs a) {
+  const int nx = a.mesh.nx, ny = a.mesh.ny;
+  const int wk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (wk >= nx * ny) return;
+  const int i = wk % nx, j = wk / nx;
+  const int c = cell2d(i, j, nx);
+  const int nb[4] = {i > 0 ? cell2d(i - 1, j, nx) : outside(a.bc[0], cell2d(nx - 1, j, nx), cell2d(-1, j, nx)),
+                     i < nx - 1 ? cell2d(i + 1, j, nx) : outside(a.bc[1], cell2d(0, j, nx), cell2d(nx, j, nx)),
+                     j > 0 ? cell2d(i, j - 1, nx) : outside(a.bc[2], cell2d(i, ny - 1, nx), cell2d(i, -1, nx)),
+                     j < ny - 1 ? cell2d(i, j + 1, nx) : outside(a.bc[3], cell2d(i, 0, nx), cell2d(i, ny, nx))};
+  int e = a.lev_q[a.level_next[c]];
+  for (int f = 0; f < 4; ++f)
+    if (nb[f] >= 0) e = max(e, a.lev_q[a.level_next[nb[f]]]);
+  a.q_eval[c] = e;
+}
+
+cudaError_t launch_next_levels(const Update2DArgs& a, cudaStream_t s) {
+  const int n = a.mesh.nx * a.mesh.ny;
+  k_next_levels<<<(n + 7) / 8, 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && a.q_eval) {
+    k_eval_q<<<(n + 255) / 256, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 // Initial refinement levels (adaptive meshes): from the finest projection, lower the level of every
@@ -230,6 +278,16 @@ __global__ void __launch_bounds__(256) k_update2d_warp(Update2DArgs a) {
   for (int cidx = blockIdx.x * UPD_WARPS + warp; cidx < nx * ny; cidx += gridDim.x * UPD_WARPS) {
     const int i = cidx % nx, j = cidx / nx;
     const int c = cell2d(i, j, nx);
+    int lev_new = 0, n_new = N, Qn = Q;
+    const double* wn = w;
+    if (a.level) {
+      lev_new = a.level_next[c];
+      n_new = a.lev_n[lev_new];
+      if (a.lev_w) {
+        Qn = a.lev_q[lev_new];
+        wn = a.lev_w + (size_t)lev_new * Q;
+      }
+    }
     const double area = a.mesh.area[(size_t)j * nx + i];
     const double* xl = a.mesh.xf + ((size_t)j * (nx + 1) + i) * 3;
     const double* xr = xl + 3;
@@ -240,7 +298,7 @@ __global__ void __launch_bounds__(256) k_update2d_warp(Update2DArgs a) {
     const int nb = j > 0 ? cell2d(i, j - 1, nx) : outside(a.bc[2], cell2d(i, ny - 1, nx), cell2d(i, -1, nx));
     const int nt = j < ny - 1 ? cell2d(i, j + 1, nx) : outside(a.bc[3], cell2d(i, 0, nx), cell2d(i, ny, nx));
     const double r = dt / area;
-    for (int q = lane; q < Q; q += 32) {
+    for (int q = lane; q < Qn; q += 32) {
       double uc[M], un[M], f[M], acc[M];
       const double* ucg = a.unode + (size_t)c * MQ;
 #pragma unroll
@@ -271,37 +329,18 @@ __global__ void __launch_bounds__(256) k_update2d_warp(Update2DArgs a) {
 #pragma unroll
         for (int k = 0; k < M; ++k) acc[k] = fma(sL, f[k], acc[k]);
       }
-      const double wq = w[q];
+      const double wq = wn[q];
 #pragma unroll
       for (int k = 0; k < M; ++k) s_v[k * Q + q] = wq * fma(-r, acc[k], uc[k]);
     }
     __syncwarp();
     double* out = a.uhat + (size_t)c * NM;
     const double old00 = out[0];
-    int n_new = N;
-    int lev_new = 0;
-    if (a.level) {
-      const int lev = a.level[c];
-      const int n_lev = a.lev_n[lev], n_prv = a.lev_prev[lev];
-      double top = 0.0, tot = 0.0;
-      for (int ii = lane; ii < n_lev; ii += 32) {
-        const double v = out[ii * M];
-        tot = fma(v, v, tot);
-        if (ii >= n_prv) top = fma(v, v, top);
-      }
-      top = warp_sum(top);
-      tot = warp_sum(tot);
-      const double S = top / tot;
-      lev_new = S < a.delta_lo ? lev - 1 : (S > a.delta_hi ? lev + 1 : lev);
-      lev_new = min(max(lev_new, 0), min(a.n_levels - 1, a.sc->level_cap));
-      n_new = a.lev_n[lev_new];
-    }
-    __syncwarp();
     for (int rr = lane; rr < NM; rr += 32) {
       const int ii = rr / M, k = rr - ii * M;
       double v = 0.0;
       if (ii < n_new) {
-        for (int q = 0; q < Q; ++q) v = fma(PhiT[(size_t)ii * Q + q], s_v[k * Q + q], v);
+        for (int q = 0; q < Qn; ++q) v = fma(PhiT[(size_t)ii * Q + q], s_v[k * Q + q], v);
       } else {
         a.lam[(size_t)c * NM + rr] = 0.0;
       }
@@ -343,6 +382,9 @@ struct Init2DArgs {
   IC2D ic;
   double* uhat;
   double* lam;
+  const int* level;      // per-level projection (rule per level), or nullptr
+  int lev_n[8], lev_q[8];
+  const double* lev_w;
 };
 
 template <int ENT>
@@ -356,13 +398,21 @@ __global__ void __launch_bounds__(T2) k_init2d(Init2DArgs a) {
   const int nx = a.ic.nx, ny = a.ic.ny, n_cells = (nx + 2) * (ny + 2);
   for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
     const int ii = c % (nx + 2), jj = c / (nx + 2);              // ghost-inclusive column and row
-    for (int q = tid; q < Q; q += T2) {
+    int Nc = N, Qc = Q;
+    const double* wc = a.tab.w;
+    if (a.level) {
+      const int l = a.level[c];
+      Nc = a.lev_n[l];
+      Qc = a.lev_q[l];
+      wc = a.lev_w + (size_t)l * Q;
+    }
+    for (int q = tid; q < Qc; q += T2) {
       double xi[3] = {0.0, 0.0, 0.0};
       for (int d = 0; d < P; ++d) xi[d] = a.tab.nodes[(size_t)q * P + d];
       double ub[M], ge[M];
       ic2d_average(a.ic, ii, jj, xi, P, ub);
       entropy_gradient<ENT, M>(ub, a.ent, ge);
-      const double wq = a.tab.w[q];
+      const double wq = wc[q];
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         s_u[k * Q + q] = wq * ub[k];
@@ -374,7 +424,7 @@ __global__ void __launch_bounds__(T2) k_init2d(Init2DArgs a) {
       double au[M], ae[M];
 #pragma unroll
       for (int k = 0; k < M; ++k) au[k] = ae[k] = 0.0;
-      for (int q = lane; q < Q; q += 32) {
+      for (int q = lane; q < (i < Nc ? Qc : 0); q += 32) {      // moments beyond the level stay zero
         const double ph = a.tab.PhiT[(size_t)i * Q + q];
 #pragma unroll
         for (int k = 0; k < M; ++k) {
@@ -396,11 +446,18 @@ __global__ void __launch_bounds__(T2) k_init2d(Init2DArgs a) {
 }
 
 cudaError_t launch_init2d(int ent, const Tables& tab, const EntParams& ent_p, const ipm_problem& prob, double* uhat,
-                          double* lam, cudaStream_t s) {
+                          double* lam, cudaStream_t s, const int* level, const int* lev_n, const int* lev_q,
+                          const double* lev_w) {
   Init2DArgs a;
   a.tab = tab;
   a.ent = ent_p;
   a.ic = ic2d_params(prob);
+  a.level = level;
+  for (int l = 0; l < 8; ++l) {
+    a.lev_n[l] = level ? lev_n[l] : 0;
+    a.lev_q[l] = level ? lev_q[l] : 0;
+  }
+  a.lev_w = lev_w;
   a.uhat = uhat;
   a.lam = lam;
   const int n_cells = (prob.nx + 2) * (prob.ny + 2);

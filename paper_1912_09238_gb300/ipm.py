@@ -40,7 +40,22 @@ class ipm_basis(ctypes.Structure):
 
 
 class ipm_quadrature(ctypes.Structure):
-    _fields_ = [("n_per_dim", ctypes.c_int)]
+    _fields_ = [("n_per_dim", ctypes.c_int), ("kind", ctypes.c_int), ("cc_level", ctypes.c_int * 8)]
+
+
+def quadrature(n_per_dim=0, cc_levels=None):
+    """ipm_quadrature: the tensor Gauss rule with n_per_dim nodes per dimension, or (cc_levels given)
+    nested Clenshaw-Curtis rules, cc_levels[l] the level of refinement level l (() = the default rule)."""
+    q = ipm_quadrature(n_per_dim=n_per_dim)
+    if cc_levels is not None:
+        q.kind = 1
+        for l, k in enumerate(cc_levels):
+            q.cc_level[l] = k
+    return q
+
+
+def _quad(n_per_dim):
+    return n_per_dim if isinstance(n_per_dim, ipm_quadrature) else ipm_quadrature(n_per_dim=n_per_dim)
 
 
 class ipm_entropy(ctypes.Structure):
@@ -142,6 +157,8 @@ SIGNATURES = [
     ("ipm_server_destroy", None, [_vp]),
     ("ipm_tables", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   _P(ctypes.c_int), _dp, _dp, _dp, _P(ctypes.c_int), _P(ctypes.c_int)]),
+    ("ipm_tables_cc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     _P(ctypes.c_int), _dp, _dp, _dp, _P(ctypes.c_int), _P(ctypes.c_int)]),
     ("ipm_sc_init", ctypes.c_int, [_P(ipm_problem), _P(ipm_basis), _P(ipm_quadrature), ctypes.c_double, _P(_vp)]),
     ("ipm_sc_step", ctypes.c_int, [_vp, _P(ipm_sc_stats)]),
     ("ipm_sc_run", ctypes.c_int, [_vp, ctypes.c_int64, _P(ipm_sc_stats)]),
@@ -204,12 +221,27 @@ def ipm_tables(p, total_degree, n_per_dim):
     return idx, nodes, w, phi
 
 
+def ipm_tables_cc(p, total_degree, kmax):
+    """Host-only nested Clenshaw-Curtis tables: (indices, nodes (Q,p), level weights (kmax+1, Q), Phi (Q,N))."""
+    N = ctypes.c_int()
+    Q = ctypes.c_int()
+    lib().ipm_tables_cc(p, total_degree, kmax, 0, 0, None, None, None, None, ctypes.byref(N), ctypes.byref(Q))
+    n, q = N.value, Q.value
+    idx = np.zeros((n, p), dtype=np.int32)
+    nodes = np.zeros((q, p))
+    w = np.zeros((kmax + 1, q))
+    phi = np.zeros((q, n))
+    _check("ipm_tables_cc", lib().ipm_tables_cc(p, total_degree, kmax, n, q, idx.ctypes.data_as(_P(ctypes.c_int)),
+                                                _dptr(nodes), _dptr(w), _dptr(phi), ctypes.byref(N), ctypes.byref(Q)))
+    return idx, nodes, w, phi
+
+
 def ipm_dual_solve_noalloc(kind, gamma, p, total_degree, n_per_dim, entropy, n_cells, d_uhat, d_lam, d_nodal,
                            d_iters, d_status, stream=0, u_minus=0.0, u_plus=0.0, options=None):
     """Dual solve on caller-owned device buffers (integer device addresses); allocates nothing.
     Returns the ipm_stats of the call (the call waits for the solve)."""
     b = ipm_basis(p, total_degree)
-    q = ipm_quadrature(n_per_dim)
+    q = _quad(n_per_dim)
     e = ipm_entropy(ENTROPY[entropy], u_minus, u_plus)
     o = options if options is not None else default_options()
     s = ipm_stats()
@@ -265,7 +297,7 @@ class Context:
 
     def __init__(self, problem, p, total_degree, n_per_dim, entropy, u_minus=0.0, u_plus=0.0, options=None):
         b = ipm_basis(p, total_degree)
-        q = ipm_quadrature(n_per_dim)
+        q = _quad(n_per_dim)
         e = ipm_entropy(ENTROPY[entropy], u_minus, u_plus)
         o = options if options is not None else default_options()
         h = _vp()
@@ -386,7 +418,7 @@ def make_request(problem, p, total_degree, n_per_dim, entropy, u_minus=0.0, u_pl
     r = ipm_request()
     r.problem = problem
     r.basis = ipm_basis(p, total_degree)
-    r.quad = ipm_quadrature(n_per_dim)
+    r.quad = _quad(n_per_dim)
     r.entropy = ipm_entropy(ENTROPY[entropy], u_minus, u_plus)
     r.options = options if options is not None else default_options()
     r.max_steps = max_steps
@@ -453,7 +485,7 @@ class Collocation:
         self.h = None
         h = _vp()
         b = ipm_basis(p=p, total_degree=total_degree)
-        q = ipm_quadrature(n_per_dim=n_per_dim)
+        q = _quad(n_per_dim)
         st = lib().ipm_sc_init(ctypes.byref(problem), ctypes.byref(b), ctypes.byref(q), float(steady_tol),
                                ctypes.byref(h))
         if st != IPM_OK:

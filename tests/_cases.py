@@ -43,9 +43,13 @@ def oracle_problem(w, tau=None):
 
 
 def oracle_problem_2d(w, tau=None):
-    """oracle.scheme2d.Problem2D for a 2-D workload dictionary."""
+    """oracle.scheme2d.Problem2D for a 2-D workload dictionary (a nested Clenshaw-Curtis space of the
+    finest level when the workload names cc_levels)."""
     from oracle import scheme2d as s2
-    sp = basis.StochasticSpace(w["p"], w["M"], w["nq"])
+    if w.get("cc_levels"):
+        sp = basis.NestedCCSpace(w["p"], w["M"], max(w["cc_levels"]))
+    else:
+        sp = basis.StochasticSpace(w["p"], w["M"], w["nq"])
     phys = physics.Euler(w["gamma"], 2)
     ent = entropy.Euler(w["gamma"], 2) if w["entropy"] == "euler" else entropy.Quadratic(4)
     if w["mesh"] == "ramp":
@@ -82,10 +86,17 @@ def gpu_problem(w):
                             right=w["right"], dright=w.get("dright"))
 
 
+def gpu_quadrature(w):
+    """The workload's rule: tensor Gauss with nq nodes per dimension, or nested Clenshaw-Curtis rules
+    when the workload names cc_levels."""
+    from paper_1912_09238_gb300 import ipm
+    return ipm.quadrature(w["nq"], cc_levels=w.get("cc_levels"))
+
+
 def gpu_collocation(w, steady_tol=0.0):
     """Stochastic Collocation of a workload on the GPU (ipm_sc_*), on the workload's quadrature."""
     from paper_1912_09238_gb300 import ipm
-    return ipm.Collocation(gpu_problem(w), w["p"], w["M"], w["nq"], steady_tol)
+    return ipm.Collocation(gpu_problem(w), w["p"], w["M"], gpu_quadrature(w), steady_tol)
 
 
 def gpu_context(w, precision="fp64", tau=None, **opt):
@@ -97,12 +108,13 @@ def gpu_context(w, precision="fp64", tau=None, **opt):
                                  dparam=w.get("dparam"), x0=w.get("x0", 0.5), left=w.get("left", (0, 0, 0, 0)),
                                  dleft=w.get("dleft"), right=w.get("right", (0, 0, 0, 0)), dright=w.get("dright"))
         o = ipm.default_options(precision, newton_tol=tau if tau is not None else w.get("newton_tol", 1e-10), **opt)
-        return ipm.Context(pr, w["p"], w["M"], w["nq"], w["entropy"], 0.0, 0.0, o)
+        return ipm.Context(pr, w["p"], w["M"], gpu_quadrature(w), w["entropy"], 0.0, 0.0, o)
     pr = ipm.make_problem(w["kind"], w["nx"], w["x_lo"], w["x_hi"], bc=w["bc"], cfl=w["cfl"], t_end=w["t_end"],
                           gamma=w["gamma"], x0=w["x0"], dx0=w["dx0"], left=w["left"], dleft=w.get("dleft"),
                           right=w["right"], dright=w.get("dright"))
     o = ipm.default_options(precision, newton_tol=tau if tau is not None else w.get("newton_tol", 1e-10), **opt)
-    return ipm.Context(pr, w["p"], w["M"], w["nq"], w["entropy"], w.get("u_minus", 0.0), w.get("u_plus", 0.0), o)
+    return ipm.Context(pr, w["p"], w["M"], gpu_quadrature(w), w["entropy"], w.get("u_minus", 0.0), w.get("u_plus", 0.0),
+                       o)
 
 
 def rel_err(a, b):

@@ -65,3 +65,19 @@ def test_init_without_a_gpu_fails_cleanly(libipm):
     with pytest.raises(ipm.IpmError) as e:
         gpu_context(workloads.BURGERS_1D)
     assert e.value.status in (9, 1)
+
+
+@pytest.mark.parametrize("p,M,kmax", [(1, 4, 3), (2, 3, 2), (3, 2, 2)])
+def test_library_clenshaw_curtis_tables_match_oracle(libipm, p, M, kmax):
+    """The library's nested Clenshaw-Curtis tables (weights from a Chebyshev moment solve) against the
+    oracle's (closed-form weights): same node order, nodes, every level's weights, basis values."""
+    from oracle import basis as ob
+    from paper_1912_09238_gb300 import ipm
+    idx, nodes, lw, phi = ipm.ipm_tables_cc(p, M, kmax)
+    onodes, _, ow = ob.nested_cc_tensor(p, kmax)
+    assert np.abs(nodes - onodes).max() < 1e-15
+    for k in range(kmax + 1):
+        assert np.abs(lw[k, :ow[k].size] - ow[k]).max() < 1e-15
+        assert np.all(lw[k, ow[k].size:] == 0.0)
+    sp = ob.NestedCCSpace(p, M, kmax)
+    assert np.array_equal(idx, sp.indices) and np.abs(phi - sp.Phi).max() < 1e-13
