@@ -405,6 +405,21 @@ def workloads_bench(args):
         out["kh2d_adaptive"] = {"workload": f"2-D shear layer, 512 x 512 periodic, 3 uniform dims, adaptive total degree "
                                 f"2-6 (10-84 x 4 moments), 7^3 = 343 nodes, first {args.kh_steps} of the 200 steps",
                                 "unit": UNIT, **r}
+    # the same with a nested Clenshaw-Curtis rule per level (default levels 2, 2, 3, 3, 3: 125 or 729 nodes)
+    w = workloads.variant(workloads.KH_2D, M=6, nq=7, cc_levels=())
+    r = {}
+    for prec in ("mixed", "fp64") if only in (None, "kh") else ():
+        ctx = gpu_context(w, precision=prec, adapt_min_degree=2, delta_lo=2e-5, delta_hi=2e-4)
+        ctx.set_stream(stream.cuda_stream)
+        n, secs, s = _timed_steps(ctx, max(1, args.kh_steps // 2))
+        lev = ctx.get_levels().reshape(w["ny"] + 2, w["nx"] + 2)[1:-1, 1:-1]
+        r[prec] = {"value": cells * n / secs, "steps": n, "seconds": secs,
+                   "cells_per_degree": {str(2 + k): int(v) for k, v in enumerate(np.bincount(lev.ravel(), minlength=5))}}
+        ctx.close()
+    if r:
+        out["kh2d_adaptive_cc"] = {"workload": "2-D shear layer as kh2d_adaptive with a nested tensor Clenshaw-Curtis "
+                                   "rule per level (degrees 2-3: 5^3 = 125 nodes, 4-6: 9^3 = 729), first "
+                                   f"{max(1, args.kh_steps // 2)} steps", "unit": UNIT, **r}
     return out
 
 
