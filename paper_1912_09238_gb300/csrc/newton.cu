@@ -992,7 +992,8 @@ cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, in
 }
 
 // Longest-first order of the Newton work queue: the work items (interior cells, mapped as in the
-// Newton kernel) sorted by the Newton count of their previous solve, descending; ties in any order.
+// Newton kernel) sorted by the largest Newton count of the cell and its face neighbours in the previous
+// solve, descending; ties in any order.
 // The order decides only which CTA takes which cell when: each cell's arithmetic is independent of
 // it, so results do not depend on it. One CTA; warp-aggregated shared-memory atomics.
 constexpr int ORDER_KEYS = 128;
@@ -1009,7 +1010,14 @@ __global__ void __launch_bounds__(ORDER_T) k_order(const int* __restrict__ iters
       const int w = base + tid;
       const bool valid = w < n_work;
       const int cell = valid ? work_cell(w, nx, gy) : 0;
-      const int key = valid ? (ORDER_KEYS - 1) - min(max(iters[cell], 0), ORDER_KEYS - 1) : -1;
+      // predicted work: the most Newton updates the cell or a face neighbour needed in the last solve (a
+      // discontinuity moves less than a cell per step, so the cells it is about to enter start early too)
+      int pred = 0;
+      if (valid) {
+        pred = max(iters[cell], max(iters[cell - 1], iters[cell + 1]));
+        if (gy) pred = max(pred, max(iters[cell - (nx + 2)], iters[cell + (nx + 2)]));
+      }
+      const int key = valid ? (ORDER_KEYS - 1) - min(max(pred, 0), ORDER_KEYS - 1) : -1;
       const unsigned peers = __match_any_sync(0xffffffffu, key);
       const int leader = __ffs(peers) - 1;
       const int rank = __popc(peers & ((1u << lane) - 1u));
