@@ -271,8 +271,8 @@ def run_gpu(args):
         ctx.set_moments(hu)
         ctx.set_duals(hl)
         ctx.step(sync=False)
-        hu[...] = ctx.get_moments()
-        hl[...] = ctx.get_duals()
+        ctx.get_moments(out=hu)                 # straight into the pinned buffers
+        ctx.get_duals(out=hl)
     barrier()
     e2e_value, _ = aggregate_throughput(time.perf_counter() - t0, cells * e2e_steps, ws, "cuda")
     nbytes = int(np.prod(shape)) * 8

@@ -320,8 +320,13 @@ class Context:
         except Exception:
             pass
 
-    def _get(self, fn, shape):
-        out = np.empty(shape)
+    def _get(self, fn, shape, out=None):
+        """Copy device state into out (a C-contiguous float64 array of this shape, e.g. in pinned memory,
+        written in place) or into a new array."""
+        if out is None:
+            out = np.empty(shape)
+        elif out.dtype != np.float64 or not out.flags.c_contiguous or out.size != int(np.prod(shape)):
+            raise ValueError(f"{fn}: out must be a C-contiguous float64 array of {int(np.prod(shape))} elements")
         _check(fn, getattr(lib(), fn)(self.h, _dptr(out), out.size), self.h)
         return out
 
@@ -329,14 +334,14 @@ class Context:
         a = np.ascontiguousarray(arr, dtype=np.float64).reshape(self.shape)
         _check(fn, getattr(lib(), fn)(self.h, _dptr(a), a.size), self.h)
 
-    def get_moments(self):
-        return self._get("ipm_get_moments", self.shape)
+    def get_moments(self, out=None):
+        return self._get("ipm_get_moments", self.shape, out)
 
     def set_moments(self, a):
         self._set("ipm_set_moments", a)
 
-    def get_duals(self):
-        return self._get("ipm_get_duals", self.shape)
+    def get_duals(self, out=None):
+        return self._get("ipm_get_duals", self.shape, out)
 
     def set_duals(self, a):
         self._set("ipm_set_duals", a)
