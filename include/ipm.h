@@ -192,7 +192,9 @@ typedef struct {
   /* Newton kernel: 0 = autotune (time each applicable variant on the initial state at ipm_init and
    * keep the fastest; the decision is remembered for the process, per problem shape (kind, entropy,
    * N, m, Q, precision, power-of-two bucket of the interior cell count), so equal shapes always run
-   * the same variant), 1 = one CTA per cell, 2 = one warp per cell (cells with N*m <= 64, fixed degree) */
+   * the same variant), 1 = one CTA per cell, 2 = one warp per cell (cells with N*m <= 64, fixed degree).
+   * Adaptive meshes solve the cells of their lowest levels with N*m <= 64 one warp per cell (nodes in
+   * chunks of 32) and the others one CTA per cell; 1 keeps every cell on the CTA kernel. */
   int newton_kernel;
 } ipm_options;
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libipm.so")
 SOURCES = ["tables.cpp", "newton.cu", "update.cu", "abi.cu", "noalloc.cu", "server.cpp", "update2d.cu", "newton_warp.cu",
-           "collocation.cu"]
+           "collocation.cu", "newton_warpq.cu"]
 HEADERS = [os.path.join(ROOT, "include", "ipm.h")] + [
     os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))
 ]

@@ -70,6 +70,10 @@ struct ipm_ctx {
   int warp_warps = 0, warp_slice = 0, warp_grid = 0;
   float tune_ms[3] = {0.f, 0.f, 0.f};
   int newton_grid = 0;
+  // adaptive meshes: the cells of the lowest warp_levels levels (N m <= 64) are solved one warp per cell
+  // (newton_warpq.cu) before the CTA-per-cell kernel takes the others
+  int warp_levels = 0;
+  int wq_warps = 0, wq_slice = 0, wq_nm = 0, wq_grid = 0;
   size_t hwork_stride = 0;
   int update_grid = 0;
   // timing events recorded inside every step (begin, after Newton, after update, end)
@@ -167,6 +171,9 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.lev_w = c->level_rules ? c->d_lev_w : nullptr;
   a.level_next = c->n_levels ? c->d_level_next : nullptr;
   a.q_eval = c->level_rules ? c->d_q_eval : nullptr;
+  a.queue = nullptr;
+  a.first_dev = nullptr;
+  a.count_dev = nullptr;
   a.mx.phi_img = c->d_phi_img;
   a.mx.phiT32 = c->d_phiT32;
   a.mx.n_pad = c->mx.n_pad;
@@ -258,6 +265,23 @@ static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), s);
+  if (c->warp_levels > 0) {
+    // split queue: the small-level cells, one warp per cell, then the others, one CTA per cell
+    if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_sc->warp_counter, 0, sizeof(int), s);
+    if (e == cudaSuccess)
+      e = launch_order(c->d_iters, c->n_interior, c->prob.nx, 1, c->d_order, s, c->d_level, c->warp_levels, c->d_sc);
+    if (e != cudaSuccess) return e;
+    NewtonArgs a = newton_args(c, one_step);
+    a.cell_list = c->d_order;
+    a.queue = &c->d_sc->warp_counter;
+    a.first_dev = &c->d_sc->n_cta_items;
+    e = launch_newton_warpq(c->entk, c->phys, c->m, c->mixed, a, c->wq_grid, c->wq_warps, c->wq_slice, c->wq_nm, s);
+    if (e != cudaSuccess) return e;
+    a.queue = nullptr;
+    a.first_dev = nullptr;
+    a.count_dev = &c->d_sc->n_cta_items;
+    return launch_newton_ctx(c, a, c->n_interior, s);
+  }
   if (e == cudaSuccess) e = launch_order(c->d_iters, c->n_interior, c->prob.nx, c->is2d ? 1 : 0, c->d_order, s);
   if (e != cudaSuccess) return e;
   NewtonArgs a = newton_args(c, one_step);
@@ -590,6 +614,30 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
         c->warp_grid = bps * prop.multiProcessorCount;
         break;
       }
+    }
+  }
+  // adaptive meshes: the lowest levels with N m <= 64 go to the warp-per-cell kernel (Newton iterations
+  // and the mixed Hessian as in the warp kernel; frozen Hessians and the FP32 factorisation keep the
+  // CTA kernel, as does newton_kernel = 1)
+  if (c->n_levels > 0 && opt.hessian_reuse == 0 && c->newton_mode != 2 && opt.newton_kernel != 1) {
+    int L = 0;
+    while (L < c->n_levels && c->lev_n[L] * c->m <= 64) ++L;
+    if (L > 0) {
+      const int nm = c->lev_n[L - 1] * c->m;
+      const size_t slice = newton_warpq_slice(nm, c->m);
+      for (int wps = 8; wps >= 1; wps /= 2) {
+        if (wps * slice * sizeof(double) > budget) continue;
+        int bps = 0;
+        if (prepare_newton_warpq(c->entk, c->phys, c->m, c->mixed, wps, (int)slice, &bps) == cudaSuccess && bps >= 1) {
+          c->warp_levels = L;
+          c->wq_warps = wps;
+          c->wq_slice = (int)slice;
+          c->wq_nm = nm;
+          c->wq_grid = bps * prop.multiProcessorCount;
+          break;
+        }
+      }
+      cudaGetLastError();
     }
   }
   c->hwork_stride = c->h_in_smem ? 0 : packed_aug_count(c->NM);

@@ -232,6 +232,8 @@ struct StepScalars {
   unsigned long long fixed_smax_bits; // speed of the fixed (Dirichlet) ghosts
   int work_counter;              // persistent-queue counter of the Newton kernel
   int update_counter;
+  int n_cta_items;               // split queue: items for the CTA-per-cell kernel (the rest: one warp per cell)
+  int warp_counter;              // split queue: counter of the warp-per-cell kernel
   double t;                      // current time
   double dt;                     // last time step
   double residual;               // last steady residual
@@ -296,6 +298,12 @@ struct NewtonArgs {
                          // are taken at that level's nodes), or nullptr
   const int* q_eval;     // per-level rules: nodes at which each cell's nodal states are written (the
                          // largest new level's rule over its stencil); the rest of its row is zeroed
+  // split queue of adaptive meshes (k_order groups the cells by kernel): the items are
+  // cell_list[*first_dev .. *count_dev) taken through the counter *queue; nullptr: 0, n_work and
+  // sc->work_counter
+  int* queue;
+  const int* first_dev;
+  const int* count_dev;
   MixedTiles mx;         // mixed path only
   uint32_t off_h, off_a, off_b;  // shared-memory byte offsets: packed H, A staging, Phi chunks
 };

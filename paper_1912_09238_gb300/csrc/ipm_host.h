@@ -86,7 +86,15 @@ size_t newton_warp_slice(int N, int m, int Q);
 cudaError_t prepare_newton_warp(int ent, int phys, int m, bool mixed, int warps, int slice, int* blocks_per_sm);
 cudaError_t launch_newton_warp(int ent, int phys, int m, bool mixed, const NewtonArgs& a, int grid, int warps, int slice,
                                cudaStream_t s);
-cudaError_t launch_order(const int* iters, int n_work, int nx, int gy, int* order, cudaStream_t s);
+// level != nullptr: the cells of the levels below warp_levels are ordered after all others and
+// sc->n_cta_items counts the others
+cudaError_t launch_order(const int* iters, int n_work, int nx, int gy, int* order, cudaStream_t s,
+                         const int* level = nullptr, int warp_levels = 0, StepScalars* sc = nullptr);
+// one warp per cell with the nodes in chunks, for the small cells of adaptive meshes (newton_warpq.cu)
+size_t newton_warpq_slice(int nm, int m);
+cudaError_t prepare_newton_warpq(int ent, int phys, int m, bool mixed, int warps, int slice, int* blocks_per_sm);
+cudaError_t launch_newton_warpq(int ent, int phys, int m, bool mixed, const NewtonArgs& a, int grid, int warps,
+                                int slice, int nm_slice, cudaStream_t s);
 cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayout& L, float* phiT32, uint8_t* img,
                               cudaStream_t s);
 cudaError_t prepare_update1d(int phys, int m, int Q);

@@ -571,12 +571,14 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
     tcs.tmem = s_tmem;
   }
 
+  const int n_work = a.count_dev ? *a.count_dev : a.n_work;
+  int* queue = a.queue ? a.queue : &a.sc->work_counter;
   bool stop = false;
   while (!stop) {
-    if (tid == 0) s_work = atomicAdd(&a.sc->work_counter, 1);
+    if (tid == 0) s_work = atomicAdd(queue, 1);
     __syncthreads();
     const int wk = s_work;
-    if (wk >= a.n_work) break;
+    if (wk >= n_work) break;
     const int cell = a.cell_list ? a.cell_list[wk] : work_cell(wk, a.nx, a.gy);
     const int N = a.level ? a.lev_n[a.level[cell]] : NX;     // moments of this cell's level
     const int NM = N * M;
@@ -996,11 +998,12 @@ cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, in
 // solve, descending; ties in any order.
 // The order decides only which CTA takes which cell when: each cell's arithmetic is independent of
 // it, so results do not depend on it. One CTA; warp-aggregated shared-memory atomics.
-constexpr int ORDER_KEYS = 128;
+constexpr int ORDER_KEYS = 256;   // two groups of 128 predicted counts
 constexpr int ORDER_T = 1024;
 
 __global__ void __launch_bounds__(ORDER_T) k_order(const int* __restrict__ iters, int n_work, int nx, int gy,
-                                                   int* __restrict__ order) {
+                                                   int* __restrict__ order, const int* __restrict__ level,
+                                                   int warp_levels, StepScalars* sc) {
   __shared__ int cnt[ORDER_KEYS];
   const int tid = threadIdx.x, lane = tid & 31;
   for (int k = tid; k < ORDER_KEYS; k += ORDER_T) cnt[k] = 0;
@@ -1017,7 +1020,9 @@ __global__ void __launch_bounds__(ORDER_T) k_order(const int* __restrict__ iters
         pred = max(iters[cell], max(iters[cell - 1], iters[cell + 1]));
         if (gy) pred = max(pred, max(iters[cell - (nx + 2)], iters[cell + (nx + 2)]));
       }
-      const int key = valid ? (ORDER_KEYS - 1) - min(max(pred, 0), ORDER_KEYS - 1) : -1;
+      // split queue (adaptive meshes): the cells of the levels below warp_levels form the second group
+      const int group = (valid && level && level[cell] < warp_levels) ? 1 : 0;
+      const int key = valid ? group * 128 + 127 - min(max(pred, 0), 127) : -1;
       const unsigned peers = __match_any_sync(0xffffffffu, key);
       const int leader = __ffs(peers) - 1;
       const int rank = __popc(peers & ((1u << lane) - 1u));
@@ -1035,13 +1040,15 @@ __global__ void __launch_bounds__(ORDER_T) k_order(const int* __restrict__ iters
         cnt[k] = run;
         run += c;
       }
+      if (sc) sc->n_cta_items = cnt[128];   // the first group ends where the second begins
     }
     __syncthreads();
   }
 }
 
-cudaError_t launch_order(const int* iters, int n_work, int nx, int gy, int* order, cudaStream_t s) {
-  k_order<<<1, ORDER_T, 0, s>>>(iters, n_work, nx, gy, order);
+cudaError_t launch_order(const int* iters, int n_work, int nx, int gy, int* order, cudaStream_t s, const int* level,
+                         int warp_levels, StepScalars* sc) {
+  k_order<<<1, ORDER_T, 0, s>>>(iters, n_work, nx, gy, order, level, warp_levels, sc);
   return cudaGetLastError();
 }
 

@@ -137,3 +137,19 @@ def test_clenshaw_curtis_rule_checks():
     ctx.step()
     ref.step()
     assert np.array_equal(ctx.get_moments(), ref.get_moments())
+
+
+@pytest.mark.parametrize("w", [KH, KH_CC], ids=["gauss", "clenshaw_curtis"])
+def test_small_cells_on_the_warp_kernel_equal_the_cta_kernel(w):
+    """The lowest levels (N m <= 64) run one warp per cell beside the CTA-per-cell kernel; forcing every
+    cell onto the CTA kernel (newton_kernel = 1) gives the same levels and moments to rounding."""
+    kw = dict(adapt_min_degree=2, delta_lo=2e-4, delta_hi=2e-5) if w is KH else dict(adapt_min_degree=1, delta_lo=2e-5,
+                                                                                      delta_hi=2e-4)
+    split = gpu_context(w, **kw)
+    cta = gpu_context(w, newton_kernel=1, **kw)
+    for _ in range(3):
+        a, b = split.step(), cta.step()
+        assert a.failed_cells == 0 and b.failed_cells == 0
+        assert a.newton_iters == b.newton_iters
+        assert np.array_equal(split.get_levels(), cta.get_levels())
+        assert rel_err(split.get_moments(), cta.get_moments()) < 1e-12
