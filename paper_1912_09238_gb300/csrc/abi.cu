@@ -595,7 +595,7 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     // the CTAs of one SM must also share its 512 tensor-memory columns
     int bps = 0;
     e = prepare_newton(c->entk, c->phys, c->m, c->newton_smem, c->h_in_smem, c->newton_mode, &bps);
-    if (e == cudaSuccess) e = c->is2d ? prepare_update2d(c->Q) : prepare_update1d(c->phys, c->m, c->Q);
+    if (e == cudaSuccess) e = c->is2d ? prepare_update2d(c->N, c->Q) : prepare_update1d(c->phys, c->m, c->N, c->Q);
     if (e != cudaSuccess || bps < 1) {
         return fail(nullptr, IPM_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
     }

@@ -97,13 +97,13 @@ cudaError_t launch_newton_warpq(int ent, int phys, int m, bool mixed, const Newt
                                 int slice, int nm_slice, cudaStream_t s);
 cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayout& L, float* phiT32, uint8_t* img,
                               cudaStream_t s);
-cudaError_t prepare_update1d(int phys, int m, int Q);
+cudaError_t prepare_update1d(int phys, int m, int N, int Q);
 cudaError_t launch_update1d(int phys, int m, const Update1DArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_init1d(int ent, int m, const Tables& tab, const EntParams& ent_p, const ipm_problem& prob,
                           double* uhat, double* lam, int n_cells, cudaStream_t s);
 cudaError_t launch_finalize(StepScalars* sc, const int* iters, const int* status, const double* cell_resid,
                             int n_cells, int first, int count, int advance_time, cudaStream_t s);
-cudaError_t prepare_update2d(int Q);
+cudaError_t prepare_update2d(int N, int Q);
 cudaError_t launch_update2d(const Update2DArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_init_levels(const Update2DArgs& a, int n_cells, cudaStream_t s);
 cudaError_t launch_cap_levels(const Update2DArgs& a, int cap, cudaStream_t s);

@@ -27,7 +27,7 @@ __device__ __forceinline__ double step_dt(const Update1DArgs& a) {
 
 template <int PHYS, int M>
 __global__ void __launch_bounds__(UT) k_update1d(Update1DArgs a) {
-  extern __shared__ __align__(16) double s_v[];     // [M][Q] integrand
+  extern __shared__ __align__(16) double s_v[];     // [M][Q] integrand, then [UWARPS][N M] partial sums
   const int N = a.tab.N, Q = a.tab.Q, NM = N * M;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double dt = step_dt(a);
@@ -36,8 +36,12 @@ __global__ void __launch_bounds__(UT) k_update1d(Update1DArgs a) {
   const double nu = a.dx / (2.0 * dt);
   const double r = dt / a.dx;
   const double* __restrict__ w = a.tab.w;
-  const double* __restrict__ PhiT = a.tab.PhiT;
+  const double* __restrict__ Phi = a.tab.Phi;
   const int MQ = M * Q;
+  double* s_part = s_v + MQ;
+  // projection split: warp k sums the nodes [k qw, (k+1) qw) for every entry, lanes over entries
+  const int qw = (Q + UWARPS - 1) / UWARPS;
+  const int q_lo = min(Q, warp * qw), q_hi = min(Q, q_lo + qw);
 
   for (int j = blockIdx.x + 1; j <= a.nx; j += gridDim.x) {
     const int jl = neighbour(j, a.nx, -1, a.bc_left);
@@ -73,24 +77,21 @@ __global__ void __launch_bounds__(UT) k_update1d(Update1DArgs a) {
     const int g1 = (j == a.nx && a.bc_right == IPM_BC_OUTFLOW) || (j == 1 && a.bc_right == IPM_BC_PERIODIC);
     double* out0 = a.uhat;                                 // ghost 0
     double* out1 = a.uhat + (size_t)(a.nx + 1) * NM;       // ghost nx+1
-    for (int i = warp; i < N; i += UWARPS) {
-      double acc[M];
+    // projection u_hat_(i,c) = sum_q phi_i(xi_q) v_c(xi_q): partial sums per warp, added in warp order
+    for (int rr = lane; rr < NM; rr += 32) {
+      const int i = rr / M, c = rr - i * M;
+      double acc = 0.0;
+      for (int q = q_lo; q < q_hi; ++q) acc = fma(Phi[(size_t)q * N + i], s_v[c * Q + q], acc);
+      s_part[warp * NM + rr] = acc;
+    }
+    __syncthreads();
+    for (int rr = tid; rr < NM; rr += UT) {
+      double v = 0.0;
 #pragma unroll
-      for (int c = 0; c < M; ++c) acc[c] = 0.0;
-      for (int q = lane; q < Q; q += 32) {
-        const double ph = PhiT[(size_t)i * Q + q];
-#pragma unroll
-        for (int c = 0; c < M; ++c) acc[c] = fma(ph, s_v[c * Q + q], acc[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < M; ++c) {
-        const double v = warp_sum(acc[c]);
-        if (lane == 0) {
-          out[i * M + c] = v;
-          if (g0) out0[i * M + c] = v;
-          if (g1) out1[i * M + c] = v;
-        }
-      }
+      for (int k = 0; k < UWARPS; ++k) v += s_part[k * NM + rr];
+      out[rr] = v;
+      if (g0) out0[rr] = v;
+      if (g1) out1[rr] = v;
     }
     if (g0 || g1) {
       const double* lj = a.lam + (size_t)j * NM;
@@ -106,15 +107,17 @@ __global__ void __launch_bounds__(UT) k_update1d(Update1DArgs a) {
   }
 }
 
-cudaError_t prepare_update1d(int phys, int m, int Q) {
-  const int smem = (int)((size_t)m * Q * sizeof(double));
+static size_t update1d_smem(int m, int N, int Q) { return ((size_t)m * Q + (size_t)UWARPS * N * m) * sizeof(double); }
+
+cudaError_t prepare_update1d(int phys, int m, int N, int Q) {
+  const size_t smem = update1d_smem(m, N, Q);
   if (phys == PHYS_BURGERS && m == 1) return raise_smem_limit(k_update1d<PHYS_BURGERS, 1>, smem);
   if (phys == PHYS_EULER1D && m == 3) return raise_smem_limit(k_update1d<PHYS_EULER1D, 3>, smem);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_update1d(int phys, int m, const Update1DArgs& a, int grid, cudaStream_t s) {
-  const size_t smem = (size_t)m * a.tab.Q * sizeof(double);
+  const size_t smem = update1d_smem(m, a.tab.N, a.tab.Q);
   if (phys == PHYS_BURGERS && m == 1) {
     k_update1d<PHYS_BURGERS, 1><<<grid, UT, smem, s>>>(a);
   } else if (phys == PHYS_EULER1D && m == 3) {

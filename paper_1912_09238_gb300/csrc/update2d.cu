@@ -22,7 +22,7 @@ constexpr int T2 = 256;
 constexpr int W2 = T2 / 32;
 
 __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
-  extern __shared__ __align__(16) double s_v[];     // [4][Q] w * integrand
+  extern __shared__ __align__(16) double s_v[];     // [4][Q] w * integrand, then [W2][N 4] partial sums
   constexpr int M = 4;
   const int N = a.tab.N, Q = a.tab.Q, NM = N * M;
   const int nx = a.mesh.nx, ny = a.mesh.ny;
@@ -36,9 +36,10 @@ __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
   if (blockIdx.x == 0 && tid == 0) a.sc->dt = dt > 0.0 ? dt : 0.0;
   if (!(dt > 0.0)) return;
   const double* __restrict__ w = a.tab.w;
-  const double* __restrict__ PhiT = a.tab.PhiT;
+  const double* __restrict__ Phi = a.tab.Phi;
   const int MQ = M * Q;
   const double g = a.gamma;
+  double* s_part = s_v + MQ;
 
   for (int cidx = blockIdx.x; cidx < nx * ny; cidx += gridDim.x) {
     const int i = cidx % nx, j = cidx / nx;
@@ -104,27 +105,28 @@ __global__ void __launch_bounds__(T2) k_update2d(Update2DArgs a) {
     __syncthreads();
     double* out = a.uhat + (size_t)c * NM;
     const double old00 = out[0];
-    for (int ii = warp; ii < N; ii += W2) {
-      if (ii >= n_new) {                                   // beyond the new level: moments and duals are zero
-        if (lane < M) {
-          out[ii * M + lane] = 0.0;
-          a.lam[(size_t)c * NM + ii * M + lane] = 0.0;
-        }
+    // projection onto the new level: warp k sums the nodes [k qw, (k+1) qw) for every entry (lanes over
+    // entries), then the warps' partial sums are added in warp order
+    const int NMn = n_new * M;
+    const int qw = (Qn + W2 - 1) / W2;
+    const int q_lo = min(Qn, warp * qw), q_hi = min(Qn, q_lo + qw);
+    for (int rr = lane; rr < NMn; rr += 32) {
+      const int ii = rr / M, k = rr - ii * M;
+      double acc = 0.0;
+      for (int q = q_lo; q < q_hi; ++q) acc = fma(Phi[(size_t)q * N + ii], s_v[k * Q + q], acc);
+      s_part[warp * NM + rr] = acc;
+    }
+    __syncthreads();
+    for (int rr = tid; rr < NM; rr += T2) {
+      if (rr >= NMn) {                                     // beyond the new level: moments and duals are zero
+        out[rr] = 0.0;
+        a.lam[(size_t)c * NM + rr] = 0.0;
         continue;
       }
-      double s[M];
+      double v = 0.0;
 #pragma unroll
-      for (int k = 0; k < M; ++k) s[k] = 0.0;
-      for (int q = lane; q < Qn; q += 32) {
-        const double ph = PhiT[(size_t)ii * Q + q];
-#pragma unroll
-        for (int k = 0; k < M; ++k) s[k] = fma(ph, s_v[k * Q + q], s[k]);
-      }
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        const double v = warp_sum(s[k]);
-        if (lane == 0) out[ii * M + k] = v;
-      }
+      for (int k = 0; k < W2; ++k) v += s_part[k * NM + rr];
+      out[rr] = v;
     }
     __syncthreads();
     if (tid == 0 && a.cell_resid) a.cell_resid[c] = area * fabs(out[0] - old00);
@@ -356,9 +358,11 @@ __global__ void __launch_bounds__(256) k_update2d_warp(Update2DArgs a) {
 // the warp variant when a warp's slice of node values is small; else one CTA per cell
 static bool update2d_use_warp(int Q) { return Q <= 64; }
 
-cudaError_t prepare_update2d(int Q) {
+static size_t update2d_smem(int N, int Q) { return ((size_t)4 * Q + (size_t)W2 * N * 4) * sizeof(double); }
+
+cudaError_t prepare_update2d(int N, int Q) {
   if (update2d_use_warp(Q)) return raise_smem_limit(k_update2d_warp, (size_t)UPD_WARPS * 4 * Q * sizeof(double));
-  return raise_smem_limit(k_update2d, (size_t)4 * Q * sizeof(double));
+  return raise_smem_limit(k_update2d, update2d_smem(N, Q));
 }
 
 cudaError_t launch_update2d(const Update2DArgs& a, int grid, cudaStream_t s) {
@@ -367,7 +371,7 @@ cudaError_t launch_update2d(const Update2DArgs& a, int grid, cudaStream_t s) {
     const int g = std::max(1, std::min((cells + UPD_WARPS - 1) / UPD_WARPS, 65535));
     k_update2d_warp<<<g, 32 * UPD_WARPS, (size_t)UPD_WARPS * 4 * a.tab.Q * sizeof(double), s>>>(a);
   } else {
-    k_update2d<<<grid, T2, (size_t)4 * a.tab.Q * sizeof(double), s>>>(a);
+    k_update2d<<<grid, T2, update2d_smem(a.tab.N, a.tab.Q), s>>>(a);
   }
   return cudaGetLastError();
 }
