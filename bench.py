@@ -393,7 +393,7 @@ def workloads_bench(args):
     w = workloads.variant(workloads.KH_2D, M=6, nq=7)
     cells = w["nx"] * w["ny"]
     r = {}
-    for prec in ("mixed", "fp64") if only in (None, "kh") else ():
+    for prec in ("mixed", "fp64", "mixed_f32f") if only in (None, "kh") else ():
         ctx = gpu_context(w, precision=prec, adapt_min_degree=2, delta_lo=2e-5, delta_hi=2e-4)
         ctx.set_stream(stream.cuda_stream)
         n, secs, s = _timed_steps(ctx, args.kh_steps)
@@ -403,7 +403,8 @@ def workloads_bench(args):
         ctx.close()
     if r:
         out["kh2d_adaptive"] = {"workload": f"2-D shear layer, 512 x 512 periodic, 3 uniform dims, adaptive total degree "
-                                f"2-6 (10-84 x 4 moments), 7^3 = 343 nodes, first {args.kh_steps} of the 200 steps",
+                                f"2-6 (10-84 x 4 moments), 7^3 = 343 nodes, first {args.kh_steps} of the 200 steps "
+                                "(mixed_f32f: the FP32-factorisation mode, not the north star's precision plan)",
                                 "unit": UNIT, **r}
     # the same with a nested Clenshaw-Curtis rule per level (default levels 2, 2, 3, 3, 3: 125 or 729 nodes)
     w = workloads.variant(workloads.KH_2D, M=6, nq=7, cc_levels=())

@@ -617,9 +617,9 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     }
   }
   // adaptive meshes: the lowest levels with N m <= 64 go to the warp-per-cell kernel (Newton iterations
-  // and the mixed Hessian as in the warp kernel; frozen Hessians and the FP32 factorisation keep the
-  // CTA kernel, as does newton_kernel = 1)
-  if (c->n_levels > 0 && opt.hessian_reuse == 0 && c->newton_mode != 2 && opt.newton_kernel != 1) {
+  // and the mixed Hessian as in the warp kernel, an FP64 factorisation of these small systems in every
+  // precision mode); frozen Hessians keep the CTA kernel, as does newton_kernel = 1
+  if (c->n_levels > 0 && opt.hessian_reuse == 0 && opt.newton_kernel != 1) {
     int L = 0;
     while (L < c->n_levels && c->lev_n[L] * c->m <= 64) ++L;
     if (L > 0) {

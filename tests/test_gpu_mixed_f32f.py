@@ -122,3 +122,23 @@ def test_sod_full_size_first_step_sampled():
 def test_rejects_frozen_hessians():
     with pytest.raises(ipm.IpmError):
         gpu_context(SOD_SMALL, precision=PREC, hessian_reuse=1)
+
+
+def test_adaptive_shear_layer_matches_the_oracle():
+    """Adaptive degrees 2-4 on the shear layer: the degree-2 cells on the warp kernel (FP64
+    factorisation of their small systems), the others with the FP32 factorisation."""
+    from oracle import adaptive as ad
+    w = workloads.variant(workloads.KH_2D, nx=12, ny=12, M=4, nq=5)
+    lv = ad.Levels(degrees=(2, 3, 4), delta_lo=2e-4, delta_hi=2e-5)
+    prob = oracle_problem_2d(w)
+    st = ad.initial_state(prob, lv)
+    ctx = gpu_context(w, precision=PREC, adapt_min_degree=2, delta_lo=2e-4, delta_hi=2e-5)
+    for n in range(4):
+        st = ad.ipm_step(prob, st, lv)
+        s = ctx.step()
+        assert s.failed_cells == 0 and s.tc_timeouts == 0
+        lev = ctx.get_levels().reshape(st.level.shape)
+        assert np.array_equal(lev[1:-1, 1:-1], st.level[1:-1, 1:-1]), n
+        got = ctx.get_moments().reshape(st.uhat.shape)
+        assert rel_err(got[1:-1, 1:-1], st.uhat[1:-1, 1:-1]) < TOL_MIXED, n
+    ctx.close()
