@@ -660,10 +660,17 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       for (int r = tid; r < NM; r += NT) {
         const int i = r / M, c = r - i * M;
         const double* wu = s_wu + c * Q;
-        double acc = 0.0;
-#pragma unroll 8
-        for (int q = 0; q < Qc; ++q) acc = fma(Phi[(size_t)q * NX + i], wu[q], acc);
-        s_g[r] = acc - s_uh[r];
+        // four independent partial sums: the node sum is a dependent chain otherwise
+        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+        int q = 0;
+        for (; q + 4 <= Qc; q += 4) {
+          acc0 = fma(Phi[(size_t)q * NX + i], wu[q], acc0);
+          acc1 = fma(Phi[(size_t)(q + 1) * NX + i], wu[q + 1], acc1);
+          acc2 = fma(Phi[(size_t)(q + 2) * NX + i], wu[q + 2], acc2);
+          acc3 = fma(Phi[(size_t)(q + 3) * NX + i], wu[q + 3], acc3);
+        }
+        for (; q < Qc; ++q) acc0 = fma(Phi[(size_t)q * NX + i], wu[q], acc0);
+        s_g[r] = ((acc0 + acc1) + (acc2 + acc3)) - s_uh[r];
       }
       __syncthreads();
       double gres[1] = {0.0};
