@@ -268,17 +268,15 @@ def run_gpu(args):
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ctx.set_moments(hu)
-        ctx.set_duals(hl)
+        ctx.set_state(hu, hl)
         ctx.step(sync=False)
-        ctx.get_moments(out=hu)                 # straight into the pinned buffers
-        ctx.get_duals(out=hl)
+        ctx.get_state(hu, hl)                   # straight into the pinned buffers
     barrier()
     e2e_value, _ = aggregate_throughput(time.perf_counter() - t0, cells * e2e_steps, ws, "cuda")
     nbytes = int(np.prod(shape)) * 8
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
-           "d2h_bytes_per_step": 2 * nbytes, "api": "ipm_set_moments + ipm_set_duals + ipm_step + "
-           "ipm_get_moments + ipm_get_duals (host buffers, pinned)"}
+           "d2h_bytes_per_step": 2 * nbytes, "api": "ipm_set_state + ipm_step + ipm_get_state (moments and "
+           "duals, pinned host buffers)"}
 
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"],

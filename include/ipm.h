@@ -258,6 +258,26 @@ ipm_status ipm_set_moments(ipm_ctx* ctx, const double* host, size_t count);
 ipm_status ipm_get_moments(ipm_ctx* ctx, double* host, size_t count);
 ipm_status ipm_set_duals(ipm_ctx* ctx, const double* host, size_t count);
 ipm_status ipm_get_duals(ipm_ctx* ctx, double* host, size_t count);
+/* Clock of a context: simulated (or pseudo-) time, last time step, steps taken, and the level cap of
+ * Algorithm 4 (adaptive contexts; levels - 1 without retardation). */
+typedef struct {
+  double t;
+  double dt;
+  int64_t steps;
+  int32_t level_cap;
+} ipm_clock;
+
+/* Checkpoint / resume: the whole state of a context in one call with one synchronisation -- moments
+ * and duals ([cell][moment][variable] each, count = n_cells*N*m doubles per array), the refinement
+ * level of every cell (adaptive contexts: n_cells ints; NULL to skip, and ignored on fixed-degree
+ * contexts) and the clock (NULL to skip). A context restored from a checkpoint of a context of the
+ * same problem continues bit for bit as the original would (kept Cholesky factors of hessian_reuse 2
+ * are not part of the state: a restored context refactorises, so its iterates differ within the
+ * stopping tolerance). Also the way to stream a step's state in and out. */
+ipm_status ipm_set_state(ipm_ctx* ctx, const double* moments, const double* duals, const int* levels,
+                         const ipm_clock* clock, size_t count);
+ipm_status ipm_get_state(ipm_ctx* ctx, double* moments, double* duals, int* levels, ipm_clock* clock,
+                         size_t count);
 /* Nodal states u_s(lambda_j^T phi(xi_k)) at the current duals, laid out [cell][variable][node]
  * (count = n_cells*m*Q). Valid after ipm_dual_solve / ipm_step / ipm_oneshot_step. */
 ipm_status ipm_get_nodal_states(ipm_ctx* ctx, double* host, size_t count);

@@ -939,6 +939,56 @@ ipm_status ipm_get_duals(ipm_ctx* c, double* h, size_t n) {
   if (!c) return IPM_EINVAL;
   return copy_state(c, h, c->d_lam, n, (size_t)c->n_cells * c->NM, cudaMemcpyDeviceToHost, true);
 }
+ipm_status ipm_set_state(ipm_ctx* c, const double* mom, const double* duals, const int* levels,
+                         const ipm_clock* clock, size_t n) {
+  if (!c) return IPM_EINVAL;
+  const size_t expect = (size_t)c->n_cells * c->NM;
+  ipm_status st = copy_state(c, c->d_uhat, mom, n, expect, cudaMemcpyHostToDevice, false);
+  if (st == IPM_OK) st = copy_state(c, c->d_lam, duals, n, expect, cudaMemcpyHostToDevice, false);
+  if (st != IPM_OK) return st;
+  if (levels && c->n_levels) {
+    for (int k = 0; k < c->n_cells; ++k)
+      if (levels[k] < 0 || levels[k] >= c->n_levels) return fail(c, IPM_EINVAL, "ipm_set_state: level out of range");
+    IPM_CK(c, cudaMemcpyAsync(c->d_level, levels, (size_t)c->n_cells * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    IPM_CK(c, cudaMemcpyAsync(c->d_level_next, c->d_level, (size_t)c->n_cells * sizeof(int), cudaMemcpyDeviceToDevice,
+                              c->stream));
+  }
+  if (clock) {
+    if (c->n_levels && (clock->level_cap < 0 || clock->level_cap >= c->n_levels))
+      return fail(c, IPM_EINVAL, "ipm_set_state: level cap out of range");
+    StepScalars h;
+    IPM_CK(c, cudaMemcpyAsync(&h, c->d_sc, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->stream));
+    IPM_CK(c, cudaStreamSynchronize(c->stream));
+    h.t = clock->t;
+    h.dt = clock->dt;
+    h.steps = clock->steps;
+    h.level_cap = c->n_levels ? clock->level_cap : 0;
+    IPM_CK(c, cudaMemcpyAsync(c->d_sc, &h, sizeof(StepScalars), cudaMemcpyHostToDevice, c->stream));
+  }
+  IPM_CK(c, cudaStreamSynchronize(c->stream));
+  return IPM_OK;
+}
+
+ipm_status ipm_get_state(ipm_ctx* c, double* mom, double* duals, int* levels, ipm_clock* clock, size_t n) {
+  if (!c) return IPM_EINVAL;
+  const size_t expect = (size_t)c->n_cells * c->NM;
+  ipm_status st = copy_state(c, mom, c->d_uhat, n, expect, cudaMemcpyDeviceToHost, false);
+  if (st == IPM_OK) st = copy_state(c, duals, c->d_lam, n, expect, cudaMemcpyDeviceToHost, false);
+  if (st != IPM_OK) return st;
+  if (levels && c->n_levels)
+    IPM_CK(c, cudaMemcpyAsync(levels, c->d_level, (size_t)c->n_cells * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  StepScalars h;
+  if (clock) IPM_CK(c, cudaMemcpyAsync(&h, c->d_sc, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->stream));
+  IPM_CK(c, cudaStreamSynchronize(c->stream));
+  if (clock) {
+    clock->t = h.t;
+    clock->dt = h.dt;
+    clock->steps = h.steps;
+    clock->level_cap = h.level_cap;
+  }
+  return IPM_OK;
+}
+
 ipm_status ipm_get_nodal_states(ipm_ctx* c, double* h, size_t n) {
   if (!c) return IPM_EINVAL;
   return copy_state(c, h, c->d_unode, n, (size_t)c->n_cells * c->m * c->Q, cudaMemcpyDeviceToHost, true);

@@ -96,6 +96,10 @@ class ipm_result(ctypes.Structure):
                 ("error", ctypes.c_char * 192)]
 
 
+class ipm_clock(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double), ("steps", ctypes.c_int64), ("level_cap", ctypes.c_int32)]
+
+
 class ipm_sc_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("max_node_steps", ctypes.c_int64), ("active_nodes", ctypes.c_int32),
                 ("t_min", ctypes.c_double), ("t_max", ctypes.c_double), ("residual_max", ctypes.c_double),
@@ -130,6 +134,8 @@ SIGNATURES = [
     ("ipm_set_duals", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
     ("ipm_get_duals", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
     ("ipm_get_nodal_states", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
+    ("ipm_set_state", ctypes.c_int, [_vp, _dp, _dp, _P(ctypes.c_int), _vp, ctypes.c_size_t]),
+    ("ipm_get_state", ctypes.c_int, [_vp, _dp, _dp, _P(ctypes.c_int), _vp, ctypes.c_size_t]),
     ("ipm_get_levels", ctypes.c_int, [_vp, _P(ctypes.c_int), ctypes.c_size_t]),
     ("ipm_get_tuning", ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_float), _P(ctypes.c_float)]),
     ("ipm_set_max_level", ctypes.c_int, [_vp, ctypes.c_int]),
@@ -345,6 +351,37 @@ class Context:
 
     def set_duals(self, a):
         self._set("ipm_set_duals", a)
+
+    def set_state(self, moments, duals, levels=None, clock=None):
+        """Restore moments and duals (C-contiguous float64 arrays of the state's shape are used in place,
+        e.g. pinned buffers), and optionally the levels (adaptive contexts) and the clock (ipm_clock)."""
+        m = np.ascontiguousarray(moments, dtype=np.float64).reshape(self.shape)
+        d = np.ascontiguousarray(duals, dtype=np.float64).reshape(self.shape)
+        lv = None if levels is None else np.ascontiguousarray(levels, dtype=np.int32)
+        _check("ipm_set_state", lib().ipm_set_state(
+            self.h, _dptr(m), _dptr(d), None if lv is None else lv.ctypes.data_as(_P(ctypes.c_int)),
+            None if clock is None else ctypes.byref(clock), m.size), self.h)
+
+    def get_state(self, moments=None, duals=None, levels=False, clock=False):
+        """(moments, duals[, levels][, clock]); given arrays (C-contiguous float64 of the state's shape)
+        are filled in place. levels=True / clock=True also return the level of every cell (adaptive
+        contexts) and the ipm_clock."""
+        m = np.empty(self.shape) if moments is None else moments
+        d = np.empty(self.shape) if duals is None else duals
+        for a in (m, d):
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != int(np.prod(self.shape)):
+                raise ValueError("get_state: arrays must be C-contiguous float64 of the state's shape")
+        lv = np.zeros(self.dims.n_cells, dtype=np.int32) if levels else None
+        ck = ipm_clock() if clock else None
+        _check("ipm_get_state", lib().ipm_get_state(
+            self.h, _dptr(m), _dptr(d), None if lv is None else lv.ctypes.data_as(_P(ctypes.c_int)),
+            None if ck is None else ctypes.byref(ck), m.size), self.h)
+        out = (m, d)
+        if levels:
+            out += (lv,)
+        if clock:
+            out += (ck,)
+        return out
 
     def get_nodal_states(self):
         d = self.dims
