@@ -105,12 +105,16 @@ static ipm_status fail(ipm_ctx* c, ipm_status s, const std::string& msg) {
   return s;
 }
 
+// A failed call returns its status; a non-sticky error (e.g. an allocation that did not fit) is also
+// cleared from the runtime's last-error slot, so that later launches of any context do not report it.
 #define IPM_CK(ctx, call)                                                                               \
   do {                                                                                                  \
     cudaError_t e_ = (call);                                                                            \
-    if (e_ != cudaSuccess)                                                                              \
+    if (e_ != cudaSuccess) {                                                                            \
+      cudaGetLastError();                                                                               \
       return fail(ctx, e_ == cudaErrorMemoryAllocation ? IPM_ENOMEM : IPM_ECUDA,                        \
                   std::string(#call) + ": " + cudaGetErrorString(e_));                                 \
+    }                                                                                                   \
   } while (0)
 
 static Tables dev_tables(const ipm_ctx* c) {
@@ -731,6 +735,7 @@ ipm_status ipm_footprint(const ipm_problem* problem, const ipm_basis* basis, con
 
 ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ipm_quadrature* quad,
                     const ipm_entropy* entropy, const ipm_options* options, ipm_ctx** out) {
+  NvtxRange nvtx_("ipm_init");
   if (!problem || !basis || !quad || !entropy || !out) return fail(nullptr, IPM_EINVAL, "ipm_init: NULL argument");
   *out = nullptr;
   ipm_options opt;
@@ -749,6 +754,7 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
 
   ipm_status st = IPM_OK;
   auto CK = [&](cudaError_t err, const char* what) {
+    if (err != cudaSuccess) cudaGetLastError();          // clear a non-sticky error for later launches
     if (err != cudaSuccess && st == IPM_OK) {
       st = fail(nullptr, err == cudaErrorMemoryAllocation ? IPM_ENOMEM : IPM_ECUDA,
                 std::string(what) + ": " + cudaGetErrorString(err));
@@ -1005,6 +1011,7 @@ ipm_status ipm_set_max_level(ipm_ctx* c, int max_level) {
 
 ipm_status ipm_oneshot_retarded(ipm_ctx* c, const int* max_levels, const double* tolerances, int n_stages, double tol,
                                 int64_t max_steps, ipm_stats* s) {
+  NvtxRange nvtx_("ipm_oneshot_retarded");
   if (!c || !max_levels || n_stages < 1 || (n_stages > 1 && !tolerances)) return IPM_EINVAL;
   int stage = 0;
   ipm_status st = ipm_set_max_level(c, max_levels[0]);
@@ -1078,6 +1085,7 @@ ipm_status ipm_sync_stats(ipm_ctx* c, ipm_stats* s) {
 }
 
 ipm_status ipm_dual_solve(ipm_ctx* c, ipm_stats* s) {
+  NvtxRange nvtx_("ipm_dual_solve");
   if (!c) return IPM_EINVAL;
   IPM_CK(c, enqueue_newton(c, 0, c->stream));
   IPM_CK(c, launch_finalize(c->d_sc, c->d_iters, c->d_status, nullptr, c->n_cells, c->is2d ? 0 : 1,
@@ -1087,6 +1095,7 @@ ipm_status ipm_dual_solve(ipm_ctx* c, ipm_stats* s) {
 }
 
 ipm_status ipm_assemble_hessian(ipm_ctx* c, double* h, size_t count) {
+  NvtxRange nvtx_("ipm_assemble_hessian");
   if (!c || (!h && count)) return IPM_EINVAL;
   const size_t nph = (size_t)c->NM * (c->NM + 1) / 2;
   if (count != (size_t)c->n_interior * nph) return fail(c, IPM_EINVAL, "ipm_assemble_hessian: count must be n_interior*NM(NM+1)/2");
@@ -1108,6 +1117,7 @@ ipm_status ipm_assemble_hessian(ipm_ctx* c, double* h, size_t count) {
 }
 
 ipm_status ipm_update(ipm_ctx* c, double dt) {
+  NvtxRange nvtx_("ipm_update");
   if (!c) return IPM_EINVAL;
   if (!(dt > 0.0)) return fail(c, IPM_EINVAL, "ipm_update: dt must be positive");
   if (c->is2d) {
@@ -1121,6 +1131,7 @@ ipm_status ipm_update(ipm_ctx* c, double dt) {
 }
 
 ipm_status ipm_step(ipm_ctx* c, ipm_stats* s) {
+  NvtxRange nvtx_("ipm_step");
   if (!c) return IPM_EINVAL;
   IPM_CK(c, cudaGraphLaunch(c->step_exec, c->stream));
   if (s) return ipm_sync_stats(c, s);
@@ -1128,6 +1139,7 @@ ipm_status ipm_step(ipm_ctx* c, ipm_stats* s) {
 }
 
 ipm_status ipm_oneshot_step(ipm_ctx* c, ipm_stats* s) {
+  NvtxRange nvtx_("ipm_oneshot_step");
   if (!c) return IPM_EINVAL;
   IPM_CK(c, cudaGraphLaunch(c->oneshot_exec, c->stream));
   if (s) return ipm_sync_stats(c, s);
@@ -1148,6 +1160,7 @@ ipm_status ipm_step_timing(ipm_ctx* c, float* newton_ms, float* update_ms, float
 }
 
 ipm_status ipm_run(ipm_ctx* c, int64_t max_steps, ipm_stats* s) {
+  NvtxRange nvtx_("ipm_run");
   if (!c) return IPM_EINVAL;
   if (!(c->prob.t_end > 0.0)) return fail(c, IPM_EINVAL, "ipm_run: t_end must be positive");
   ipm_stats cur;

@@ -384,9 +384,11 @@ static ipm_status sc_fail(ipm_sc* s, ipm_status st, const std::string& msg) {
 #define SC_CK(s, call)                                                                                  \
   do {                                                                                                  \
     cudaError_t e_ = (call);                                                                            \
-    if (e_ != cudaSuccess)                                                                              \
+    if (e_ != cudaSuccess) {                                                                            \
+      cudaGetLastError();                                                                               \
       return sc_fail(s, e_ == cudaErrorMemoryAllocation ? IPM_ENOMEM : IPM_ECUDA,                       \
                      std::string(#call) + ": " + cudaGetErrorString(e_));                              \
+    }                                                                                                   \
   } while (0)
 
 template <typename T>
@@ -568,6 +570,7 @@ ipm_status ipm_sc_init(const ipm_problem* problem, const ipm_basis* basis, const
   do {                                                                                                  \
     cudaError_t e_ = (call);                                                                            \
     if (e_ != cudaSuccess) {                                                                            \
+      cudaGetLastError();                                                                               \
       s->err = std::string("ipm_sc_init: ") + #call + ": " + cudaGetErrorString(e_);                   \
       return fail_free(e_ == cudaErrorMemoryAllocation ? IPM_ENOMEM : IPM_ECUDA);                      \
     }                                                                                                   \
@@ -636,6 +639,7 @@ ipm_status ipm_sc_init(const ipm_problem* problem, const ipm_basis* basis, const
 }
 
 ipm_status ipm_sc_step(ipm_sc* s, ipm_sc_stats* stats) {
+  NvtxRange nvtx_("ipm_sc_step");
   if (!s) return sc_fail(nullptr, IPM_EINVAL, "ipm_sc_step: null handle");
   SC_CK(s, cudaEventRecord(s->ev[0], s->stream));
   SC_CK(s, sc_launch_step(s, s->cur, 1));
@@ -651,6 +655,7 @@ ipm_status ipm_sc_step(ipm_sc* s, ipm_sc_stats* stats) {
 }
 
 ipm_status ipm_sc_run(ipm_sc* s, int64_t max_steps, ipm_sc_stats* stats) {
+  NvtxRange nvtx_("ipm_sc_run");
   if (!s) return sc_fail(nullptr, IPM_EINVAL, "ipm_sc_run: null handle");
   SC_CK(s, cudaEventRecord(s->ev[0], s->stream));
   while (s->active > 0 && s->steps < max_steps) {

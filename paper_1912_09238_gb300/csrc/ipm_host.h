@@ -6,11 +6,20 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/ipm.h"
 #include "ipm_device.cuh"
 
 namespace ipm {
+
+// NVTX range over a host call (seen by profilers as a named region; nothing without a tool attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct HostTables {
   int p = 0, M = 0, N = 0, Q = 0;
