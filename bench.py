@@ -33,7 +33,7 @@ FP64_PEAK_TFLOPS = 1.25      # nominal dense FP64 of a GB300 (probe: 1.19 measur
 KERNELS_PER_STEP = 4         # k_order, k_newton, k_update1d, k_finalize (one CUDA graph per step)
 # dram__bytes_read.sum + dram__bytes_write.sum of one mixed-path k_newton launch on this workload,
 # from an ncu capture of the current kernel (a warm step); None for the FP64 kernel (no capture yet)
-NEWTON_TRAFFIC_BYTES = {"mixed": 6.02e6, "fp64": None, "mixed_f32f": None}
+NEWTON_TRAFFIC_BYTES = {"mixed": 6.03e6, "fp64": None, "mixed_f32f": None}
 L2_FLUSH_BYTES = 512 << 20   # > 4x the 126 MiB L2
 WINDOW = dict(nx=200, x_lo=0.45, x_hi=0.55)   # same dx as the 2000-cell mesh, around the interface
 
