@@ -33,7 +33,7 @@ FP64_PEAK_TFLOPS = 1.25      # nominal dense FP64 of a GB300 (probe: 1.19 measur
 KERNELS_PER_STEP = 4         # k_order, k_newton, k_update1d, k_finalize (one CUDA graph per step)
 # dram__bytes_read.sum + dram__bytes_write.sum of one mixed-path k_newton launch on this workload,
 # from an ncu capture of the current kernel (a warm step); None for the FP64 kernel (no capture yet)
-NEWTON_TRAFFIC_BYTES = {"mixed": 6.03e6, "fp64": None, "mixed_f32f": None}
+NEWTON_TRAFFIC_BYTES = {"mixed": None, "fp64": None, "mixed_f32f": None}
 L2_FLUSH_BYTES = 512 << 20   # > 4x the 126 MiB L2
 WINDOW = dict(nx=200, x_lo=0.45, x_hi=0.55)   # same dx as the 2000-cell mesh, around the interface
 
@@ -112,9 +112,10 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def newton_fp64_flops(N, m, Q, cells, iters, with_hessian):
+def newton_fp64_flops(N, m, Q, cells, iters, with_hessian, cached=0):
     """Algorithmic FP64 flops of one Newton launch: every cell evaluates the gradient (reconstruction +
-    projection, 4QNm) once more than it updates; every update adds the Cholesky factorisation
+    projection, 4QNm) once more than it updates, except the `cached` cells whose first check came from
+    their moment image (S - u_hat and its norm, 3Nm); every update adds the Cholesky factorisation
     ((Nm)^3/3), two triangular solves (2 (Nm)^2) and the direction at the nodes (2QNm), and on the FP64
     path the Hessian (B Q N(N+1): unique entries of B blocks, Q-term dot products). Closures and
     line-search trials are not counted."""
@@ -124,7 +125,7 @@ def newton_fp64_flops(N, m, Q, cells, iters, with_hessian):
     per_update = NM ** 3 / 3.0 + 2.0 * NM ** 2 + 2.0 * Q * N * m
     if with_hessian:
         per_update += B * Q * N * (N + 1)
-    return (cells + iters) * grad_eval + iters * per_update
+    return (cells - cached + iters) * grad_eval + cached * 3.0 * N * m + iters * per_update
 
 
 def hessian_tc_flops(N, m, Q, iters):
@@ -169,7 +170,7 @@ def measure(args, precision, flush, stream, barrier, ws):
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    newton_ms, iters = [], []
+    newton_ms, iters, cached = [], [], []
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -179,6 +180,7 @@ def measure(args, precision, flush, stream, barrier, ws):
         s = ctx.sync_stats()
         newton_ms.append(nm)
         iters.append(s.newton_iters)
+        cached.append(s.cached_checks)
         if s.failed_cells or s.tc_timeouts:
             raise RuntimeError(f"dual solve failed in {s.failed_cells} cells: {s.as_dict()}")
     barrier()
@@ -186,14 +188,15 @@ def measure(args, precision, flush, stream, barrier, ws):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     cells = d.n_interior
     value, _ = aggregate_throughput(sum(step_ms) / 1e3, cells * args.steps, ws, "cuda")
-    flops = [newton_fp64_flops(d.N, d.m, d.Q, cells, it, precision == "fp64") for it in iters]
+    flops = [newton_fp64_flops(d.N, d.m, d.Q, cells, it, precision == "fp64", ch) for it, ch in zip(iters, cached)]
     newton_s = statistics.mean(newton_ms) / 1e3
     out = {"value": value, "ms_per_step": statistics.mean(step_ms),
            "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
            "newton_ms_mean": statistics.mean(newton_ms), "newton_share_of_step": sum(newton_ms) / sum(step_ms),
            "fp64_flops_per_launch": sum(flops) / len(flops),
            "fp64_tflops": (sum(flops) / len(flops)) / newton_s / 1e12,
-           "newton_iters_per_step": statistics.mean(iters), "clocks": cl, "cells": cells, "dims": d}
+           "newton_iters_per_step": statistics.mean(iters), "cached_checks_per_step": statistics.mean(cached),
+           "clocks": cl, "cells": cells, "dims": d}
     if precision != "fp64":
         tcf = statistics.mean(hessian_tc_flops(d.N, d.m, d.Q, it) for it in iters)
         out["tensor_flops_per_launch"] = tcf
@@ -254,7 +257,8 @@ def run_gpu(args):
                 "newton_ms_mean": round(main["newton_ms_mean"], 4),
                 "newton_share_of_step": round(main["newton_share_of_step"], 4),
                 "algorithmic_fp64_flops_per_launch": round(main["fp64_flops_per_launch"]),
-                "newton_iters_per_step": round(main["newton_iters_per_step"], 1)}
+                "newton_iters_per_step": round(main["newton_iters_per_step"], 1),
+                "cached_checks_per_step": round(main["cached_checks_per_step"], 1)}
     if precision == "mixed":
         roofline["tensor_bf16_flops_per_launch"] = round(main["tensor_flops_per_launch"])
 

@@ -196,6 +196,13 @@ typedef struct {
    * Adaptive meshes solve the cells of their lowest levels with N*m <= 64 one warp per cell (nodes in
    * chunks of 32) and the others one CTA per cell; 1 keeps every cell on the CTA kernel. */
   int newton_kernel;
+  /* Convergence checks from moment images (fixed-degree meshes, CTA-per-cell kernel): 1 (default) = every
+   * cell keeps S = sum_k w_k u(Lambda(xi_k)) phi(xi_k) of the duals its last successful solve ended at,
+   * with those duals; a solve that starts from the same duals (bit for bit) takes its first gradient as
+   * S - u_hat, which is the gradient of Eq. gradient with the same arithmetic, and a cell that meets
+   * Eq. tauCrit there skips the reconstruction and the closures. Results are identical to 0 (always
+   * evaluate); device memory 2 n_cells N m doubles. */
+  int check_cache;
 } ipm_options;
 
 /* Sizes of a context's arrays. */
@@ -224,6 +231,8 @@ typedef struct {
   int64_t factorizations;   /* Cholesky factorisations of the last solve (equals newton_iters without
                                frozen Hessians) */
   int32_t fp32_fallbacks;   /* IPM_PREC_MIXED_F32_FACTOR: FP32 factorisations redone in FP64 (cumulative) */
+  int64_t cached_checks;    /* cells of the last solve whose convergence check came from their moment
+                               image (ipm_options.check_cache) */
 } ipm_stats;
 
 typedef struct ipm_ctx ipm_ctx;

@@ -43,6 +43,11 @@ struct ipm_ctx {
   double* d_factors = nullptr;      // hessian_reuse 2: kept Cholesky factors per cell
   int* d_factor_valid = nullptr;
   size_t factor_stride = 0;
+  // moment images per cell (fixed-degree meshes, check_cache != 0): the convergence check of a cell whose
+  // duals did not move since its last solve comes from them (CTA-per-cell Newton kernel)
+  bool img = false;
+  double *d_img = nullptr, *d_img_lam = nullptr, *d_img_smax = nullptr;
+  int* d_img_valid = nullptr;
   double *d_area = nullptr, *d_xf = nullptr, *d_yf = nullptr;
   int device = 0;
   cudaStream_t own_stream = nullptr;
@@ -178,6 +183,11 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.queue = nullptr;
   a.first_dev = nullptr;
   a.count_dev = nullptr;
+  const bool img = c->img && c->newton_kind == 0;
+  a.img = img ? c->d_img : nullptr;
+  a.img_lam = img ? c->d_img_lam : nullptr;
+  a.img_smax = img ? c->d_img_smax : nullptr;
+  a.img_valid = img ? c->d_img_valid : nullptr;
   a.mx.phi_img = c->d_phi_img;
   a.mx.phiT32 = c->d_phiT32;
   a.mx.n_pad = c->mx.n_pad;
@@ -418,7 +428,8 @@ static void free_ctx(ipm_ctx* c) {
   void* ptrs[] = {c->d_Phi, c->d_PhiT, c->d_w, c->d_nodes, c->d_pairs, c->d_uhat, c->d_lam, c->d_unode,
                   c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc,
                   c->d_phiT32, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf, c->d_level,
-                  c->d_factors, c->d_factor_valid, c->d_level_next, c->d_lev_w, c->d_q_eval};
+                  c->d_factors, c->d_factor_valid, c->d_level_next, c->d_lev_w, c->d_q_eval,
+                  c->d_img, c->d_img_lam, c->d_img_smax, c->d_img_valid};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -481,6 +492,7 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   if (opt.newton_kernel < 0 || opt.newton_kernel > 2) return fail(nullptr, IPM_EINVAL, "ipm_init: unknown Newton kernel");
   if (opt.hessian_reuse < 0 || opt.hessian_reuse > 2 || !(opt.reuse_ratio > 0.0 && opt.reuse_ratio < 1.0))
     return fail(nullptr, IPM_EINVAL, "ipm_init: hessian_reuse must be 0..2 with 0 < reuse_ratio < 1");
+  if (opt.check_cache != 0 && opt.check_cache != 1) return fail(nullptr, IPM_EINVAL, "ipm_init: check_cache must be 0 or 1");
   c->prob = *problem;
   c->basis = *basis;
   c->quad = *quad;
@@ -646,6 +658,7 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   }
   c->hwork_stride = c->h_in_smem ? 0 : packed_aug_count(c->NM);
   c->update_grid = std::min(c->n_interior, 65535);
+  c->img = opt.check_cache != 0 && c->n_levels == 0;
   return IPM_OK;
 }
 
@@ -660,6 +673,7 @@ static size_t ctx_footprint(const ipm_ctx* c) {
   if (c->n_levels) b += 2 * nc * 4;
   if (c->level_rules) b += nc * 4 + c->lev_w.size() * 8;
   if (c->factor_stride) b += nc * (c->factor_stride * 8 + 4);
+  if (c->img) b += nc * (2 * NM * 8 + 8 + 4);
   return b;
 }
 
@@ -679,6 +693,7 @@ void ipm_default_options(ipm_options* o) {
   o->hessian_reuse = 0;
   o->reuse_ratio = 0.5;
   o->newton_kernel = 0;
+  o->check_cache = 1;
 }
 
 const char* ipm_last_error(const ipm_ctx* c) {
@@ -789,6 +804,13 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
     CK(cudaMalloc(&c->d_factor_valid, (size_t)c->n_cells * sizeof(int)), "cudaMalloc factor flags");
     if (st == IPM_OK) CK(cudaMemsetAsync(c->d_factor_valid, 0, (size_t)c->n_cells * sizeof(int), c->stream), "memset factor flags");
   }
+  if (c->img) {
+    CK(cudaMalloc(&c->d_img, nstate * sizeof(double)), "cudaMalloc moment images");
+    CK(cudaMalloc(&c->d_img_lam, nstate * sizeof(double)), "cudaMalloc image duals");
+    CK(cudaMalloc(&c->d_img_smax, (size_t)c->n_cells * sizeof(double)), "cudaMalloc image speeds");
+    CK(cudaMalloc(&c->d_img_valid, (size_t)c->n_cells * sizeof(int)), "cudaMalloc image flags");
+    if (st == IPM_OK) CK(cudaMemsetAsync(c->d_img_valid, 0, (size_t)c->n_cells * sizeof(int), c->stream), "memset image flags");
+  }
   if (st != IPM_OK) {
     free_ctx(c);
     return st;
@@ -883,6 +905,9 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   if (st == IPM_OK && c->warp_warps > 0) {
     if (c->opt.newton_kernel == 0) st = autotune_newton(c);
     else c->newton_kind = c->opt.newton_kernel == 2 ? 1 : 0;
+    // the timing runs restored the duals but left images and nodal states of their own
+    if (st == IPM_OK && c->img)
+      CK(cudaMemsetAsync(c->d_img_valid, 0, (size_t)c->n_cells * sizeof(int), c->stream), "reset image flags");
   } else if (st == IPM_OK && c->opt.newton_kernel == 2) {
     st = fail(nullptr, IPM_EINVAL, "ipm_init: the warp-per-cell kernel needs N*m <= 64 and a fixed degree");
   }
@@ -1073,6 +1098,7 @@ static void fill_stats(const StepScalars& h, ipm_stats* s) {
   s->tc_timeouts = h.tc_timeouts;
   s->factorizations = (int64_t)h.last_factorizations;
   s->fp32_fallbacks = h.fp32_fallbacks;
+  s->cached_checks = (int64_t)h.last_cached_checks;
 }
 
 ipm_status ipm_sync_stats(ipm_ctx* c, ipm_stats* s) {

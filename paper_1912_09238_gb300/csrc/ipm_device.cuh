@@ -248,6 +248,8 @@ struct StepScalars {
   unsigned long long factorizations;       // Cholesky factorisations since the last reduction
   unsigned long long last_factorizations;  // ... of the last solve (frozen-Hessian statistics)
   int fp32_fallbacks;                      // FP32-factor mode: factorisations redone in FP64 (cumulative)
+  unsigned long long cached_checks;        // cells whose convergence check came from their moment image
+  unsigned long long last_cached_checks;   // ... of the last solve
 };
 
 // Mixed-precision Hessian (tensor cores): tiling of H_ab = Phi^T diag(w J_ab) Phi as MMAs with
@@ -304,6 +306,14 @@ struct NewtonArgs {
   int* queue;
   const int* first_dev;
   const int* count_dev;
+  // moment images (fixed-degree meshes, CTA-per-cell kernel; nullptr: off): img[cell] holds
+  // S = sum_k w_k u(Lambda(xi_k)) phi(xi_k) of the duals img_lam[cell] that the cell's last successful
+  // solve ended at, img_smax[cell] the wave speed at those duals' nodal states; img_valid[cell] != 0
+  // when the three belong together
+  double* img;           // [cell][NM]
+  double* img_lam;       // [cell][NM]
+  double* img_smax;      // [cell]
+  int* img_valid;        // [cell]
   MixedTiles mx;         // mixed path only
   uint32_t off_h, off_a, off_b;  // shared-memory byte offsets: packed H, A staging, Phi chunks
 };

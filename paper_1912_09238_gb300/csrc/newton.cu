@@ -56,6 +56,21 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* s_red) {
   __syncthreads();
 }
 
+// Stopping quantity of Eq. tauCrit: sum over the moments i of the 2-norm of g_i over the variables
+// (block-wide; every thread returns it)
+template <int M>
+__device__ __forceinline__ double grad_residual(const double* s_g, int N, double* s_red) {
+  double gres[1] = {0.0};
+  for (int i = threadIdx.x; i < N; i += NT) {
+    double nrm = 0.0;
+#pragma unroll
+    for (int c = 0; c < M; ++c) nrm = fma(s_g[i * M + c], s_g[i * M + c], nrm);
+    gres[0] += sqrt(nrm);
+  }
+  block_sum<1>(gres, s_red);
+  return gres[0];
+}
+
 // (a, b) of the packed index ab (a <= b)
 template <int M>
 __device__ __forceinline__ void unpack_ab(int ab, int& a, int& b) {
@@ -594,6 +609,41 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
     }
     __syncthreads();
 
+    // Convergence check from the moment image. While the duals are bit for bit those the cell's last
+    // successful solve ended at, the gradient at the start of this solve is S - u_hat (Eq. gradient)
+    // with exactly the arithmetic of a fresh evaluation (same nodes, same sums), so a cell whose new
+    // moments already meet Eq. tauCrit needs no reconstruction and no closures; its nodal states and
+    // wave speed are those its last solve left for the same duals.
+    // The images are kept by every solve that moves the duals (One-Shot steps included); a Hessian dump
+    // leaves them out and only invalidates.
+    const bool img_rd = a.img != nullptr && !a.one_step && !a.h_dump;
+    const bool img_wr = a.img != nullptr && !a.h_dump;
+    if (img_rd) {
+      bool same = a.img_valid[cell] != 0;
+      if (same) {
+        const double* Sc = a.img + (size_t)cell * NMX;
+        const double* Lc = a.img_lam + (size_t)cell * NMX;
+        for (int r = tid; r < NM; r += NT) {
+          same = same && __double_as_longlong(Lc[r]) == __double_as_longlong(s_lam[r]);
+          s_g[r] = Sc[r] - s_uh[r];
+        }
+      }
+      if (__syncthreads_and(same)) {
+        const double res = grad_residual<M>(s_g, N, s_red);
+        if (res < a.tau) {                           // false for NaN
+          if (tid == 0) {
+            a.iters[cell] = 0;
+            a.status[cell] = ST_OK;
+            atomicAdd(&a.sc->cached_checks, 1ULL);
+            if (a.track_speed) atomic_max_pos(&a.sc->smax_bits, a.img_smax[cell]);
+          }
+          __syncthreads();
+          continue;
+        }
+      }
+    }
+    if (a.img != nullptr && tid == 0) a.img_valid[cell] = 0;   // this solve rewrites the cell's states
+
     int it = 0, st = ST_OK;
     // frozen Hessians (hessian_reuse > 0): the Cholesky factor of an earlier iterate is kept and reused
     // while the Newton steps it gives converge fast enough
@@ -670,18 +720,12 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
           acc3 = fma(Phi[(size_t)(q + 3) * NX + i], wu[q + 3], acc3);
         }
         for (; q < Qc; ++q) acc0 = fma(Phi[(size_t)q * NX + i], wu[q], acc0);
-        s_g[r] = ((acc0 + acc1) + (acc2 + acc3)) - s_uh[r];
+        const double S = (acc0 + acc1) + (acc2 + acc3);
+        s_g[r] = S - s_uh[r];
+        if (img_wr) a.img[(size_t)cell * NMX + r] = S;
       }
       __syncthreads();
-      double gres[1] = {0.0};
-      for (int i = tid; i < N; i += NT) {
-        double nrm = 0.0;
-#pragma unroll
-        for (int c = 0; c < M; ++c) nrm = fma(s_g[i * M + c], s_g[i * M + c], nrm);
-        gres[0] += sqrt(nrm);
-      }
-      block_sum<1>(gres, s_red);
-      const double res = gres[0];
+      const double res = grad_residual<M>(s_g, N, s_red);
 
       if (red[2] > 0.0) { st = ST_INFEASIBLE; break; }
       if (!isfinite(res)) { st = ST_NONFINITE; break; }
@@ -853,7 +897,10 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       for (int r = tid; r < NM; r += NT) fs[nph + r] = s_dinv[r];
       if (tid == 0) a.factor_valid[cell] = 1;
     }
-    if (a.track_speed) {
+    const bool keep_img = img_wr && st == ST_OK;
+    if (keep_img)
+      for (int r = tid; r < NM; r += NT) a.img_lam[(size_t)cell * NMX + r] = s_lam[r];
+    if (a.track_speed || keep_img) {
       // wave speeds at the nodes of the rule this cell's update integrates with
       const int qs = (a.lev_w && a.level_next) ? a.lev_q[a.level_next[cell]] : Q;
       double smax = 0.0;
@@ -870,7 +917,11 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       if (tid == 0) {
         double v = 0.0;
         for (int ww = 0; ww < NWARPS; ++ww) v = fmax(v, s_red[ww]);
-        atomic_max_pos(&a.sc->smax_bits, v);
+        if (a.track_speed) atomic_max_pos(&a.sc->smax_bits, v);
+        if (keep_img) {
+          a.img_smax[cell] = v;
+          a.img_valid[cell] = 1;
+        }
       }
     }
     __syncthreads();

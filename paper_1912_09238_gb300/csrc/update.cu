@@ -293,6 +293,8 @@ __global__ void __launch_bounds__(256) k_finalize(StepScalars* sc, const int* it
     sc->first_status = s_fail[0] ? status[s_first[0]] : 0;
     sc->last_factorizations = sc->factorizations;
     sc->factorizations = 0;
+    sc->last_cached_checks = sc->cached_checks;
+    sc->cached_checks = 0;
     sc->work_counter = 0;
     sc->update_counter = 0;
     sc->smax_bits = sc->fixed_smax_bits;

@@ -66,7 +66,8 @@ class ipm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("newton_tol", ctypes.c_double), ("max_newton", ctypes.c_int),
                 ("armijo_c", ctypes.c_double), ("max_halvings", ctypes.c_int), ("slack_rel", ctypes.c_double),
                 ("adapt_min_degree", ctypes.c_int), ("delta_lo", ctypes.c_double), ("delta_hi", ctypes.c_double),
-                ("hessian_reuse", ctypes.c_int), ("reuse_ratio", ctypes.c_double), ("newton_kernel", ctypes.c_int)]
+                ("hessian_reuse", ctypes.c_int), ("reuse_ratio", ctypes.c_double), ("newton_kernel", ctypes.c_int),
+                ("check_cache", ctypes.c_int)]
 
 
 class ipm_dims(ctypes.Structure):
@@ -79,7 +80,7 @@ class ipm_stats(ctypes.Structure):
                 ("first_failed_cell", ctypes.c_int32), ("first_status", ctypes.c_int32),
                 ("dt", ctypes.c_double), ("t", ctypes.c_double), ("residual", ctypes.c_double),
                 ("steps", ctypes.c_int64), ("tc_timeouts", ctypes.c_int32), ("factorizations", ctypes.c_int64),
-                ("fp32_fallbacks", ctypes.c_int32)]
+                ("fp32_fallbacks", ctypes.c_int32), ("cached_checks", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
