@@ -375,6 +375,11 @@ static ipm_status autotune_newton(ipm_ctx* c) {
       if (e == cudaSuccess) {
         NewtonArgs a = newton_args(c, 0);
         a.track_speed = 0;
+        // both variants evaluate every check: the timing compares the kernels, not the image cache
+        a.img = nullptr;
+        a.img_lam = nullptr;
+        a.img_smax = nullptr;
+        a.img_valid = nullptr;
         e = launch_newton_ctx(c, a, c->n_interior, c->stream);
       }
       if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
