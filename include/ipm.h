@@ -196,12 +196,13 @@ typedef struct {
    * Adaptive meshes solve the cells of their lowest levels with N*m <= 64 one warp per cell (nodes in
    * chunks of 32) and the others one CTA per cell; 1 keeps every cell on the CTA kernel. */
   int newton_kernel;
-  /* Convergence checks from moment images (fixed-degree meshes, CTA-per-cell kernel): 1 (default) = every
+  /* Convergence checks from moment images (fixed-degree meshes on the CTA-per-cell kernel; adaptive
+   * meshes with one quadrature rule for every level, on both of their kernels): 1 (default) = every
    * cell keeps S = sum_k w_k u(Lambda(xi_k)) phi(xi_k) of the duals its last successful solve ended at,
-   * with those duals; a solve that starts from the same duals (bit for bit) takes its first gradient as
-   * S - u_hat, which is the gradient of Eq. gradient with the same arithmetic, and a cell that meets
-   * Eq. tauCrit there skips the reconstruction and the closures. Results are identical to 0 (always
-   * evaluate); device memory 2 n_cells N m doubles. */
+   * with those duals and its level; a solve that starts from the same duals (bit for bit) at the same
+   * level takes its first gradient as S - u_hat, which is the gradient of Eq. gradient with the same
+   * arithmetic, and a cell that meets Eq. tauCrit there skips the reconstruction and the closures.
+   * Results are identical to 0 (always evaluate); device memory 2 n_cells N m doubles. */
   int check_cache;
 } ipm_options;
 

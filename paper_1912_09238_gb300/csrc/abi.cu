@@ -663,7 +663,9 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   }
   c->hwork_stride = c->h_in_smem ? 0 : packed_aug_count(c->NM);
   c->update_grid = std::min(c->n_interior, 65535);
-  c->img = opt.check_cache != 0 && c->n_levels == 0;
+  // moment images: fixed degree, or adaptive degree on one rule for every level (with a rule per level
+  // the nodal states a cell writes depend on its neighbours' levels too)
+  c->img = opt.check_cache != 0 && !c->level_rules;
   return IPM_OK;
 }
 

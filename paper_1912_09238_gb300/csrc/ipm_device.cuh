@@ -306,10 +306,9 @@ struct NewtonArgs {
   int* queue;
   const int* first_dev;
   const int* count_dev;
-  // moment images (fixed-degree meshes, CTA-per-cell kernel; nullptr: off): img[cell] holds
-  // S = sum_k w_k u(Lambda(xi_k)) phi(xi_k) of the duals img_lam[cell] that the cell's last successful
-  // solve ended at, img_smax[cell] the wave speed at those duals' nodal states; img_valid[cell] != 0
-  // when the three belong together
+  // moment images (nullptr: off): img[cell] holds S = sum_k w_k u(Lambda(xi_k)) phi(xi_k) of the duals
+  // img_lam[cell] that the cell's last successful solve ended at, img_smax[cell] the wave speed at those
+  // duals' nodal states; img_valid[cell] = level + 1 when the three belong together (0: none)
   double* img;           // [cell][NM]
   double* img_lam;       // [cell][NM]
   double* img_smax;      // [cell]

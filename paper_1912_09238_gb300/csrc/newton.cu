@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
     const bool img_rd = a.img != nullptr && !a.one_step && !a.h_dump;
     const bool img_wr = a.img != nullptr && !a.h_dump;
     if (img_rd) {
-      bool same = a.img_valid[cell] != 0;
+      bool same = a.img_valid[cell] == lev_c + 1;     // the image belongs to this level
       if (same) {
         const double* Sc = a.img + (size_t)cell * NMX;
         const double* Lc = a.img_lam + (size_t)cell * NMX;
@@ -920,7 +920,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
         if (a.track_speed) atomic_max_pos(&a.sc->smax_bits, v);
         if (keep_img) {
           a.img_smax[cell] = v;
-          a.img_valid[cell] = 1;
+          a.img_valid[cell] = lev_c + 1;
         }
       }
     }

@@ -82,6 +82,44 @@ __global__ void __launch_bounds__(256) k_newton_warpq(NewtonArgs a, int slice, i
       s_uh[r] = uh_g[r];
     }
     __syncwarp();
+    // convergence check from the cell's moment image (as in the CTA-per-cell kernel): S - u_hat with the
+    // sums of this kernel's own evaluation, valid while the duals and the level are those it was taken at
+    const bool img_rd = a.img != nullptr && !a.one_step && !a.h_dump;
+    const bool img_wr = a.img != nullptr && !a.h_dump;
+    if (img_rd) {
+      bool same = a.img_valid[cell] == lev + 1;
+      if (same) {
+        const double* Sc = a.img + (size_t)cell * NMX;
+        const double* Lc = a.img_lam + (size_t)cell * NMX;
+        for (int r = lane; r < NM; r += 32) {
+          same = same && __double_as_longlong(Lc[r]) == __double_as_longlong(s_lam[r]);
+          s_g[r] = Sc[r] - s_uh[r];
+        }
+      }
+      if (__all_sync(0xffffffffu, same)) {
+        __syncwarp();
+        double res = 0.0;
+        for (int i = lane; i < N; i += 32) {
+          double nrm = 0.0;
+#pragma unroll
+          for (int c = 0; c < M; ++c) nrm = fma(s_g[i * M + c], s_g[i * M + c], nrm);
+          res += sqrt(nrm);
+        }
+        res = warp_sum(res);
+        if (res < a.tau) {
+          if (lane == 0) {
+            a.iters[cell] = 0;
+            a.status[cell] = ST_OK;
+            atomicAdd(&a.sc->cached_checks, 1ULL);
+            if (a.track_speed) atomic_max_pos(&a.sc->smax_bits, a.img_smax[cell]);
+          }
+          __syncwarp();
+          continue;
+        }
+      }
+    }
+    if (a.img != nullptr && lane == 0) a.img_valid[cell] = 0;
+    __syncwarp();
     int it = 0, st = ST_OK;
     for (;;) {
       // (a1)-(a3): reconstruction and closure per node, cost terms, gradient sums chunk by chunk; the
@@ -130,6 +168,7 @@ __global__ void __launch_bounds__(256) k_newton_warpq(NewtonArgs a, int slice, i
         const double t = s_lam[r] * s_uh[r];
         red[3] += t;
         red[4] += fabs(t);
+        if (img_wr) a.img[(size_t)cell * NMX + r] = s_g[r];
         s_g[r] -= s_uh[r];
       }
       warp_sums_q<5>(red);
@@ -329,7 +368,10 @@ __global__ void __launch_bounds__(256) k_newton_warpq(NewtonArgs a, int slice, i
       a.iters[cell] = it;
       a.status[cell] = st;
     }
-    if (a.track_speed) {
+    const bool keep_img = img_wr && st == ST_OK;
+    if (keep_img)
+      for (int r = lane; r < NM; r += 32) a.img_lam[(size_t)cell * NMX + r] = s_lam[r];
+    if (a.track_speed || keep_img) {
       const int qs = (a.lev_w && a.level_next) ? a.lev_q[a.level_next[cell]] : Qc;
       double smax = 0.0;
       for (int q = lane; q < qs; q += 32) {
@@ -340,7 +382,13 @@ __global__ void __launch_bounds__(256) k_newton_warpq(NewtonArgs a, int slice, i
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-      if (lane == 0) atomic_max_pos(&a.sc->smax_bits, smax);
+      if (lane == 0) {
+        if (a.track_speed) atomic_max_pos(&a.sc->smax_bits, smax);
+        if (keep_img) {
+          a.img_smax[cell] = smax;
+          a.img_valid[cell] = lev + 1;
+        }
+      }
     }
     __syncwarp();
   }

@@ -111,3 +111,54 @@ def test_checkpoint_restore_into_a_fresh_context():
     _same(a, c)
     for x in (a, b, c):
         x.close()
+
+
+def test_headline_workload_full_size():
+    """The 2000-cell Sod workload in mixed precision, in the launch configuration the bench times: ten
+    steps with images against ten without, bit for bit (the first step is checked against the oracle
+    on sampled cells in test_gpu_mixed_1d)."""
+    a = gpu_context(workloads.SOD_1D, precision="mixed", check_cache=1)
+    b = gpu_context(workloads.SOD_1D, precision="mixed", check_cache=0)
+    cached = _steps(a, b, 10)
+    _same(a, b)
+    assert cached > 8 * 1500
+    a.close()
+    b.close()
+
+
+ADAPTIVE = [
+    # shear layer: the transverse perturbation moves every cell, so few checks come from images
+    (workloads.variant(workloads.KH_2D, nx=16, ny=16, M=4, nq=5), dict(delta_lo=2e-4, delta_hi=2e-5), 0),
+    # ramp: the freestream ahead of the shock is settled after a few steps
+    (workloads.variant(workloads.RAMP_2D, nx=16, ny=8, M=4, nq=5), dict(delta_lo=1e-10, delta_hi=1e-8), 1),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ADAPTIVE, ids=["shear_layer", "ramp"])
+def test_adaptive_degrees_on_one_rule(precision, case):
+    """Adaptive degrees (Algorithm 3) with the shared Gauss rule: the images carry the level they were
+    taken at, so a cell whose level changed is evaluated; the degree-2 cells (one warp per cell, nodes in
+    chunks) and the others (one CTA per cell) both use them. Levels, moments and duals bit for bit."""
+    w, lv, min_cached = case
+    kw = dict(precision=precision, adapt_min_degree=2, **lv)
+    a, b = gpu_context(w, check_cache=1, **kw), gpu_context(w, check_cache=0, **kw)
+    cached = 0
+    for _ in range(8):
+        sa, sb = a.step(), b.step()
+        assert sa.failed_cells == 0 and (sa.newton_iters, sa.dt) == (sb.newton_iters, sb.dt)
+        assert np.array_equal(a.get_levels(), b.get_levels())
+        cached += sa.cached_checks
+    _same(a, b)
+    assert cached >= min_cached
+    a.close()
+    b.close()
+
+
+def test_per_level_rules_do_not_use_images():
+    w = workloads.variant(workloads.KH_2D, nx=10, ny=10, M=3, nq=3, p=2, cc_levels=(1, 2, 2),
+                          dparam=((0.005, 0.0, 0.0), (0.0, 0.1, 0.0), (0.05, 0.0, 0.0), (0.0, 0.0, 0.0)))
+    ctx = gpu_context(w, adapt_min_degree=1, delta_lo=2e-5, delta_hi=2e-4)
+    for _ in range(3):
+        assert ctx.step().cached_checks == 0
+    ctx.close()
