@@ -362,34 +362,59 @@ __device__ void forward_substitute(const T* A, int n, const T* s_dinv, T* x) {
   }
 }
 
-// Back substitution L^T x = b in place on x (x holds b on entry), blocks of NB from the bottom: one
-// warp solves the diagonal block (lane i holds entry kb + i), then all threads update the entries above.
+// Diagonal block of the back substitution, one warp: lane i holds entry kb + i of the right-hand side
+// in v on entry and of the solution on exit (lanes >= kw: unused).
+template <typename T>
+__device__ __forceinline__ T back_diag(const T* A, int kb, int kw, const T* s_dinv, T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = NB - 1; k >= 0; --k) {
+    if (k < kw) {
+      const T xk = __shfl_sync(0xffffffffu, v, k) * s_dinv[kb + k];
+      if (lane == k) v = xk;
+      if (lane < k) v = fma(-A[rowoff(kb + k) + kb + lane], xk, v);
+    }
+  }
+  return v;
+}
+
+// Back substitution L^T x = b in place on x (x holds b on entry), blocks of NB from the bottom, with
+// one block of look-ahead: once block kb is solved, warp 0 applies it to the NB entries of the next
+// block up and solves that block's diagonal, while warps 1.. apply it to all entries above those.
+// Every entry receives the same products in the same order as without the look-ahead.
 template <typename T>
 __device__ void back_substitute(const T* A, int n, const T* s_dinv, T* x) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  for (int kb = ((n - 1) / NB) * NB; kb >= 0; kb -= NB) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int kb = ((n - 1) / NB) * NB;
+  if (warp == 0) {
     const int kw = min(NB, n - kb);
-    if (tid < 32) {
-      T v = lane < kw ? x[kb + lane] : (T)0;
+    const T v = back_diag(A, kb, kw, s_dinv, lane < kw ? x[kb + lane] : (T)0);
+    if (lane < kw) x[kb + lane] = v;
+  }
+  __syncthreads();
+  while (kb > 0) {
+    const int kw = min(NB, n - kb), kb1 = kb - NB;   // the blocks above the last one are full
+    if (warp == 0) {
+      T v = (T)0;
+      if (lane < NB) {
+        v = x[kb1 + lane];
 #pragma unroll
-      for (int k = NB - 1; k >= 0; --k) {
-        if (k < kw) {
-          const T xk = __shfl_sync(0xffffffffu, v, k) * s_dinv[kb + k];
-          if (lane == k) v = xk;
-          if (lane < k) v = fma(-A[rowoff(kb + k) + kb + lane], xk, v);
-        }
+        for (int k = 0; k < NB; ++k)
+          if (k < kw) v = fma(-A[rowoff(kb + k) + kb1 + lane], x[kb + k], v);
       }
-      if (lane < kw) x[kb + lane] = v;
-    }
-    __syncthreads();
-    for (int r = tid; r < kb; r += NT) {
-      T v = x[r];
+      v = back_diag(A, kb1, NB, s_dinv, v);
+      if (lane < NB) x[kb1 + lane] = v;
+    } else {
+      for (int r = tid - 32; r < kb1; r += NT - 32) {
+        T v = x[r];
 #pragma unroll
-      for (int k = 0; k < NB; ++k)
-        if (k < kw) v = fma(-A[rowoff(kb + k) + r], x[kb + k], v);
-      x[r] = v;
+        for (int k = 0; k < NB; ++k)
+          if (k < kw) v = fma(-A[rowoff(kb + k) + r], x[kb + k], v);
+        x[r] = v;
+      }
     }
     __syncthreads();
+    kb = kb1;
   }
 }
 
