@@ -48,6 +48,10 @@ struct ipm_ctx {
   bool img = false;
   double *d_img = nullptr, *d_img_lam = nullptr, *d_img_smax = nullptr;
   int* d_img_valid = nullptr;
+  // 1-D meshes: the Lax-Friedrichs terms the CTA-per-cell Newton launch folds in (A, B per cell) and
+  // the per-cell counts of finished neighbours
+  double *d_lf_a = nullptr, *d_lf_b = nullptr;
+  int* d_lf_cnt = nullptr;
   double *d_area = nullptr, *d_xf = nullptr, *d_yf = nullptr;
   int device = 0;
   cudaStream_t own_stream = nullptr;
@@ -188,6 +192,11 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.img_lam = img ? c->d_img_lam : nullptr;
   a.img_smax = img ? c->d_img_smax : nullptr;
   a.img_valid = img ? c->d_img_valid : nullptr;
+  a.lf_a = nullptr;                // set by enqueue_step on 1-D meshes
+  a.lf_b = nullptr;
+  a.lf_cnt = nullptr;
+  a.bc_left = c->prob.bc_left;
+  a.bc_right = c->prob.bc_right;
   a.mx.phi_img = c->d_phi_img;
   a.mx.phiT32 = c->d_phiT32;
   a.mx.n_pad = c->mx.n_pad;
@@ -270,7 +279,7 @@ static cudaError_t launch_newton_ctx(const ipm_ctx* c, const NewtonArgs& a, int 
 }
 
 // enqueue: queue reset, Newton over the interior
-static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
+static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s, bool lf = false) {
   cudaError_t e = cudaSuccess;
   if (c->n_levels) {
     // the levels of this step's update (from the moments the dual problems are solved for): the Newton
@@ -297,20 +306,31 @@ static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s) {
     return launch_newton_ctx(c, a, c->n_interior, s);
   }
   if (e == cudaSuccess) e = launch_order(c->d_iters, c->n_interior, c->prob.nx, c->is2d ? 1 : 0, c->d_order, s);
+  if (e == cudaSuccess && lf) e = cudaMemsetAsync(c->d_lf_cnt, 0, (size_t)c->n_cells * sizeof(int), s);
   if (e != cudaSuccess) return e;
   NewtonArgs a = newton_args(c, one_step);
   a.cell_list = c->d_order;
+  if (lf) {
+    a.lf_a = c->d_lf_a;
+    a.lf_b = c->d_lf_b;
+    a.lf_cnt = c->d_lf_cnt;
+  }
   return launch_newton_ctx(c, a, c->n_interior, s);
 }
 
 // one step of Algorithm 1 (one_step = 0) or Algorithm 2 (one_step = 1)
 static cudaError_t enqueue_step(ipm_ctx* c, int one_step, cudaStream_t s) {
+  // 1-D meshes on the CTA-per-cell kernel: the Newton launch folds in the Lax-Friedrichs terms and a
+  // small kernel applies dt
+  const bool lf = !c->is2d && c->newton_kind == 0 && c->d_lf_a != nullptr;
   cudaError_t e = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal);
-  if (e == cudaSuccess) e = enqueue_newton(c, one_step, s);
+  if (e == cudaSuccess) e = enqueue_newton(c, one_step, s, lf);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal);
   if (e != cudaSuccess) return e;
   if (c->is2d) {
     e = launch_update2d(update2d_args(c, 0.0, true, one_step == 0), c->update_grid, s);
+  } else if (lf) {
+    e = launch_lf_combine(update_args(c, 0.0, true), c->NM, c->d_lf_a, c->d_lf_b, c->update_grid, s);
   } else {
     Update1DArgs u = update_args(c, 0.0, true);
     e = launch_update1d(c->phys, c->m, u, c->update_grid, s);
@@ -434,7 +454,7 @@ static void free_ctx(ipm_ctx* c) {
                   c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc,
                   c->d_phiT32, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf, c->d_level,
                   c->d_factors, c->d_factor_valid, c->d_level_next, c->d_lev_w, c->d_q_eval,
-                  c->d_img, c->d_img_lam, c->d_img_smax, c->d_img_valid};
+                  c->d_img, c->d_img_lam, c->d_img_smax, c->d_img_valid, c->d_lf_a, c->d_lf_b, c->d_lf_cnt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -681,6 +701,7 @@ static size_t ctx_footprint(const ipm_ctx* c) {
   if (c->level_rules) b += nc * 4 + c->lev_w.size() * 8;
   if (c->factor_stride) b += nc * (c->factor_stride * 8 + 4);
   if (c->img) b += nc * (2 * NM * 8 + 8 + 4);
+  if (!c->is2d) b += nc * (2 * NM * 8 + 4);
   return b;
 }
 
@@ -817,6 +838,11 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
     CK(cudaMalloc(&c->d_img_smax, (size_t)c->n_cells * sizeof(double)), "cudaMalloc image speeds");
     CK(cudaMalloc(&c->d_img_valid, (size_t)c->n_cells * sizeof(int)), "cudaMalloc image flags");
     if (st == IPM_OK) CK(cudaMemsetAsync(c->d_img_valid, 0, (size_t)c->n_cells * sizeof(int), c->stream), "memset image flags");
+  }
+  if (!c->is2d) {
+    CK(cudaMalloc(&c->d_lf_a, nstate * sizeof(double)), "cudaMalloc folded update terms");
+    CK(cudaMalloc(&c->d_lf_b, nstate * sizeof(double)), "cudaMalloc folded update terms");
+    CK(cudaMalloc(&c->d_lf_cnt, (size_t)c->n_cells * sizeof(int)), "cudaMalloc folded update counts");
   }
   if (st != IPM_OK) {
     free_ctx(c);

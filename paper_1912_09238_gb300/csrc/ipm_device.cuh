@@ -313,6 +313,15 @@ struct NewtonArgs {
   double* img_lam;       // [cell][NM]
   double* img_smax;      // [cell]
   int* img_valid;        // [cell]
+  // 1-D Lax-Friedrichs update folded into the Newton launch (nullptr: off). With nu = dx / (2 dt) the
+  // update of cell j is u_hat_j = A_j - (dt/dx) B_j with A_j = P(w (u_l + u_r) / 2) and
+  // B_j = P(w (f(u_r) - f(u_l)) / 2) over the nodal states of its two neighbours, neither of which
+  // needs dt; the CTA that finishes the last neighbour of j forms lf_a[j] = A_j and lf_b[j] = B_j.
+  // lf_cnt[j] counts the finished neighbours (zeroed before the launch).
+  double* lf_a;          // [cell][NM]
+  double* lf_b;          // [cell][NM]
+  int* lf_cnt;           // [cell]
+  int bc_left, bc_right;
   MixedTiles mx;         // mixed path only
   uint32_t off_h, off_a, off_b;  // shared-memory byte offsets: packed H, A staging, Phi chunks
 };

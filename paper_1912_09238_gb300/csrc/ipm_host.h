@@ -108,6 +108,10 @@ cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayou
                               cudaStream_t s);
 cudaError_t prepare_update1d(int phys, int m, int N, int Q);
 cudaError_t launch_update1d(int phys, int m, const Update1DArgs& a, int grid, cudaStream_t s);
+// u_hat_j = lf_a[j] - (dt/dx) lf_b[j] on the interior cells (the Lax-Friedrichs update folded into the
+// Newton launch), with the ghost copies and residual of launch_update1d
+cudaError_t launch_lf_combine(const Update1DArgs& a, int NM, const double* lf_a, const double* lf_b, int grid,
+                              cudaStream_t s);
 cudaError_t launch_init1d(int ent, int m, const Tables& tab, const EntParams& ent_p, const ipm_problem& prob,
                           double* uhat, double* lam, int n_cells, cudaStream_t s);
 cudaError_t launch_finalize(StepScalars* sc, const int* iters, const int* status, const double* cell_resid,

@@ -561,6 +561,98 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
   return true;
 }
 
+// ------------------------------------------------------------------------------------------------
+// 1-D Lax-Friedrichs update folded into the Newton launch (Algorithm 1, the moment update; App. A).
+// With nu = dx / (2 dt) the update of cell j,
+//   u_hat_j = sum_k w_k [u_j - dt/dx (g(u_j, u_r) - g(u_l, u_j))] phi(xi_k),
+// reduces to A_j - (dt/dx) B_j with A_j = sum_k w_k (u_l + u_r)/2 phi and B_j = sum_k w_k (f(u_r) -
+// f(u_l))/2 phi: the centre value cancels and neither term needs dt, which is known only when every
+// cell is solved. Cell k, once its nodal states are final, counts itself towards each cell whose
+// neighbour it is; the CTA that completes a count forms that cell's A and B. Fixed (Dirichlet) ghosts
+// are final from the start and are not counted; a cell with two of them is formed by its own CTA.
+// Scratch: s_ia, s_ib [M][Q] integrands, s_part [2][NWARPS][NM] partial sums; all threads call.
+// ------------------------------------------------------------------------------------------------
+template <int PHYS, int M>
+__device__ void lf_fold(const NewtonArgs& a, int k, double* s_ia, double* s_ib, double* s_part, int* s_ready) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nx = a.nx, Q = a.tab.Q, N = a.tab.N, NM = N * M;
+  __threadfence();                                   // this CTA's nodal states of k, before the counts
+  __syncthreads();
+  if (tid == 0) {
+    int n = 0;
+    const int cand[5] = {k - 1, k + 1, k, 1, nx};
+    for (int ci = 0; ci < 5; ++ci) {
+      const int j = cand[ci];
+      bool seen = j < 1 || j > nx;
+      for (int cj = 0; cj < ci; ++cj) seen = seen || cand[cj] == j;
+      if (seen) continue;
+      const int jl = neighbour(j, nx, -1, a.bc_left), jr = neighbour(j, nx, +1, a.bc_right);
+      const bool il = jl >= 1 && jl <= nx, ir = jr >= 1 && jr <= nx && jr != jl;
+      const int target = (il ? 1 : 0) + (ir ? 1 : 0);
+      if (target == 0) {
+        if (j == k) s_ready[n++] = j;
+      } else if (jl == k || jr == k) {
+        if (atomicAdd(&a.lf_cnt[j], 1) == target - 1) s_ready[n++] = j;
+      }
+    }
+    __threadfence();                                 // the other CTAs' nodal states, after the counts
+    s_ready[3] = n;
+  }
+  __syncthreads();
+  const int n_ready = s_ready[3];
+  const double* __restrict__ w = a.tab.w;
+  const double* __restrict__ Phi = a.tab.Phi;
+  const int MQ = M * Q;
+  const int qw = (Q + NWARPS - 1) / NWARPS;
+  const int q_lo = min(Q, warp * qw), q_hi = min(Q, q_lo + qw);
+  for (int t = 0; t < n_ready; ++t) {
+    const int j = s_ready[t];
+    const double* ul_g = a.unode + (size_t)neighbour(j, nx, -1, a.bc_left) * MQ;
+    const double* ur_g = a.unode + (size_t)neighbour(j, nx, +1, a.bc_right) * MQ;
+    for (int q = tid; q < Q; q += NT) {
+      double ul[M], ur[M], fl[M], fr[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        ul[c] = ul_g[c * Q + q];
+        ur[c] = ur_g[c * Q + q];
+      }
+      Flux1D<PHYS, M>::f(ul, a.ent.gamma, fl);
+      Flux1D<PHYS, M>::f(ur, a.ent.gamma, fr);
+      const double wq = w[q];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        s_ia[c * Q + q] = wq * (0.5 * (ul[c] + ur[c]));
+        s_ib[c * Q + q] = wq * (0.5 * (fr[c] - fl[c]));
+      }
+    }
+    __syncthreads();
+    // projections: warp k sums the nodes [k qw, (k+1) qw) for every entry; partials added in warp order
+    for (int rr = lane; rr < NM; rr += 32) {
+      const int i = rr / M, c = rr - i * M;
+      double sa = 0.0, sb = 0.0;
+      for (int q = q_lo; q < q_hi; ++q) {
+        const double ph = Phi[(size_t)q * N + i];
+        sa = fma(ph, s_ia[c * Q + q], sa);
+        sb = fma(ph, s_ib[c * Q + q], sb);
+      }
+      s_part[warp * NM + rr] = sa;
+      s_part[(NWARPS + warp) * NM + rr] = sb;
+    }
+    __syncthreads();
+    for (int rr = tid; rr < NM; rr += NT) {
+      double va = 0.0, vb = 0.0;
+#pragma unroll
+      for (int kw = 0; kw < NWARPS; ++kw) {
+        va += s_part[kw * NM + rr];
+        vb += s_part[(NWARPS + kw) * NM + rr];
+      }
+      a.lf_a[(size_t)j * NM + rr] = va;
+      a.lf_b[(size_t)j * NM + rr] = vb;
+    }
+    __syncthreads();
+  }
+}
+
 template <int ENT, int PHYS, int M, bool H_SMEM, bool MIXED, bool F32F>
 __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
   constexpr int B = packed_count(M);
@@ -570,6 +662,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
   __shared__ int s_flag;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bars[3];
+  __shared__ int s_lf_ready[4];
   // shared arrays are sized for the table's N (the finest level); a cell may use fewer moments
   const int NX = a.tab.N, Q = a.tab.Q, NMX = NX * M;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -663,6 +756,8 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
             if (a.track_speed) atomic_max_pos(&a.sc->smax_bits, a.img_smax[cell]);
           }
           __syncthreads();
+          if constexpr (PHYS != PHYS_EULER2D)
+            if (a.lf_a) lf_fold<PHYS, M>(a, cell, s_Lam, s_dLam, s_P, s_lf_ready);
           continue;
         }
       }
@@ -949,6 +1044,8 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
         }
       }
     }
+    if constexpr (PHYS != PHYS_EULER2D)
+      if (a.lf_a) lf_fold<PHYS, M>(a, cell, s_Lam, s_dLam, s_P, s_lf_ready);
     __syncthreads();
   }
 

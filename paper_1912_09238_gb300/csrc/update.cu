@@ -107,6 +107,49 @@ __global__ void __launch_bounds__(UT) k_update1d(Update1DArgs a) {
   }
 }
 
+// The Lax-Friedrichs update from the terms the Newton launch folded (lf_fold in newton.cu):
+// u_hat_j = A_j - (dt/dx) B_j, with dt from the speeds of this solve; ghost copies and the steady
+// residual as in k_update1d.
+__global__ void __launch_bounds__(UT) k_lf_combine(Update1DArgs a, int NM, const double* __restrict__ lf_a,
+                                                   const double* __restrict__ lf_b) {
+  const int tid = threadIdx.x;
+  const double dt = step_dt(a);
+  if (blockIdx.x == 0 && tid == 0) a.sc->dt = dt > 0.0 ? dt : 0.0;
+  if (!(dt > 0.0)) return;
+  const double r = dt / a.dx;
+  for (int j = blockIdx.x + 1; j <= a.nx; j += gridDim.x) {
+    double* out = a.uhat + (size_t)j * NM;
+    const double old00 = out[0];                       // thread 0 reads it before it writes entry 0
+    const int g0 = (j == 1 && a.bc_left == IPM_BC_OUTFLOW) || (j == a.nx && a.bc_left == IPM_BC_PERIODIC);
+    const int g1 = (j == a.nx && a.bc_right == IPM_BC_OUTFLOW) || (j == 1 && a.bc_right == IPM_BC_PERIODIC);
+    double* out0 = a.uhat;
+    double* out1 = a.uhat + (size_t)(a.nx + 1) * NM;
+    const double* A = lf_a + (size_t)j * NM;
+    const double* B = lf_b + (size_t)j * NM;
+    for (int rr = tid; rr < NM; rr += UT) {
+      const double v = fma(-r, B[rr], A[rr]);
+      if (rr == 0 && a.cell_resid) a.cell_resid[j] = a.dx * fabs(v - old00);
+      out[rr] = v;
+      if (g0) out0[rr] = v;
+      if (g1) out1[rr] = v;
+    }
+    if (g0 || g1) {
+      const double* lj = a.lam + (size_t)j * NM;
+      for (int rr = tid; rr < NM; rr += UT) {
+        const double v = lj[rr];
+        if (g0) a.lam[rr] = v;
+        if (g1) a.lam[(size_t)(a.nx + 1) * NM + rr] = v;
+      }
+    }
+  }
+}
+
+cudaError_t launch_lf_combine(const Update1DArgs& a, int NM, const double* lf_a, const double* lf_b, int grid,
+                              cudaStream_t s) {
+  k_lf_combine<<<grid, UT, 0, s>>>(a, NM, lf_a, lf_b);
+  return cudaGetLastError();
+}
+
 static size_t update1d_smem(int m, int N, int Q) { return ((size_t)m * Q + (size_t)UWARPS * N * m) * sizeof(double); }
 
 cudaError_t prepare_update1d(int phys, int m, int N, int Q) {
