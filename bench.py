@@ -30,10 +30,10 @@ if ROOT not in sys.path:
 METRIC = "IPM cell-steps/s (mixed+batched vs FP64 GPU at equal error); p50/p99 latency"
 UNIT = "cell-steps/s"
 FP64_PEAK_TFLOPS = 1.25      # nominal dense FP64 of a GB300 (probe: 1.19 measured with FMA chains)
-KERNELS_PER_STEP = 4         # k_order, k_newton, k_update1d, k_finalize (one CUDA graph per step)
+KERNELS_PER_STEP = 4         # k_order, k_newton, k_lf_combine, k_finalize (one CUDA graph per step)
 # dram__bytes_read.sum + dram__bytes_write.sum of one mixed-path k_newton launch on this workload,
 # from an ncu capture of the current kernel (a warm step); None for the FP64 kernel (no capture yet)
-NEWTON_TRAFFIC_BYTES = {"mixed": 11.43e6, "fp64": None, "mixed_f32f": None}
+NEWTON_TRAFFIC_BYTES = {"mixed": 21.58e6, "fp64": None, "mixed_f32f": None}
 L2_FLUSH_BYTES = 512 << 20   # > 4x the 126 MiB L2
 WINDOW = dict(nx=200, x_lo=0.45, x_hi=0.55)   # same dx as the 2000-cell mesh, around the interface
 
@@ -253,8 +253,10 @@ def run_gpu(args):
                 "peak_source": "nominal GB300 dense FP64 (fallback table; no FP64 figure in the measured peaks); "
                                "an FMA-chain probe measured 1.19 TFLOP/s",
                 "traffic": NEWTON_TRAFFIC_BYTES[precision],
-                # moments and duals read, plus each cell's moment image and the duals it belongs to
-                "algorithmic_bytes_per_launch": 4 * 8 * d.n_cells * d.N * d.m,
+                # moments and duals read, each cell's moment image and the duals it belongs to; on 1-D
+                # meshes also the folded update: two neighbours' nodal states read, two terms written
+                "algorithmic_bytes_per_launch": 4 * 8 * d.n_cells * d.N * d.m
+                + 8 * d.n_interior * (2 * d.m * d.Q + 2 * d.N * d.m),
                 "newton_ms_mean": round(main["newton_ms_mean"], 4),
                 "newton_share_of_step": round(main["newton_share_of_step"], 4),
                 "algorithmic_fp64_flops_per_launch": round(main["fp64_flops_per_launch"]),
