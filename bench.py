@@ -409,7 +409,7 @@ def workloads_bench(args):
     if r:
         out["kh2d_adaptive"] = {"workload": f"2-D shear layer, 512 x 512 periodic, 3 uniform dims, adaptive total degree "
                                 f"2-6 (10-84 x 4 moments), 7^3 = 343 nodes, first {args.kh_steps} of the 200 steps "
-                                "(mixed_f32f: the FP32-factorisation mode, not the north star's precision plan)",
+                                "(mixed_f32f: the FP32-factorisation mode, a departure from the FP64 factorisation of the headline)",
                                 "unit": UNIT, **r}
     # the same with a nested Clenshaw-Curtis rule per level (default levels 2, 2, 3, 3, 3: 125 or 729 nodes)
     w = workloads.variant(workloads.KH_2D, M=6, nq=7, cc_levels=())
