@@ -220,3 +220,27 @@ def test_oneshot_and_ipm_reach_the_same_steady_state():
         # the residual watches only the zero-order moment; higher moments trail it by ~1e-10
         np.testing.assert_allclose(st.uhat[1:-1], np.broadcast_to(target, st.uhat[1:-1].shape), rtol=0, atol=1e-9)
     np.testing.assert_allclose(results["ipm"], results["oneshot"], rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("which", ["burgers", "sod"])
+def test_global_lf_update_is_the_centred_average(which):
+    """With the global viscosity dx/(2 dt) of App. A the cell's own state cancels from the update:
+    u_j - dt/dx (g_{j+1/2} - g_{j-1/2}) = (u_{j-1} + u_{j+1})/2 - dt/(2 dx) (f(u_{j+1}) - f(u_{j-1})),
+    the classical Lax-Friedrichs scheme (the form the GPU path folds into its Newton launch)."""
+    rng = np.random.default_rng(7)
+    prob = burgers_problem(nx=9) if which == "burgers" else sod_problem(nx=9)
+    Q = prob.space.Q
+    if which == "burgers":
+        U = rng.uniform(1.0, 12.0, size=(11, Q, 1))
+    else:
+        rho, v, p = rng.uniform(0.2, 2.0, (11, Q)), rng.uniform(-1.0, 1.0, (11, Q)), rng.uniform(0.1, 2.0, (11, Q))
+        U = np.stack([rho, rho * v, p / 0.4 + 0.5 * rho * v * v], axis=-1)
+    dt = 0.37 * prob.dx
+    got = s1.nodal_update(prob, U, dt)
+    f = prob.phys.flux
+    want = 0.5 * (U[:-2] + U[2:]) - dt / (2.0 * prob.dx) * (f(U[2:]) - f(U[:-2]))
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+    # and the centre state does not enter: changing it leaves the update unchanged up to rounding
+    U2 = U.copy()
+    U2[5] *= 1.5
+    assert np.max(np.abs(s1.nodal_update(prob, U2, dt)[4] - got[4])) <= 1e-13 * np.max(np.abs(want))
