@@ -81,3 +81,25 @@ def test_library_clenshaw_curtis_tables_match_oracle(libipm, p, M, kmax):
         assert np.all(lw[k, ow[k].size:] == 0.0)
     sp = ob.NestedCCSpace(p, M, kmax)
     assert np.array_equal(idx, sp.indices) and np.abs(phi - sp.Phi).max() < 1e-13
+
+
+def test_option_defaults_and_validation_without_a_gpu(libipm):
+    """ipm_default_options through the ctypes mirror of ipm_options (a layout mismatch would show as
+    wrong defaults), and option checks that refuse a plan before any device work."""
+    import ctypes
+    from paper_1912_09238_gb300 import ipm, workloads
+    from tests._cases import gpu_problem, gpu_quadrature
+    o = ipm.default_options("mixed")
+    assert (o.precision, o.max_newton, o.max_halvings, o.hessian_reuse, o.newton_kernel, o.check_cache) == (
+        ipm.PRECISION["mixed"], 100, 30, 0, 0, 1)
+    assert o.newton_tol == 1e-10 and o.reuse_ratio == 0.5
+    w = workloads.SOD_1D
+    pr, quad = gpu_problem(w), gpu_quadrature(w)
+    basis = ipm.ipm_basis(w["p"], w["M"])
+    ent = ipm.ipm_entropy(ipm.ENTROPY[w["entropy"]], 0.0, 0.0)
+    b = ctypes.c_size_t()
+    for bad in (dict(check_cache=2), dict(newton_kernel=3), dict(hessian_reuse=3)):
+        ob = ipm.default_options("fp64", **bad)
+        st = libipm.ipm_footprint(ctypes.byref(pr), ctypes.byref(basis), ctypes.byref(quad), ctypes.byref(ent),
+                                  ctypes.byref(ob), ctypes.byref(b))
+        assert st == 1, (bad, st)
