@@ -153,14 +153,14 @@ def aggregate_throughput(local_seconds, units_per_rank, ws, device):
 
 
 # ------------------------------------------------------------------------------------------------
-def measure(args, precision, flush, stream, barrier, ws):
+def measure(args, precision, flush, stream, barrier, ws, **opt):
     """W warm-up + K timed Algorithm-1 steps of one precision; returns (summary dict, context)."""
     import numpy as np
     import torch
     from tests._cases import gpu_context
 
     w = workload()
-    ctx = gpu_context(w, precision=precision)
+    ctx = gpu_context(w, precision=precision, **opt)
     ctx.set_stream(stream.cuda_stream)
     d = ctx.dims
     for _ in range(args.warmup):
@@ -244,6 +244,11 @@ def run_gpu(args):
         f32["max_rel_diff_moments_vs_fp64"] = float(np.max(np.abs(c - b)) / np.max(np.abs(b)))
         f32["fp32_fallbacks"] = fctx.sync_stats().fp32_fallbacks
         fctx.close()
+        # the headline path evaluating every convergence check (no moment images): same steps, and
+        # the moments must come out bit for bit the same
+        plain, pctx = measure(args, precision, flush, stream, barrier, ws, check_cache=0)
+        plain["bit_identical_moments"] = bool(np.array_equal(pctx.get_moments(), a))
+        pctx.close()
         rctx.close()
 
     roofline = {"bound": "alu", "kernel": "k_newton (fused dual solve: reconstruction, closure, gradient, "
@@ -293,6 +298,11 @@ def run_gpu(args):
             "config": workload_desc(w, precision), "roofline": roofline, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": main["clocks"]}
     if ref is not None:
+        line["without_moment_images"] = {
+            "value": plain["value"], "unit": UNIT, "ms_per_step": plain["ms_per_step"],
+            "newton_ms_mean": plain["newton_ms_mean"], "bit_identical_moments": plain["bit_identical_moments"],
+            "what": "the headline path with ipm_options.check_cache = 0: every cell evaluates its first "
+                    "convergence check instead of taking it from the moment image of its unchanged duals"}
         line["fp64_gpu"] = {"value": ref["value"], "unit": UNIT, "ms_per_step": ref["ms_per_step"],
                             "newton_ms_mean": ref["newton_ms_mean"],
                             "newton_iters_per_step": ref["newton_iters_per_step"],
