@@ -320,9 +320,8 @@ static cudaError_t enqueue_newton(ipm_ctx* c, int one_step, cudaStream_t s, bool
 
 // one step of Algorithm 1 (one_step = 0) or Algorithm 2 (one_step = 1)
 static cudaError_t enqueue_step(ipm_ctx* c, int one_step, cudaStream_t s) {
-  // 1-D meshes on the CTA-per-cell kernel: the Newton launch folds in the Lax-Friedrichs terms and a
-  // small kernel applies dt
-  const bool lf = !c->is2d && c->newton_kind == 0 && c->d_lf_a != nullptr;
+  // 1-D meshes: the Newton launch folds in the Lax-Friedrichs terms and a small kernel applies dt
+  const bool lf = !c->is2d && c->d_lf_a != nullptr;
   cudaError_t e = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal);
   if (e == cudaSuccess) e = enqueue_newton(c, one_step, s, lf);
   if (e == cudaSuccess) e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal);

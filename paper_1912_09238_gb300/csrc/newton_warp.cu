@@ -35,6 +35,81 @@ __host__ __device__ inline size_t warp_slice_doubles(int N, int m, int Q) {
   return 5 * NM + 4 * (size_t)m * Q + B * Q + (NM + 1) * (NM + 2) / 2;
 }
 
+// The 1-D Lax-Friedrichs update folded into the launch, one warp (as lf_fold in newton.cu): once the
+// nodal states of cell k are final, count k towards each cell it neighbours; for each count this warp
+// completes, form that cell's A = P(w (u_l + u_r)/2) and B = P(w (f(u_r) - f(u_l))/2), lanes over the
+// nodes for the integrands and over the entries for the projections. Scratch s_ia, s_ib [M][Q].
+template <int PHYS, int M>
+__device__ void lf_fold_warp(const NewtonArgs& a, int k, double* s_ia, double* s_ib) {
+  const int lane = threadIdx.x & 31;
+  const int nx = a.nx, Q = a.tab.Q, N = a.tab.N, NM = N * M;
+  __threadfence();                                   // this warp's nodal states of k, before the counts
+  __syncwarp();
+  int n = 0, r0 = 0, r1 = 0, r2 = 0;
+  if (lane == 0) {
+    const int cand[5] = {k - 1, k + 1, k, 1, nx};
+    for (int ci = 0; ci < 5; ++ci) {
+      const int j = cand[ci];
+      bool seen = j < 1 || j > nx;
+      for (int cj = 0; cj < ci; ++cj) seen = seen || cand[cj] == j;
+      if (seen) continue;
+      const int jl = neighbour(j, nx, -1, a.bc_left), jr = neighbour(j, nx, +1, a.bc_right);
+      const bool il = jl >= 1 && jl <= nx, ir = jr >= 1 && jr <= nx && jr != jl;
+      const int target = (il ? 1 : 0) + (ir ? 1 : 0);
+      bool ready = false;
+      if (target == 0) ready = j == k;
+      else if (jl == k || jr == k) ready = atomicAdd(&a.lf_cnt[j], 1) == target - 1;
+      if (ready) {
+        if (n == 0) r0 = j;
+        else if (n == 1) r1 = j;
+        else r2 = j;
+        ++n;
+      }
+    }
+    __threadfence();                                 // the other warps' nodal states, after the counts
+  }
+  n = __shfl_sync(0xffffffffu, n, 0);
+  r0 = __shfl_sync(0xffffffffu, r0, 0);
+  r1 = __shfl_sync(0xffffffffu, r1, 0);
+  r2 = __shfl_sync(0xffffffffu, r2, 0);
+  const double* __restrict__ w = a.tab.w;
+  const double* __restrict__ Phi = a.tab.Phi;
+  for (int t = 0; t < n; ++t) {
+    const int j = t == 0 ? r0 : (t == 1 ? r1 : r2);
+    const double* ul_g = a.unode + (size_t)neighbour(j, nx, -1, a.bc_left) * M * Q;
+    const double* ur_g = a.unode + (size_t)neighbour(j, nx, +1, a.bc_right) * M * Q;
+    for (int q = lane; q < Q; q += 32) {
+      double ul[M], ur[M], fl[M], fr[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        ul[c] = ul_g[c * Q + q];
+        ur[c] = ur_g[c * Q + q];
+      }
+      Flux1D<PHYS, M>::f(ul, a.ent.gamma, fl);
+      Flux1D<PHYS, M>::f(ur, a.ent.gamma, fr);
+      const double wq = w[q];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        s_ia[c * Q + q] = wq * (0.5 * (ul[c] + ur[c]));
+        s_ib[c * Q + q] = wq * (0.5 * (fr[c] - fl[c]));
+      }
+    }
+    __syncwarp();
+    for (int rr = lane; rr < NM; rr += 32) {
+      const int i = rr / M, c = rr - i * M;
+      double sa = 0.0, sb = 0.0;
+      for (int q = 0; q < Q; ++q) {
+        const double ph = Phi[(size_t)q * N + i];
+        sa = fma(ph, s_ia[c * Q + q], sa);
+        sb = fma(ph, s_ib[c * Q + q], sb);
+      }
+      a.lf_a[(size_t)j * NM + rr] = sa;
+      a.lf_b[(size_t)j * NM + rr] = sb;
+    }
+    __syncwarp();
+  }
+}
+
 template <int ENT, int PHYS, int M, bool MIXED>
 __global__ void __launch_bounds__(256) k_newton_warp(NewtonArgs a, int slice) {
   constexpr int B = packed_count(M);
@@ -280,6 +355,8 @@ __global__ void __launch_bounds__(256) k_newton_warp(NewtonArgs a, int slice) {
       if (lane == 0) atomic_max_pos(&a.sc->smax_bits, smax);
     }
     __syncwarp();
+    if constexpr (PHYS != PHYS_EULER2D)
+      if (a.lf_a) lf_fold_warp<PHYS, M>(a, cell, s_Lam, s_dLam);
   }
 }
 
