@@ -1,18 +1,20 @@
 #!/usr/bin/env python
-"""IPM benchmark: cell-steps/s of Algorithm 1 (IPM time step) on the 1-D Euler Sod workload
+"""IPM benchmark: cell-steps/s of Algorithm 1 (IPM time steps) on the 1-D Euler Sod workload
 (2000 cells, 3 uncertain dims, total degree 5 -> N = 56 moments x 3 variables, 6^3 = 216 Gauss nodes).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--full]
 
-One step = one call of ipm_step: the Newton solve of the dual problem in every cell, the CFL time
-step, the kinetic-flux moment update (one captured CUDA graph). The headline is the mixed-precision
-path (Hessian on the tensor cores, everything else FP64); the plain FP64 GPU path is timed on the
-same workload in the same run and reported beside it (--precision fp64 makes FP64 the headline),
-and so is the FP32-factorisation mode (key "mixed_f32_factor").
-Prints one JSON line (rank 0).
+One bench step = one complete Algorithm-1 run of the workload from its initial data at t = 0 to
+t_end = 0.14 (1344 time steps; each time step is the Newton solve of the dual problem in every cell,
+the CFL time step and the kinetic-flux moment update, one captured CUDA graph), through ipm_run. The
+headline is the mixed-precision path (Hessian on the tensor cores, everything else FP64); the plain FP64
+GPU path and the FP32-factorisation mode run the same full run in the same process and are reported
+beside it, with the difference of their final moments. Prints one JSON line (rank 0).
 --impl reference times the CPU oracle on the host cores instead (each step a bounded sample).
 With torchrun (N > 1) every rank runs an independent replica of the workload on its own GPU
 (the method needs no data exchange between replicas), value = all cells updated / max time.
+--full adds the long forms of the other workloads (shear layer to 200 steps, the 10,000-request
+serving stream at three arrival rates, the ramp on the FP64 path to its residual).
 """
 import argparse
 import json
@@ -29,13 +31,13 @@ if ROOT not in sys.path:
 
 METRIC = "IPM cell-steps/s (mixed+batched vs FP64 GPU at equal error); p50/p99 latency"
 UNIT = "cell-steps/s"
-FP64_PEAK_TFLOPS = 1.25      # nominal dense FP64 of a GB300 (probe: 1.19 measured with FMA chains)
-KERNELS_PER_STEP = 4         # k_order, k_newton, k_lf_combine, k_finalize (one CUDA graph per step)
+KERNELS_PER_TIME_STEP = 4    # k_order, k_newton, k_lf_combine, k_finalize (one CUDA graph per time step)
 # dram__bytes_read.sum + dram__bytes_write.sum of one mixed-path k_newton launch on this workload,
-# from an ncu capture of the current kernel (a warm step); None for the FP64 kernel (no capture yet)
-NEWTON_TRAFFIC_BYTES = {"mixed": 21.58e6, "fp64": None, "mixed_f32f": None}
+# from an ncu capture of the current kernel; None when no capture of the current kernel exists
+NEWTON_TRAFFIC_BYTES = {"mixed": None, "fp64": None, "mixed_f32f": None}
 L2_FLUSH_BYTES = 512 << 20   # > 4x the 126 MiB L2
-WINDOW = dict(nx=200, x_lo=0.45, x_hi=0.55)   # same dx as the 2000-cell mesh, around the interface
+FP64_PROBE_N = 6144          # cuBLAS DGEMM size of the FP64 ceiling measurement
+CPU_SAMPLE_STEPS = 20        # Algorithm-1 steps of the oracle in the cpu_baseline sample
 
 
 def workload():
@@ -48,9 +50,11 @@ def workload_desc(w, precision):
         "workload": (f"{w['name']}: 1-D Euler Sod tube IPM, {w['nx']} cells on [0,1], gamma 1.4, 3 uniform "
                      f"uncertain dims (rho_L, p_L, interface), total degree {w['M']} Legendre (N=56 x 3 vars), "
                      f"tensor Gauss {w['nq']}^3=216 nodes, Euler entropy (App. B), global LF kinetic flux, "
-                     f"CFL {w['cfl']}, Newton tol {w['newton_tol']}; Algorithm 1 time steps from t=0"),
+                     f"CFL {w['cfl']}, Newton tol {w['newton_tol']}; one bench step = Algorithm 1 from t=0 to "
+                     f"t_end={w['t_end']} (every time step of the run)"),
         "precision": precision,
-        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write on the same stream, excluded from step times)",
+        "l2": f"flushed between timed runs ({L2_FLUSH_BYTES >> 20} MiB write on the same stream, outside the "
+              "timed region); within a run the 9.7 MB state stays resident",
         "inputs": "initial data projected on the device; state resident in HBM",
     }
 
@@ -128,15 +132,15 @@ def newton_fp64_flops(N, m, Q, cells, iters, with_hessian, cached=0):
     return (cells - cached + iters) * grad_eval + cached * 3.0 * N * m + iters * per_update
 
 
-def hessian_tc_flops(N, m, Q, iters):
-    """Tensor-core flops of the mixed Hessian per launch: per update, row tiles of 128 over the B*N rows,
-    n_pad = N rounded up to 16 columns, Q rounded up to the K-chunk, three BF16 products each."""
+def hessian_tc_flops(N, m, Q):
+    """Tensor-core flops of one mixed Hessian assembly: row tiles of 128 over the B*N rows, n_pad = N
+    rounded up to 16 columns, Q rounded up to the K-chunk, three BF16 products each."""
     B = m * (m + 1) // 2
     tiles = -(-B * N // 128)
     n_pad = -(-N // 16) * 16
     kc = 32 if Q > 16 else 16
     q_pad = -(-Q // kc) * kc
-    return iters * 3 * 2.0 * tiles * 128 * n_pad * q_pad
+    return 3 * 2.0 * tiles * 128 * n_pad * q_pad
 
 
 def aggregate_throughput(local_seconds, units_per_rank, ws, device):
@@ -152,55 +156,124 @@ def aggregate_throughput(local_seconds, units_per_rank, ws, device):
     return ws * units_per_rank / secs, secs
 
 
-# ------------------------------------------------------------------------------------------------
-def measure(args, precision, flush, stream, barrier, ws, **opt):
-    """W warm-up + K timed Algorithm-1 steps of one precision; returns (summary dict, context)."""
-    import numpy as np
+def fp64_ceiling():
+    """FP64 ceiling of this GPU measured here: cuBLAS DGEMM (torch.matmul on float64) of FP64_PROBE_N^3,
+    best of 5 after one warm-up, CUDA events. The measured peaks file carries no FP64 figure."""
     import torch
-    from tests._cases import gpu_context
+    n = FP64_PROBE_N
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    best = float("inf")
+    s = torch.cuda.current_stream()
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        torch.matmul(a, b)
+        e1.record(s)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    torch.cuda.empty_cache()
+    return {"tflops": 2.0 * n ** 3 / best / 1e12,
+            "source": f"measured in this run: cuBLAS DGEMM (torch.matmul, float64) {n}^3, best of 5, CUDA events"}
 
-    w = workload()
-    ctx = gpu_context(w, precision=precision, **opt)
-    ctx.set_stream(stream.cuda_stream)
-    d = ctx.dims
-    for _ in range(args.warmup):
-        flush.zero_()
-        ctx.step(sync=False)
-    barrier()
-    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
-    clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    newton_ms, iters, cached = [], [], []
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        ctx.step(sync=False)
-        ev[k][1].record(stream)
-        nm, _, _ = ctx.step_timing()               # waits for this step; outside the event pair
-        s = ctx.sync_stats()
-        newton_ms.append(nm)
-        iters.append(s.newton_iters)
-        cached.append(s.cached_checks)
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------------------------------------
+class SodRuns:
+    """Complete Algorithm-1 runs of one workload in one precision on one resident context: the initial
+    state is kept in pinned host buffers and restored (moments, duals, clock t = 0) before every run."""
+
+    def __init__(self, w, precision, stream, **opt):
+        import torch
+        from paper_1912_09238_gb300 import ipm, workloads
+        self.w = w
+        self.ctx = workloads.context(w, precision=precision, **opt)
+        self.ctx.set_stream(stream.cuda_stream)
+        self.stream = stream
+        shape = self.ctx.shape
+        self.u0 = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        self.l0 = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        self.ctx.get_state(self.u0, self.l0)
+        self.clock0 = ipm.ipm_clock(t=0.0, dt=0.0, steps=0, level_cap=0)
+        self.cells = self.ctx.dims.n_interior
+
+    def reset(self):
+        self.ctx.set_state(self.u0, self.l0, clock=self.clock0)
+
+    def timed_run(self, flush=None):
+        """One run from t = 0 to t_end through ipm_run, CUDA-event timed on the context's stream;
+        returns (seconds, time steps, last stats)."""
+        import torch
+        self.reset()
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(self.stream)
+        s = self.ctx.run()
+        b.record(self.stream)
+        b.synchronize()
         if s.failed_cells or s.tc_timeouts:
             raise RuntimeError(f"dual solve failed in {s.failed_cells} cells: {s.as_dict()}")
-    barrier()
-    cl = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    cells = d.n_interior
-    value, _ = aggregate_throughput(sum(step_ms) / 1e3, cells * args.steps, ws, "cuda")
-    flops = [newton_fp64_flops(d.N, d.m, d.Q, cells, it, precision == "fp64", ch) for it, ch in zip(iters, cached)]
-    newton_s = statistics.mean(newton_ms) / 1e3
-    out = {"value": value, "ms_per_step": statistics.mean(step_ms),
-           "p50_step_ms": statistics.median(step_ms), "p99_step_ms": float(np.percentile(step_ms, 99)),
-           "newton_ms_mean": statistics.mean(newton_ms), "newton_share_of_step": sum(newton_ms) / sum(step_ms),
-           "fp64_flops_per_launch": sum(flops) / len(flops),
-           "fp64_tflops": (sum(flops) / len(flops)) / newton_s / 1e12,
-           "newton_iters_per_step": statistics.mean(iters), "cached_checks_per_step": statistics.mean(cached),
-           "clocks": cl, "cells": cells, "dims": d}
-    if precision != "fp64":
-        tcf = statistics.mean(hessian_tc_flops(d.N, d.m, d.Q, it) for it in iters)
-        out["tensor_flops_per_launch"] = tcf
-    return out, ctx
+        if s.t < self.w["t_end"] * (1 - 1e-12):
+            raise RuntimeError(f"run stopped at t = {s.t}")
+        return a.elapsed_time(b) / 1e3, int(s.steps), s
+
+    def profile_run(self, with_hessian_flops):
+        """One run step by step with the events inside each step's graph: per-step Newton-kernel and step
+        times, Newton updates, cached checks, tensor-core Hessian phase times."""
+        self.reset()
+        d = self.ctx.dims
+        rows = []
+        while True:
+            s = self.ctx.step()
+            nm, _, tm = self.ctx.step_timing()
+            if s.failed_cells or s.tc_timeouts:
+                raise RuntimeError(f"dual solve failed: {s.as_dict()}")
+            rows.append({"t": s.t, "newton_ms": nm, "step_ms": tm, "iters": s.newton_iters, "max_iters": s.max_iters,
+                         "cached": s.cached_checks, "hessian_ns": s.hessian_ns, "hessian_count": s.hessian_count,
+                         "flops": newton_fp64_flops(d.N, d.m, d.Q, self.cells, s.newton_iters, with_hessian_flops,
+                                                    s.cached_checks)})
+            if s.t >= self.w["t_end"] * (1 - 1e-12):
+                return rows
+
+    def close(self):
+        self.ctx.close()
+
+
+def tenths(rows):
+    """Per tenth of a run's time steps: the time reached, ms per time step, Newton ms, updates and cached
+    convergence checks per time step."""
+    n = len(rows)
+    out = []
+    for k in range(10):
+        sl = rows[k * n // 10:(k + 1) * n // 10]
+        if not sl:
+            continue
+        out.append({"t": round(sl[-1]["t"], 5), "ms_per_time_step": round(statistics.mean(r["step_ms"] for r in sl), 4),
+                    "newton_ms": round(statistics.mean(r["newton_ms"] for r in sl), 4),
+                    "newton_updates": round(statistics.mean(r["iters"] for r in sl), 1),
+                    "max_updates_per_cell": max(r["max_iters"] for r in sl),
+                    "cached_checks": round(statistics.mean(r["cached"] for r in sl), 1)})
+    return out
+
+
+def window(rows, first, last, cells):
+    sl = rows[first - 1:last]
+    return {"time_steps": f"{first}..{last}", "value": cells * len(sl) / (sum(r["step_ms"] for r in sl) / 1e3),
+            "unit": UNIT, "ms_per_time_step": statistics.mean(r["step_ms"] for r in sl)}
+
+
+def rel_diff(a, b):
+    import numpy as np
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
 def run_gpu(args):
@@ -218,8 +291,9 @@ def run_gpu(args):
     w = workload()
     stream = torch.cuda.Stream()                    # a real (non-default) stream shared by torch and libipm
     torch.cuda.set_stream(stream)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     assert torch.cuda.current_stream().cuda_stream == stream.cuda_stream != 0
+    fp64 = fp64_ceiling()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
         torch.cuda.synchronize()
@@ -228,123 +302,172 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     precision = args.precision
-    main, ctx = measure(args, precision, flush, stream, barrier, ws)
-    d = main["dims"]
-    cells = main["cells"]
-    # the plain FP64 GPU path on the same workload and steps (the comparison the metric names)
-    ref = None
-    if precision == "mixed" and not args.no_fp64_compare:
-        ref, rctx = measure(args, "fp64", flush, stream, barrier, ws)
-        # equal error: both paths ran the same steps from the same initial data
-        a, b = ctx.get_moments(), rctx.get_moments()
-        ref["max_rel_diff_moments_vs_mixed"] = float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
-        # the FP32-factorisation mode on the same steps, against the FP64 path's moments
-        f32, fctx = measure(args, "mixed_f32f", flush, stream, barrier, ws)
-        c = fctx.get_moments()
-        f32["max_rel_diff_moments_vs_fp64"] = float(np.max(np.abs(c - b)) / np.max(np.abs(b)))
-        f32["fp32_fallbacks"] = fctx.sync_stats().fp32_fallbacks
-        fctx.close()
-        # the headline path evaluating every convergence check (no moment images): same steps, and
-        # the moments must come out bit for bit the same
-        plain, pctx = measure(args, precision, flush, stream, barrier, ws, check_cache=0)
-        plain["bit_identical_moments"] = bool(np.array_equal(pctx.get_moments(), a))
-        pctx.close()
-        rctx.close()
+    # ---- headline: W warm-up runs, K timed runs, every run from t = 0 to t_end
+    runs = SodRuns(w, precision, stream)
+    for _ in range(args.warmup):
+        runs.timed_run(flush)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    secs, steps_per_run, finals = [], [], []
+    for _ in range(args.steps):
+        sec, n, _ = runs.timed_run(flush)
+        secs.append(sec)
+        steps_per_run.append(n)
+        finals.append(runs.ctx.get_moments())          # outside the event pair
+    barrier()
+    cl = clocks.stop()
+    cells = runs.cells
+    cell_steps = cells * sum(steps_per_run)
+    value, _ = aggregate_throughput(sum(secs), cell_steps, ws, "cuda")
+    head_final = finals[-1]
+    runs_identical = all(np.array_equal(f, head_final) for f in finals)
 
+    # ---- the same run step by step: per-tenth table, first-steps window, Newton-kernel roofline
+    prof = runs.profile_run(precision == "fp64")
+    newton_s = sum(r["newton_ms"] for r in prof) / 1e3
+    flops = sum(r["flops"] for r in prof)
+    achieved = flops / newton_s / 1e12
+    d = runs.ctx.dims
     roofline = {"bound": "alu", "kernel": "k_newton (fused dual solve: reconstruction, closure, gradient, "
-                "Hessian" + (" on tcgen05 tensor cores" if precision == "mixed" else "") +
-                ", Cholesky, solves, Armijo)", "achieved": round(main["fp64_tflops"], 4), "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(main["fp64_tflops"] / FP64_PEAK_TFLOPS, 4),
-                "peak_source": "nominal GB300 dense FP64 (fallback table; no FP64 figure in the measured peaks); "
-                               "an FMA-chain probe measured 1.19 TFLOP/s",
-                "traffic": NEWTON_TRAFFIC_BYTES[precision],
-                # moments and duals read, each cell's moment image and the duals it belongs to; on 1-D
-                # meshes also the folded update: two neighbours' nodal states read, two terms written
+                "Hessian" + (" on tcgen05 tensor cores" if precision != "fp64" else "") +
+                ", Cholesky, solves, Armijo, folded update terms)",
+                "achieved": round(achieved, 4), "peak": round(fp64["tflops"], 4), "unit": "TFLOP/s",
+                "frac": round(achieved / fp64["tflops"], 4), "peak_source": fp64["source"],
+                "traffic": NEWTON_TRAFFIC_BYTES.get(precision),
+                "measured_over": f"all {len(prof)} time steps of one full run, CUDA events around every Newton "
+                                 "launch inside the step graphs",
+                # moments and duals read, each cell's moment image and the duals it belongs to; the folded
+                # update: two neighbours' nodal states read, two terms written
                 "algorithmic_bytes_per_launch": 4 * 8 * d.n_cells * d.N * d.m
                 + 8 * d.n_interior * (2 * d.m * d.Q + 2 * d.N * d.m),
-                "newton_ms_mean": round(main["newton_ms_mean"], 4),
-                "newton_share_of_step": round(main["newton_share_of_step"], 4),
-                "algorithmic_fp64_flops_per_launch": round(main["fp64_flops_per_launch"]),
-                "newton_iters_per_step": round(main["newton_iters_per_step"], 1),
-                "cached_checks_per_step": round(main["cached_checks_per_step"], 1)}
-    if precision == "mixed":
-        roofline["tensor_bf16_flops_per_launch"] = round(main["tensor_flops_per_launch"])
+                "algorithmic_fp64_flops_per_launch": round(flops / len(prof)),
+                "newton_ms_mean": round(1e3 * newton_s / len(prof), 4),
+                "newton_share_of_step": round(newton_s * 1e3 / sum(r["step_ms"] for r in prof), 4),
+                "newton_updates_per_time_step": round(statistics.mean(r["iters"] for r in prof), 1),
+                "cached_checks_per_time_step": round(statistics.mean(r["cached"] for r in prof), 1)}
+    roofline_b = None
+    hc = sum(r["hessian_count"] for r in prof)
+    if precision != "fp64" and hc:
+        hns = sum(r["hessian_ns"] for r in prof)
+        per = hessian_tc_flops(d.N, d.m, d.Q)
+        bf16 = measured_peaks().get("bf16_tflops_sustained")
+        ach = per * hc / (hns / 1e9) / 1e12
+        roofline_b = {"bound": "tensor", "kernel": "k_newton, row (b): split-BF16 Hessian on tcgen05, per SM",
+                      "achieved_per_sm": round(ach, 5), "unit": "TFLOP/s",
+                      "assemblies": hc, "phase_us_mean": round(hns / hc / 1e3, 3),
+                      "tensor_flops_per_assembly": per}
+        if bf16:
+            per_sm_peak = bf16 / 152.0
+            roofline_b.update({"peak_per_sm": round(per_sm_peak, 4), "frac": round(ach / per_sm_peak, 4),
+                               "peak_source": "bf16_tflops_sustained of the measured peaks / 152 SMs (one CTA, "
+                                              "one SM per assembly)"})
 
-    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
-    shape = ctx.shape
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if precision == "fp64" else "f64+bf16", "data": "synthetic",
+            "config": workload_desc(w, precision), "roofline": roofline,
+            "run": {"time_steps_per_run": steps_per_run[0], "ms_per_time_step": 1e3 * sum(secs) / sum(steps_per_run),
+                    "p50_run_ms": 1e3 * statistics.median(secs), "max_run_ms": 1e3 * max(secs),
+                    "runs_bit_identical": runs_identical,
+                    "per_tenth_of_run": tenths(prof),
+                    "first_time_steps": window(prof, 1, CPU_SAMPLE_STEPS, cells),
+                    "steps_6_to_25": window(prof, 6, 25, cells)},
+            "gpu_launches": KERNELS_PER_TIME_STEP * sum(steps_per_run), "clocks": cl}
+    if roofline_b:
+        line["roofline_hessian"] = roofline_b
+
+    # ---- the other precision modes on the same full run
+    if precision == "mixed" and not args.no_fp64_compare:
+        comp = {}
+        for name, prec, opt in (("fp64_gpu", "fp64", {}), ("mixed_f32_factor", "mixed_f32f", {}),
+                                ("without_moment_images", "mixed", {"check_cache": 0})):
+            r = SodRuns(w, prec, stream, **opt)
+            r.ctx.run(20)                                   # warm-up: first time steps, then restored
+            sec_c = []
+            for _ in range(args.compare_runs):
+                sc_, n_c, _ = r.timed_run(flush)
+                sec_c.append(sc_)
+            fin = r.ctx.get_moments()
+            entry = {"value": cells * n_c * len(sec_c) / sum(sec_c), "unit": UNIT,
+                     "ms_per_run": 1e3 * statistics.mean(sec_c), "runs": len(sec_c), "time_steps_per_run": n_c}
+            if prec == "fp64":
+                rows = r.profile_run(True)
+                entry["per_tenth_of_run"] = tenths(rows)
+                entry["first_time_steps"] = window(rows, 1, CPU_SAMPLE_STEPS, cells)
+                nf = sum(x["flops"] for x in rows)
+                ns_ = sum(x["newton_ms"] for x in rows) / 1e3
+                entry["fp64_tflops"] = round(nf / ns_ / 1e12, 4)
+                entry["frac_of_fp64_ceiling"] = round(nf / ns_ / 1e12 / fp64["tflops"], 4)
+                fp64_final = fin
+            comp[name] = (entry, fin)
+            r.close()
+        fp64_entry, fp64_final = comp["fp64_gpu"]
+        fp64_entry["max_rel_diff_final_moments_mixed_vs_fp64"] = rel_diff(head_final, fp64_final)
+        fp64_entry["speedup_mixed_over_fp64"] = value / fp64_entry["value"]
+        line["fp64_gpu"] = fp64_entry
+        e, fin = comp["mixed_f32_factor"]
+        e["max_rel_diff_final_moments_vs_fp64"] = rel_diff(fin, fp64_final)
+        e["speedup_over_fp64"] = e["value"] / fp64_entry["value"]
+        e["what"] = ("precision mixed_f32f: tensor-core Hessian as in the headline, Cholesky factorisation and "
+                     "triangular solves in FP32 (FP64 refactorisation on a non-positive FP32 pivot); gradient, "
+                     "stopping test, line search and update in FP64. Not the headline: the headline keeps the "
+                     "factorisation in FP64.")
+        line["mixed_f32_factor"] = e
+        e, fin = comp["without_moment_images"]
+        e["bit_identical_final_moments"] = bool(np.array_equal(fin, head_final))
+        e["what"] = ("the headline path with ipm_options.check_cache = 0: every cell evaluates its first "
+                     "convergence check instead of taking it from the moment image of its unchanged duals")
+        line["without_moment_images"] = e
+
+    # ---- end to end through the C ABI: pinned host state in, full run, pinned host state out
+    shape = runs.ctx.shape
     hu = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
     hl = torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
-    hu[...] = ctx.get_moments()
-    hl[...] = ctx.get_duals()
-    e2e_steps = args.steps
+    e2e_runs = args.e2e_runs
     barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.set_state(hu, hl)
-        ctx.step(sync=False)
-        ctx.get_state(hu, hl)                   # straight into the pinned buffers
+    e2e_steps = 0
+    for _ in range(e2e_runs):
+        runs.ctx.set_state(runs.u0, runs.l0, clock=runs.clock0)     # the run's inputs, pinned host -> device
+        s = runs.ctx.run()
+        runs.ctx.get_state(hu, hl)                                  # the run's result, device -> pinned host
+        e2e_steps += int(s.steps)
     barrier()
     e2e_value, _ = aggregate_throughput(time.perf_counter() - t0, cells * e2e_steps, ws, "cuda")
     nbytes = int(np.prod(shape)) * 8
-    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
-           "d2h_bytes_per_step": 2 * nbytes, "api": "ipm_set_state + ipm_step + ipm_get_state (moments and "
-           "duals, pinned host buffers)"}
+    line["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes, "d2h_bytes_per_step": 2 * nbytes,
+                   "runs": e2e_runs, "final_moments_equal_headline": bool(np.array_equal(hu, head_final)),
+                   "api": "ipm_set_state (initial moments and duals from pinned host buffers, clock t = 0) + "
+                          "ipm_run (to t_end) + ipm_get_state (final moments and duals into pinned host buffers); "
+                          "wall clock"}
+    runs.close()
 
-    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
-            "p50_step_ms": main["p50_step_ms"], "p99_step_ms": main["p99_step_ms"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if precision == "fp64" else "f64+bf16", "data": "synthetic",
-            "config": workload_desc(w, precision), "roofline": roofline, "e2e": e2e,
-            "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": main["clocks"]}
-    if ref is not None:
-        line["without_moment_images"] = {
-            "value": plain["value"], "unit": UNIT, "ms_per_step": plain["ms_per_step"],
-            "newton_ms_mean": plain["newton_ms_mean"], "bit_identical_moments": plain["bit_identical_moments"],
-            "what": "the headline path with ipm_options.check_cache = 0: every cell evaluates its first "
-                    "convergence check instead of taking it from the moment image of its unchanged duals"}
-        line["fp64_gpu"] = {"value": ref["value"], "unit": UNIT, "ms_per_step": ref["ms_per_step"],
-                            "newton_ms_mean": ref["newton_ms_mean"],
-                            "newton_iters_per_step": ref["newton_iters_per_step"],
-                            "fp64_tflops": round(ref["fp64_tflops"], 4),
-                            "max_rel_diff_moments_vs_mixed": ref["max_rel_diff_moments_vs_mixed"],
-                            "speedup_mixed_over_fp64": main["value"] / ref["value"]}
-        line["mixed_f32_factor"] = {
-            "value": f32["value"], "unit": UNIT, "ms_per_step": f32["ms_per_step"],
-            "p50_step_ms": f32["p50_step_ms"], "p99_step_ms": f32["p99_step_ms"],
-            "newton_ms_mean": f32["newton_ms_mean"], "newton_iters_per_step": f32["newton_iters_per_step"],
-            "max_rel_diff_moments_vs_fp64": f32["max_rel_diff_moments_vs_fp64"],
-            "fp32_fallbacks": f32["fp32_fallbacks"], "speedup_over_fp64": f32["value"] / ref["value"],
-            "what": "precision mixed_f32f: tensor-core Hessian as in the headline, Cholesky factorisation and "
-                    "triangular solves in FP32 (FP64 refactorisation on a non-positive FP32 pivot); gradient, "
-                    "stopping test, line search and update in FP64. Not the headline: the headline keeps the "
-                    "factorisation in FP64."}
+    if rank == 0 and not args.no_workloads:
+        line["workloads"] = workloads_bench(args)
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_bench(args)
     if rank == 0 and not args.no_workloads:
-        line["workloads"] = workloads_bench(args)
-    if rank == 0 and not args.no_workloads:
         line["frozen_hessian"] = frozen_hessian_bench(args)
-    if rank == 0 and not args.no_workloads:
         line["collocation"] = collocation_bench(args)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 
 
 # ------------------------------------------------------------------------------------------------
-def _timed_steps(ctx, n, oneshot=False, stop_residual=None):
+def _timed_steps(ctx, n, oneshot=False, stop_residual=None, chunk=None):
     """n steps (or until the steady residual falls below stop_residual), CUDA-event timed on the
-    context's stream; returns (steps, seconds, last stats)."""
+    context's stream; returns (steps, seconds, last stats, residual curve)."""
     import torch
     stream = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    done, secs, s = 0, 0.0, None
-    chunk = 50 if stop_residual else n
+    done, secs, s, curve = 0, 0.0, None, []
+    chunk = chunk or (100 if stop_residual else n)
     while done < n:
         k = min(chunk, n - done)
         a.record(stream)
@@ -355,20 +478,21 @@ def _timed_steps(ctx, n, oneshot=False, stop_residual=None):
         secs += a.elapsed_time(b) / 1e3
         done += k
         s = ctx.sync_stats()
+        curve.append((done, s.residual))
         if s.failed_cells:
             raise RuntimeError(f"failed cells: {s.as_dict()}")
         if stop_residual and s.residual < stop_residual:
             break
-    return done, secs, s
+    return done, secs, s, curve
 
 
 def workloads_bench(args):
-    """The other workloads, each as a bounded run on both precision paths (cell-steps/s by CUDA events):
-    1-D Burgers to its t_end; the 2-D ramp by One-Shot pseudo-time steps towards its 1e-8 residual (step
-    cap); the 2-D shear layer with adaptive degree 2-6 and 7^3 nodes (a bounded number of steps)."""
+    """The other workloads on both precision paths (cell-steps/s by CUDA events): 1-D Burgers to its
+    t_end; the 2-D ramp by One-Shot pseudo-time steps to its 1e-8 residual; the 2-D shear layer with
+    adaptive degree 2-6 and 7^3 nodes; the Sod tube under the literal 4-variable reading of its
+    configuration (the 2-D Euler system on a one-row mesh)."""
     import numpy as np
     from paper_1912_09238_gb300 import workloads
-    from tests._cases import gpu_context
     import torch
     out = {}
     stream = torch.cuda.current_stream()
@@ -377,65 +501,105 @@ def workloads_bench(args):
     w = workloads.BURGERS_1D
     r = {}
     for prec in ("mixed", "fp64") if only in (None, "burgers") else ():
-        ctx = gpu_context(w, precision=prec)
+        ctx = workloads.context(w, precision=prec)
         ctx.set_stream(stream.cuda_stream)
-        n, secs, s = _timed_steps(ctx, 176)
-        r[prec] = {"value": w["nx"] * n / secs, "steps": n, "t": s.t, "seconds": secs}
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s = ctx.run()
+        b.record(stream)
+        b.synchronize()
+        secs = a.elapsed_time(b) / 1e3
+        r[prec] = {"value": w["nx"] * s.steps / secs, "steps": int(s.steps), "t": s.t, "seconds": secs}
         ctx.close()
     if r:
-        out["burgers1d"] = {"workload": "1-D Burgers IPM, 200 cells, N = 6, Q = 10, barrier entropy, to t_end = 0.11",
-                            "unit": UNIT, **r}
-    # 2-D ramp, One-Shot towards residual 1e-8
+        out["burgers1d"] = {"workload": "1-D Burgers IPM, 200 cells, N = 6, Q = 10, barrier entropy, Algorithm 1 "
+                                        "from t = 0 to t_end = 0.11 (ipm_run)", "unit": UNIT, **r}
+    # 2-D ramp, One-Shot to residual 1e-8
     w = workloads.RAMP_2D
     cells = w["nx"] * w["ny"]
     r = {}
     for prec in ("mixed", "fp64") if only in (None, "ramp") else ():
-        ctx = gpu_context(w, precision=prec)
+        ctx = workloads.context(w, precision=prec)
         ctx.set_stream(stream.cuda_stream)
-        cap = args.ramp_steps if prec == "mixed" else min(args.ramp_steps, 200)
+        full = prec == "mixed" or args.full
+        cap = args.ramp_steps if full else args.ramp_fp64_steps
         tune = ctx.tuning()
-        n, secs, s = _timed_steps(ctx, cap, oneshot=True, stop_residual=w["residual_tol"] if prec == "mixed" else None)
+        n, secs, s, curve = _timed_steps(ctx, cap, oneshot=True, stop_residual=w["residual_tol"] if full else None)
         r[prec] = {"value": cells * n / secs, "steps": n, "residual": s.residual, "seconds": secs,
+                   "reached_tolerance": bool(s.residual < w["residual_tol"]),
+                   "residual_every_800_steps": [(k, float(f"{v:.3e}")) for k, v in curve[7::8]],
                    "newton_kernel": {1: "cta_per_cell", 2: "warp_per_cell"}[tune[0]],
                    "autotune_ms": {"cta_per_cell": tune[1], "warp_per_cell": tune[2]}}
         ctx.close()
     if r:
         out["ramp2d_oneshot"] = {"workload": "2-D steady Euler, 15-degree ramp, 256 x 128 cells, 2 uniform dims, "
-                                 "total degree 4 (15 x 4 moments), 5 x 5 nodes, One-Shot IPM (Algorithm 2); mixed "
-                                 "runs towards residual 1e-8 (capped), FP64 times the first 200 steps",
+                                 "total degree 4 (15 x 4 moments), 5 x 5 nodes, One-Shot IPM (Algorithm 2) from the "
+                                 "freestream until the steady residual (Eq. residualSteady) is below 1e-8"
+                                 + ("" if args.full else f"; FP64 times its first {args.ramp_fp64_steps} steps"),
                                  "unit": UNIT, **r}
     # 2-D shear layer, adaptive degree 2..6, 7^3 nodes
     w = workloads.variant(workloads.KH_2D, M=6, nq=7)
     cells = w["nx"] * w["ny"]
     r = {}
+    kh_steps = 200 if args.full else args.kh_steps
     for prec in ("mixed", "fp64", "mixed_f32f") if only in (None, "kh") else ():
-        ctx = gpu_context(w, precision=prec, adapt_min_degree=2, delta_lo=2e-5, delta_hi=2e-4)
+        ctx = workloads.context(w, precision=prec, adapt_min_degree=2, delta_lo=2e-5, delta_hi=2e-4)
         ctx.set_stream(stream.cuda_stream)
-        n, secs, s = _timed_steps(ctx, args.kh_steps)
+        nsteps = kh_steps if prec == "mixed" or args.full else max(1, kh_steps // 2)
+        n, secs, s, _ = _timed_steps(ctx, nsteps, chunk=10)
         lev = ctx.get_levels().reshape(w["ny"] + 2, w["nx"] + 2)[1:-1, 1:-1]
         r[prec] = {"value": cells * n / secs, "steps": n, "seconds": secs,
-                   "cells_per_degree": {str(2 + k): int(v) for k, v in enumerate(np.bincount(lev.ravel(), minlength=5))}}
+                   "cells_per_degree_at_end": {str(2 + k): int(v) for k, v in
+                                               enumerate(np.bincount(lev.ravel(), minlength=5))}}
         ctx.close()
     if r:
-        out["kh2d_adaptive"] = {"workload": f"2-D shear layer, 512 x 512 periodic, 3 uniform dims, adaptive total degree "
-                                f"2-6 (10-84 x 4 moments), 7^3 = 343 nodes, first {args.kh_steps} of the 200 steps "
-                                "(mixed_f32f: the FP32-factorisation mode, a departure from the FP64 factorisation of the headline)",
+        out["kh2d_adaptive"] = {"workload": "2-D shear layer, 512 x 512 periodic, 3 uniform dims, adaptive total degree "
+                                "2-6 (10-84 x 4 moments), 7^3 = 343 nodes, Algorithm 3 from the initial data "
+                                f"(mixed: {kh_steps} of the 200 steps; FP64 and mixed_f32f: "
+                                f"{kh_steps if args.full else max(1, kh_steps // 2)}; mixed_f32f is the "
+                                "FP32-factorisation mode, a departure from the FP64 factorisation of the headline)",
                                 "unit": UNIT, **r}
     # the same with a nested Clenshaw-Curtis rule per level (default levels 2, 2, 3, 3, 3: 125 or 729 nodes)
     w = workloads.variant(workloads.KH_2D, M=6, nq=7, cc_levels=())
     r = {}
+    cc_steps = max(1, kh_steps // 4)
     for prec in ("mixed", "fp64") if only in (None, "kh") else ():
-        ctx = gpu_context(w, precision=prec, adapt_min_degree=2, delta_lo=2e-5, delta_hi=2e-4)
+        ctx = workloads.context(w, precision=prec, adapt_min_degree=2, delta_lo=2e-5, delta_hi=2e-4)
         ctx.set_stream(stream.cuda_stream)
-        n, secs, s = _timed_steps(ctx, max(1, args.kh_steps // 2))
+        n, secs, s, _ = _timed_steps(ctx, cc_steps, chunk=5)
         lev = ctx.get_levels().reshape(w["ny"] + 2, w["nx"] + 2)[1:-1, 1:-1]
         r[prec] = {"value": cells * n / secs, "steps": n, "seconds": secs,
-                   "cells_per_degree": {str(2 + k): int(v) for k, v in enumerate(np.bincount(lev.ravel(), minlength=5))}}
+                   "cells_per_degree_at_end": {str(2 + k): int(v) for k, v in
+                                               enumerate(np.bincount(lev.ravel(), minlength=5))}}
         ctx.close()
     if r:
         out["kh2d_adaptive_cc"] = {"workload": "2-D shear layer as kh2d_adaptive with a nested tensor Clenshaw-Curtis "
                                    "rule per level (degrees 2-3: 5^3 = 125 nodes, 4-6: 9^3 = 729), first "
-                                   f"{max(1, args.kh_steps // 2)} steps", "unit": UNIT, **r}
+                                   f"{cc_steps} steps", "unit": UNIT, **r}
+    # Sod under the literal "56 moments x 4" reading: the 4-variable 2-D Euler system on a 2000 x 1 mesh
+    # (periodic in y, v_2 = 0), Algorithm 1 to t_end
+    w = workloads.SOD_1D_AS_2D
+    r = {}
+    for prec in ("mixed", "fp64") if only in (None, "sod_m4") else ():
+        ctx = workloads.context(w, precision=prec)
+        ctx.set_stream(stream.cuda_stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s = ctx.run() if prec == "mixed" or args.full else ctx.run(args.sod_m4_fp64_steps)
+        b.record(stream)
+        b.synchronize()
+        if s.failed_cells:
+            raise RuntimeError(f"failed cells: {s.as_dict()}")
+        secs = a.elapsed_time(b) / 1e3
+        r[prec] = {"value": w["nx"] * s.steps / secs, "steps": int(s.steps), "t": s.t, "seconds": secs}
+        ctx.close()
+    if r:
+        out["sod1d_m4"] = {"workload": "Sod as the headline under the literal '56 moments x 4' reading: 2-D Euler "
+                           "(rho, rho v1, rho v2, E) on a 2000 x 1 Cartesian mesh, outflow left/right, periodic "
+                           "bottom/top, v2 = 0, total degree 5 in 3 dims (N = 56 x 4), 216 Gauss nodes, local LF "
+                           "(Rusanov) faces, CFL 0.5, to t_end 0.14" +
+                           ("" if args.full else f" (FP64: its first {args.sod_m4_fp64_steps} time steps)"),
+                           "unit": UNIT, **r}
     return out
 
 
@@ -462,7 +626,6 @@ def collocation_bench(args):
     headline's."""
     import numpy as np
     from paper_1912_09238_gb300 import workloads
-    from tests._cases import gpu_collocation, gpu_context
     import torch
     out = {}
     stream = torch.cuda.current_stream()
@@ -473,7 +636,7 @@ def collocation_bench(args):
         err = lambda a, b: float(np.sqrt(np.sum(dx * (a - b) ** 2) / np.sum(dx * b ** 2)))
         rows = []
         for N, Q in ((3, 5), (6, 10), (10, 20)):
-            ctx = gpu_context(workloads.variant(w, M=N - 1, nq=Q), precision="fp64")
+            ctx = workloads.context(workloads.variant(w, M=N - 1, nq=Q), precision="fp64")
             ctx.set_stream(stream.cuda_stream)
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
@@ -485,7 +648,7 @@ def collocation_bench(args):
                          "E_rel_l2": err(u[:, 0], E_ref), "Var_rel_l2": err(np.sum(u[:, 1:] ** 2, axis=1), V_ref)})
             ctx.close()
         for Q in (5, 10, 20, 40):
-            g = gpu_collocation(workloads.variant(w, M=Q - 1, nq=Q))
+            g = workloads.collocation(workloads.variant(w, M=Q - 1, nq=Q))
             st = g.run()
             u = g.get_moments()[1:-1, :, 0]        # N = Q moments: their squares sum to the nodal variance
             rows.append({"method": "SC", "Q": Q, "steps": int(st.max_node_steps), "ms": st.elapsed_ms,
@@ -495,7 +658,7 @@ def collocation_bench(args):
                                               "solution's cell averages (the first-order LF error included)",
                                   "runs": rows}
     w = workloads.SOD_1D
-    g = gpu_collocation(w)
+    g = workloads.collocation(w)
     st = g.run()
     steps, _, _ = g.node_info()
     out["sod1d"] = {"workload": "1-D Sod, 2000 cells, 216 Gauss nodes (6^3), to t_end 0.14", "ms": st.elapsed_ms,
@@ -507,21 +670,19 @@ def collocation_bench(args):
 
 def frozen_hessian_bench(args):
     """The Sod workload with frozen Hessians (ipm_options.hessian_reuse 2: Cholesky factors kept per
-    cell across solves, reused while they converge): both precision paths, 5 warm-up + 30 timed steps."""
+    cell across solves, reused while they converge): both precision paths, the full run."""
     from paper_1912_09238_gb300 import workloads
-    from tests._cases import gpu_context
     import torch
-    out = {"workload": "Sod (as the headline) with hessian_reuse = 2, reuse_ratio 0.5", "unit": UNIT}
+    out = {"workload": "Sod (as the headline) with hessian_reuse = 2, reuse_ratio 0.5, one full run to t_end",
+           "unit": UNIT}
     stream = torch.cuda.current_stream()
     for prec in ("mixed", "fp64"):
-        ctx = gpu_context(workloads.SOD_1D, precision=prec, hessian_reuse=2)
+        ctx = workloads.context(workloads.SOD_1D, precision=prec, hessian_reuse=2)
         ctx.set_stream(stream.cuda_stream)
-        for _ in range(5):
-            ctx.step(sync=False)
-        it = fa = 0
-        n, secs, _ = 30, 0.0, None
+        it = fa = n = 0
+        secs = 0.0
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for _ in range(n):
+        while True:
             a.record(stream)
             ctx.step(sync=False)
             b.record(stream)
@@ -529,25 +690,20 @@ def frozen_hessian_bench(args):
             secs += a.elapsed_time(b) / 1e3
             it += s.newton_iters
             fa += s.factorizations
-        out[prec] = {"value": workloads.SOD_1D["nx"] * n / secs, "ms_per_step": 1e3 * secs / n,
-                     "newton_updates_per_step": it / n, "factorizations_per_step": fa / n}
+            n += 1
+            if s.failed_cells:
+                raise RuntimeError(f"failed cells: {s.as_dict()}")
+            if s.t >= workloads.SOD_1D["t_end"] * (1 - 1e-12):
+                break
+        out[prec] = {"value": workloads.SOD_1D["nx"] * n / secs, "time_steps": n, "ms_per_time_step": 1e3 * secs / n,
+                     "newton_updates_per_time_step": it / n, "factorizations_per_time_step": fa / n}
         ctx.close()
     return out
 
 
 # ------------------------------------------------------------------------------------------------
-def _request(w, precision):
-    from paper_1912_09238_gb300 import ipm
-    pr = ipm.make_problem(w["kind"], w["nx"], w["x_lo"], w["x_hi"], bc=w["bc"], cfl=w["cfl"], t_end=w["t_end"],
-                          gamma=w["gamma"], x0=w["x0"], dx0=w["dx0"], left=w["left"], dleft=w.get("dleft"),
-                          right=w["right"], dright=w.get("dright"))
-    o = ipm.default_options(precision, newton_tol=w.get("newton_tol", 1e-10))
-    return ipm.make_request(pr, w["p"], w["M"], w["nq"], w["entropy"], w.get("u_minus", 0.0), w.get("u_plus", 0.0),
-                            o, max_steps=w["steps"])
-
-
 def _serve(reqs, arrivals, max_active):
-    """Replay the arrivals against one server; returns per-request (latency_s, cell_steps) and the makespan."""
+    """Replay the arrivals against one server; returns per-request latencies, cell-steps and the makespan."""
     import numpy as np
     from paper_1912_09238_gb300 import ipm
     srv = ipm.Server(mem_cap_bytes=0, max_active=max_active)
@@ -558,7 +714,7 @@ def _serve(reqs, arrivals, max_active):
         if dt > 0:
             time.sleep(dt)
         tickets.append(srv.submit(req))
-    srv.drain(1800.0)
+    srv.drain(3600.0)
     res = [srv.poll(t, fetch=False)[0] for t in tickets]
     srv.close()
     if any(r.status != 0 for r in res):
@@ -572,30 +728,42 @@ def _serve(reqs, arrivals, max_active):
 
 def serving_bench(args):
     """Serving workload (seeded Poisson arrivals of 1-D Burgers / Euler requests of mixed sizes, N 3..84,
-    Q = (degree+1)^dims): the mixed-precision server at saturation and at 0.8x its saturation rate, and the
-    same requests run one after another on the plain FP64 GPU path."""
+    Q = (degree+1)^dims): the mixed-precision server at saturation and at Poisson rates of 0.5, 0.8 and
+    1.0 x its saturation rate, and a prefix of the same requests run one after another on the plain FP64
+    GPU path."""
     import numpy as np
     import torch
     from paper_1912_09238_gb300 import workloads
-    from tests._cases import gpu_context
-    n, steps = args.serving_requests, args.serving_steps
+    n = 10000 if args.full else args.serving_requests
+    steps = args.serving_steps
     stream = [w for _, w in workloads.serving_requests(n, seed=1234, steps=steps)]
-    reqs = [(_request(w, "mixed"), w) for w in stream]
+    reqs = [(workloads.request(w, "mixed"), w) for w in stream]
+    out = {"workload": (f"{n} seeded requests (seed 1234), each 1-D Burgers or 1-D Euler, cells U[200,4000], total "
+                        f"degree 2-6 in 1-3 uniform dims (N 3-84), tensor Gauss (degree+1)^dims, {steps} Algorithm-1 "
+                        f"steps each, mixed precision, {args.serving_slots} slots, memory cap 90% of free HBM"),
+           "requests": n}
     # saturation: everything arrives at once
     lat_sat, cs, span = _serve(reqs, [0.0] * n, args.serving_slots)
     rate_sat = n / span
-    # Poisson arrivals at 0.8 x the saturation rate (same requests, seeded inter-arrival times)
-    rng = np.random.default_rng(1234)
-    arr = np.cumsum(rng.exponential(1.0 / (0.8 * rate_sat), n)) - 0.0
-    arr -= arr[0]
-    lat, cs2, span2 = _serve(reqs, list(arr), args.serving_slots)
-    # sequential FP64 GPU: one request at a time, each to completion
+    out["cell_steps"] = cs
+    out["saturation"] = {"value": cs / span, "unit": UNIT, "makespan_s": span, "requests_per_s": rate_sat,
+                         "p50_latency_s": float(np.percentile(lat_sat, 50)),
+                         "p99_latency_s": float(np.percentile(lat_sat, 99))}
+    # Poisson arrivals at fractions of the saturation rate (same requests, seeded inter-arrival times)
+    for frac in (0.5, 0.8, 1.0):
+        rng = np.random.default_rng(1234)
+        arr = np.cumsum(rng.exponential(1.0 / (frac * rate_sat), n))
+        arr -= arr[0]
+        lat, cs2, span2 = _serve(reqs, list(arr), args.serving_slots)
+        out[f"poisson_{frac}x"] = {"value": cs2 / span2, "unit": UNIT, "makespan_s": span2, "rate_per_s": frac * rate_sat,
+                                   "p50_latency_s": float(np.percentile(lat, 50)),
+                                   "p99_latency_s": float(np.percentile(lat, 99))}
+    # sequential FP64 GPU: one request at a time, each to completion (a prefix of the stream)
     torch.cuda.synchronize()
-    t_seq = 0.0
-    seq_lat = []
-    for w in stream:
+    t_seq, seq_lat, cs_seq = 0.0, [], 0
+    for w in stream[:args.sequential_requests]:
         t0 = time.perf_counter()
-        ctx = gpu_context(w, precision="fp64")
+        ctx = workloads.context(w, precision="fp64")
         for _ in range(w["steps"]):
             ctx.step(sync=False)
         s = ctx.sync_stats()
@@ -606,85 +774,129 @@ def serving_bench(args):
             raise RuntimeError("sequential FP64 request failed")
         t_seq += dt
         seq_lat.append(dt)
-    return {
-        "workload": (f"{n} seeded requests (seed 1234), each 1-D Burgers or 1-D Euler, cells U[200,4000], total "
-                     f"degree 2-6 in 1-3 uniform dims (N 3-84), tensor Gauss (degree+1)^dims, {steps} Algorithm-1 "
-                     f"steps each, mixed precision, {args.serving_slots} slots, memory cap 90% of free HBM"),
-        "cell_steps": cs,
-        "saturation": {"value": cs / span, "unit": UNIT, "makespan_s": span, "requests_per_s": rate_sat,
-                       "p50_latency_s": float(np.percentile(lat_sat, 50)),
-                       "p99_latency_s": float(np.percentile(lat_sat, 99))},
-        "poisson_0.8x": {"value": cs2 / span2, "unit": UNIT, "makespan_s": span2, "rate_per_s": 0.8 * rate_sat,
-                         "p50_latency_s": float(np.percentile(lat, 50)),
-                         "p99_latency_s": float(np.percentile(lat, 99))},
-        "sequential_fp64_gpu": {"value": cs / t_seq, "unit": UNIT, "total_s": t_seq,
-                                "p50_latency_s": float(np.percentile(seq_lat, 50)),
-                                "p99_latency_s": float(np.percentile(seq_lat, 99)),
-                                "note": "each request alone, wall time including context set-up, as the server's "
-                                        "latencies include it"},
-        "speedup_served_mixed_over_sequential_fp64": (cs / span) / (cs / t_seq),
-    }
+        cs_seq += w["nx"] * w["steps"]
+    out["sequential_fp64_gpu"] = {"value": cs_seq / t_seq, "unit": UNIT, "requests": len(seq_lat), "total_s": t_seq,
+                                  "p50_latency_s": float(np.percentile(seq_lat, 50)),
+                                  "p99_latency_s": float(np.percentile(seq_lat, 99)),
+                                  "note": "the first requests of the stream, each alone, wall time including context "
+                                          "set-up, as the server's latencies include it"}
+    out["speedup_served_mixed_over_sequential_fp64"] = (cs / span) / (cs_seq / t_seq)
+    return out
 
 
 # ------------------------------------------------------------------------------------------------
-def oracle_step_sample(kind, n_steps):
-    """Time the CPU oracle (single thread) on a bounded sample of the Sod workload.
+def _oracle_dual_chunk(args):
+    """Worker of the host-core baseline: the oracle's dual solve (Eq. dualIterationFunction to Eq.
+    tauCrit) on one contiguous range of cells."""
+    w, lam, uhat = args
+    from oracle import dual as od
+    prob = _oracle_chunk_problem(w)
+    out = od.dual_solve(prob.space, prob.ent, lam, uhat, prob.newton)
+    return out[0], out[1], out[2]
 
-    kind == "first_step": Algorithm 1 step 1 of the full 2000-cell workload from its initial data.
-    kind == "window": n_steps consecutive Algorithm-1 steps on the 200 cells around the interface
-    (same dx), from the initial data. Returns the seconds of each step."""
-    from paper_1912_09238_gb300 import workloads
+
+_PROB_CACHE = {}
+
+
+def _oracle_chunk_problem(w, warm_only=False):
+    key = w["name"]
+    if key not in _PROB_CACHE:
+        from tests._cases import oracle_problem
+        _PROB_CACHE[key] = oracle_problem(w)
+    return None if warm_only else _PROB_CACHE[key]
+
+
+def _oracle_warm(w):
+    _oracle_chunk_problem(w, warm_only=True)
+
+
+def oracle_sample(n_steps, procs, keep_state=False):
+    """Time the CPU oracle on the first n_steps Algorithm-1 steps of the full 2000-cell Sod workload from
+    its initial data, with the cells' dual solves split over `procs` worker processes (the solve of each
+    cell is independent; the oracle's own dual_solve runs unchanged on each range) and the rest of each
+    step (nodal states, time step, moment update, boundary cells: oracle.scheme1d's functions, in the order
+    of its ipm_step) in this process. Returns the seconds of each step."""
+    import multiprocessing as mp
+    import numpy as np
     from tests._cases import oracle_problem
     from oracle import scheme1d as s1
-    w = workload() if kind == "first_step" else workloads.variant(workload(), **WINDOW)
+    w = workload()
     prob = oracle_problem(w)
     st = s1.initial_state(prob)
+    ctxm = mp.get_context("spawn")
     secs = []
-    for _ in range(1 if kind == "first_step" else n_steps):
-        t0 = time.perf_counter()
-        st = s1.ipm_step(prob, st)
-        secs.append(time.perf_counter() - t0)
-        assert (st.newton_status == 0).all()
-    return {"cells": w["nx"], "seconds": secs}
+    with ctxm.Pool(procs) as pool:
+        pool.map(_oracle_warm, [w] * procs)                   # workers build their tables before the clock
+        bounds = np.linspace(0, st.uhat.shape[0], procs + 1).astype(int)
+        for _ in range(n_steps):
+            t0 = time.perf_counter()
+            parts = pool.map(_oracle_dual_chunk, [(w, st.lam[a:b], st.uhat[a:b]) for a, b in zip(bounds[:-1], bounds[1:])])
+            lam = np.concatenate([p[0] for p in parts])
+            stat = np.concatenate([p[2] for p in parts])
+            assert (stat == 0).all()
+            U = s1.nodal_states(prob, lam)
+            dt = s1.time_step(prob, U, st.t)
+            uhat = st.uhat.copy()
+            uhat[1:-1] = s1.moment_update(prob, lam, dt)
+            s1.apply_bc(prob, uhat)
+            lam_next = lam.copy()
+            s1.apply_bc(prob, lam_next)
+            st = s1.State1D(uhat=uhat, lam=lam_next, t=st.t + dt, n=st.n + 1, last_dt=dt)
+            secs.append(time.perf_counter() - t0)
+    out = {"cells": w["nx"], "seconds": secs, "procs": procs}
+    if keep_state:
+        out["uhat"] = st.uhat
+    return out
 
 
-def _oracle_subprocess(kind, n_steps=1):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_subprocess(n_steps, procs):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         env.pop(k, None)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", kind,
-                        "--steps", str(n_steps)], env=env, capture_output=True, text=True, timeout=1800)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n_steps),
+                        "--oracle-procs", str(procs)], env=env, capture_output=True, text=True, timeout=1800)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def cpu_baseline():
-    res = _oracle_subprocess("first_step")
-    secs = res["seconds"][0]
-    return {"value": res["cells"] / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle (numpy FP64, one thread) Algorithm-1 step 1 of the full {res['cells']}-cell Sod "
-                      f"workload from its initial data: {secs:.1f} s"}
+    procs = host_cores()
+    res = _oracle_subprocess(CPU_SAMPLE_STEPS, procs)
+    secs = sum(res["seconds"])
+    return {"value": res["cells"] * len(res["seconds"]) / secs, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"oracle (numpy FP64) Algorithm-1 steps 1..{len(res['seconds'])} of the full {res['cells']}-cell "
+                      f"Sod workload from its initial data, the cells' dual solves split over {procs} processes "
+                      f"(one thread each): {secs:.1f} s; the GPU's rate on the same steps is "
+                      "run.first_time_steps"}
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    res = _oracle_subprocess("window", args.warmup + args.steps)
+    procs = host_cores()
+    res = _oracle_subprocess(args.warmup + args.steps, procs)
     times = res["seconds"][args.warmup:]
     cells = res["cells"]
     value = cells * len(times) / sum(times)
     w = workload()
-    sample = (f"oracle (numpy FP64, one thread) Algorithm-1 steps {args.warmup + 1}..{args.warmup + args.steps} "
-              f"on the {cells} cells of the Sod workload around the interface (x in [0.45,0.55], same dx), "
-              f"from the initial data")
+    sample = (f"oracle (numpy FP64) Algorithm-1 steps {args.warmup + 1}..{args.warmup + args.steps} of the full "
+              f"{cells}-cell Sod workload from its initial data, each step one bench step, the cells' dual solves "
+              f"split over {procs} processes (one thread each)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {**workload_desc(w, "fp64"), "l2": "not applicable (host run)",
                        "inputs": "initial data projected by the oracle in host memory"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -692,25 +904,32 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=5, help="timed full runs")
+    ap.add_argument("--warmup", type=int, default=3, help="untimed full runs before them")
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--precision", choices=["fp64", "mixed", "mixed_f32f"], default="mixed")
-    ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the plain FP64 GPU path")
+    ap.add_argument("--full", action="store_true", help="long forms of the other workloads")
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip timing the other precision modes")
+    ap.add_argument("--compare-runs", type=int, default=2, help="timed full runs of each other precision mode")
+    ap.add_argument("--e2e-runs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--no-workloads", action="store_true", help="skip the Burgers / ramp / shear-layer runs")
-    ap.add_argument("--ramp-steps", type=int, default=1000, help="One-Shot step cap of the ramp workload")
-    ap.add_argument("--kh-steps", type=int, default=10, help="steps of the adaptive shear-layer workload")
-    ap.add_argument("--only", choices=["burgers", "ramp", "kh", "collocation"], default=None,
-                    help="run only this workload's timing (no JSON bench line; for profiling)")
-    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--no-workloads", action="store_true", help="skip the other workloads")
+    ap.add_argument("--ramp-steps", type=int, default=20000, help="One-Shot step cap of the ramp workload")
+    ap.add_argument("--ramp-fp64-steps", type=int, default=1000)
+    ap.add_argument("--kh-steps", type=int, default=20, help="steps of the adaptive shear layer (mixed)")
+    ap.add_argument("--sod-m4-fp64-steps", type=int, default=200)
+    ap.add_argument("--only", choices=["burgers", "ramp", "kh", "sod_m4", "collocation", "serving"], default=None,
+                    help="run only this workload's timing (no headline; for profiling)")
+    ap.add_argument("--serving-requests", type=int, default=1000)
     ap.add_argument("--serving-steps", type=int, default=10)
     ap.add_argument("--serving-slots", type=int, default=32)
-    ap.add_argument("--oracle-sample", choices=["first_step", "window"], default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--sequential-requests", type=int, default=200)
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-procs", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_sample:
-        print(json.dumps(oracle_step_sample(args.oracle_sample, args.steps)), flush=True)
+        print(json.dumps(oracle_sample(args.oracle_sample, args.oracle_procs)), flush=True)
         return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -722,7 +941,13 @@ def main():
         torch.cuda.set_stream(torch.cuda.Stream())
         import __graft_entry__
         __graft_entry__.build()
-        print(json.dumps(collocation_bench(args) if args.only == "collocation" else workloads_bench(args)), flush=True)
+        if args.only == "collocation":
+            res = collocation_bench(args)
+        elif args.only == "serving":
+            res = serving_bench(args)
+        else:
+            res = workloads_bench(args)
+        print(json.dumps(res), flush=True)
     else:
         run_gpu(args)
 

@@ -228,12 +228,19 @@ typedef struct {
   double residual;          /* steady residual of the last step (Eq. residualSteady, first variable) */
   int64_t steps;            /* steps taken since ipm_init */
   int32_t tc_timeouts;      /* mixed path: bounded tensor-core / bulk-copy waits that ran out (0 normally;
-                               the affected cells report IPM_ETIMEOUT) */
+                               the affected cells report IPM_ETIMEOUT). If a CTA then cannot drain its
+                               outstanding tensor-core work either, it keeps its tensor memory, the
+                               stats call returns IPM_ETIMEOUT and every later launching call on the
+                               context returns IPM_ETIMEOUT without launching: destroy the context. */
   int64_t factorizations;   /* Cholesky factorisations of the last solve (equals newton_iters without
                                frozen Hessians) */
   int32_t fp32_fallbacks;   /* IPM_PREC_MIXED_F32_FACTOR: FP32 factorisations redone in FP64 (cumulative) */
   int64_t cached_checks;    /* cells of the last solve whose convergence check came from their moment
                                image (ipm_options.check_cache) */
+  int64_t hessian_ns;       /* mixed paths, CTA-per-cell kernel: summed duration of the last solve's
+                               tensor-core Hessian assemblies (row (b) of Sec. 3.1), each timed on the
+                               device from its start to its last barrier; 0 on the FP64 path */
+  int64_t hessian_count;    /* ... the number of assemblies that sum covers */
 } ipm_stats;
 
 typedef struct ipm_ctx ipm_ctx;
@@ -376,10 +383,12 @@ ipm_status ipm_sync_stats(ipm_ctx* ctx, ipm_stats* stats);
  * cudaMalloc, cudaFree or allocating library routine is called. Sizes beyond the scratch (or more
  * than IPM_NOALLOC_MAX_CELLS cells) return IPM_EINVAL with a message in ipm_last_error(NULL).
  * Calls share the array and it keeps the last call's contents (counters are cleared at the start
- * of each call); calls that overlap on the GPU race and must not be issued concurrently. The first
- * call on a device looks up the array's address (cudaGetSymbolAddress); make that first call before
- * any stream capture. The call waits for the table upload on the stream; with stats != NULL it
- * also waits for the solve and fills the counters. FP64 precision, 1-D problem kinds only. */
+ * of each call); calls that overlap on the GPU race and must not be issued concurrently. Every call
+ * looks up the array's device address on the current device (cudaGetSymbolAddress); the first call
+ * on a device also loads the library's kernels there, so make that first call before any stream
+ * capture. Each call uploads its tables from host memory and waits on the stream for that upload;
+ * with stats != NULL it also waits for the solve and fills the counters. Unknown problem or entropy
+ * kinds return IPM_EINVAL. FP64 precision, 1-D problem kinds only. */
 ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, const ipm_basis* basis,
                                   const ipm_quadrature* quad, const ipm_entropy* entropy,
                                   const ipm_options* options, int n_cells, const double* d_uhat,

@@ -151,14 +151,15 @@ class FreestreamIC:
 
 @dataclass
 class RiemannXIC:
-    """One jump in x at x0, uniform in y: primitive (rho, v_1, v_2, p) states left and right, each
-    affine in xi (rows of d... are the xi-derivatives of the four primitives). Exact cell averages
-    in x (rectangular cells)."""
+    """One jump in x at x0 + dx0 . xi, uniform in y: primitive (rho, v_1, v_2, p) states left and right,
+    each affine in xi (rows of d... are the xi-derivatives of the four primitives). Exact cell averages
+    in x (rectangular cells), node by node."""
     left: tuple
     right: tuple
     x0: float
     dleft: tuple = ((0.0, 0.0, 0.0),) * 4
     dright: tuple = ((0.0, 0.0, 0.0),) * 4
+    dx0: tuple = (0.0, 0.0, 0.0)
 
     def _state(self, phys, prim0, dprim, nodes):
         g = phys.gamma
@@ -172,8 +173,9 @@ class RiemannXIC:
         x = mesh.X[:, 0]
         dx = x[1] - x[0]
         xl = np.concatenate([[x[0] - dx], x[:-1], [x[-1]]])           # left edges incl. ghosts
-        frac = np.clip((self.x0 - xl) / dx, 0.0, 1.0)                 # (nx+2,)
-        u = frac[:, None, None] * UL[None] + (1 - frac[:, None, None]) * UR[None]   # (nx+2, Q, 4)
+        x0 = _affine(self.x0, self.dx0, nodes)                         # (Q,)
+        frac = np.clip((x0[None, :] - xl[:, None]) / dx, 0.0, 1.0)    # (nx+2, Q)
+        u = frac[:, :, None] * UL[None] + (1 - frac[:, :, None]) * UR[None]   # (nx+2, Q, 4)
         return np.broadcast_to(u[None], (ny2,) + u.shape).copy()
 
 

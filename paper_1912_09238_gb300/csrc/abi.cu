@@ -90,6 +90,9 @@ struct ipm_ctx {
   // graphs
   cudaGraphExec_t step_exec = nullptr;
   cudaGraphExec_t oneshot_exec = nullptr;
+  // set once a Newton CTA reported tensor-core work it could not drain (StepScalars::tc_stuck): its
+  // tensor memory stays allocated and nothing more is launched into this context
+  bool unusable = false;
   std::string err;
 };
 
@@ -1131,6 +1134,8 @@ static void fill_stats(const StepScalars& h, ipm_stats* s) {
   s->factorizations = (int64_t)h.last_factorizations;
   s->fp32_fallbacks = h.fp32_fallbacks;
   s->cached_checks = (int64_t)h.last_cached_checks;
+  s->hessian_ns = (int64_t)h.last_hessian_ns;
+  s->hessian_count = (int64_t)h.last_hessian_count;
 }
 
 ipm_status ipm_sync_stats(ipm_ctx* c, ipm_stats* s) {
@@ -1139,12 +1144,17 @@ ipm_status ipm_sync_stats(ipm_ctx* c, ipm_stats* s) {
   IPM_CK(c, cudaMemcpyAsync(&h, c->d_sc, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->stream));
   IPM_CK(c, cudaStreamSynchronize(c->stream));
   fill_stats(h, s);
+  if (h.tc_stuck) {
+    c->unusable = true;
+    return fail(c, IPM_ETIMEOUT, "tensor-core work could not be drained after a timeout; the context is unusable");
+  }
   return IPM_OK;
 }
 
 ipm_status ipm_dual_solve(ipm_ctx* c, ipm_stats* s) {
   NvtxRange nvtx_("ipm_dual_solve");
   if (!c) return IPM_EINVAL;
+  if (c->unusable) return fail(c, IPM_ETIMEOUT, "context unusable after an undrained tensor-core timeout");
   IPM_CK(c, enqueue_newton(c, 0, c->stream));
   IPM_CK(c, launch_finalize(c->d_sc, c->d_iters, c->d_status, nullptr, c->n_cells, c->is2d ? 0 : 1,
                             c->is2d ? c->n_cells : c->n_interior, 0, c->stream));
@@ -1155,6 +1165,7 @@ ipm_status ipm_dual_solve(ipm_ctx* c, ipm_stats* s) {
 ipm_status ipm_assemble_hessian(ipm_ctx* c, double* h, size_t count) {
   NvtxRange nvtx_("ipm_assemble_hessian");
   if (!c || (!h && count)) return IPM_EINVAL;
+  if (c->unusable) return fail(c, IPM_ETIMEOUT, "context unusable after an undrained tensor-core timeout");
   const size_t nph = (size_t)c->NM * (c->NM + 1) / 2;
   if (count != (size_t)c->n_interior * nph) return fail(c, IPM_EINVAL, "ipm_assemble_hessian: count must be n_interior*NM(NM+1)/2");
   double* d = nullptr;
@@ -1177,6 +1188,7 @@ ipm_status ipm_assemble_hessian(ipm_ctx* c, double* h, size_t count) {
 ipm_status ipm_update(ipm_ctx* c, double dt) {
   NvtxRange nvtx_("ipm_update");
   if (!c) return IPM_EINVAL;
+  if (c->unusable) return fail(c, IPM_ETIMEOUT, "context unusable after an undrained tensor-core timeout");
   if (!(dt > 0.0)) return fail(c, IPM_EINVAL, "ipm_update: dt must be positive");
   if (c->is2d) {
     IPM_CK(c, launch_update2d(update2d_args(c, dt, false, false), c->update_grid, c->stream));
@@ -1191,6 +1203,7 @@ ipm_status ipm_update(ipm_ctx* c, double dt) {
 ipm_status ipm_step(ipm_ctx* c, ipm_stats* s) {
   NvtxRange nvtx_("ipm_step");
   if (!c) return IPM_EINVAL;
+  if (c->unusable) return fail(c, IPM_ETIMEOUT, "context unusable after an undrained tensor-core timeout");
   IPM_CK(c, cudaGraphLaunch(c->step_exec, c->stream));
   if (s) return ipm_sync_stats(c, s);
   return IPM_OK;
@@ -1199,6 +1212,7 @@ ipm_status ipm_step(ipm_ctx* c, ipm_stats* s) {
 ipm_status ipm_oneshot_step(ipm_ctx* c, ipm_stats* s) {
   NvtxRange nvtx_("ipm_oneshot_step");
   if (!c) return IPM_EINVAL;
+  if (c->unusable) return fail(c, IPM_ETIMEOUT, "context unusable after an undrained tensor-core timeout");
   IPM_CK(c, cudaGraphLaunch(c->oneshot_exec, c->stream));
   if (s) return ipm_sync_stats(c, s);
   return IPM_OK;
@@ -1220,6 +1234,7 @@ ipm_status ipm_step_timing(ipm_ctx* c, float* newton_ms, float* update_ms, float
 ipm_status ipm_run(ipm_ctx* c, int64_t max_steps, ipm_stats* s) {
   NvtxRange nvtx_("ipm_run");
   if (!c) return IPM_EINVAL;
+  if (c->unusable) return fail(c, IPM_ETIMEOUT, "context unusable after an undrained tensor-core timeout");
   if (!(c->prob.t_end > 0.0)) return fail(c, IPM_EINVAL, "ipm_run: t_end must be positive");
   ipm_stats cur;
   ipm_status st = ipm_sync_stats(c, &cur);

@@ -5,7 +5,7 @@
 //   1-D Riemann data: frac U_L(xi) + (1 - frac) U_R(xi), frac = clip((x0(xi) - x_{j-1/2}) / dx, 0, 1).
 //   2-D (Sec. 7): uniform freestream (Mach and flow angle uncertain); a shear band averaged exactly
 //   over the cell's y-extent with the transverse velocity at the cell centre's x; a Riemann jump in x
-//   averaged exactly over the cell's x-extent.
+//   (interface x0(xi)) averaged exactly over the cell's x-extent.
 #pragma once
 #include <cmath>
 
@@ -22,7 +22,7 @@ struct IC1D {
 struct IC2D {
   int nx, ny, ic_kind;
   double x_lo, dx, y_lo, dy, gamma;
-  double x0;
+  double x0, dx0[3];
   double left[4], dleft[4][3], right[4], dright[4][3];
   double param[4], dparam[4][3];
 };
@@ -56,6 +56,7 @@ inline IC2D ic2d_params(const ipm_problem& prob) {
   a.dy = (prob.y_hi - prob.y_lo) / prob.ny;
   a.gamma = prob.gamma;
   a.x0 = prob.ic_x0;
+  for (int d = 0; d < 3; ++d) a.dx0[d] = prob.ic_dx0[d];
   for (int v = 0; v < 4; ++v) {
     a.left[v] = prob.ic_left[v];
     a.right[v] = prob.ic_right[v];
@@ -162,7 +163,8 @@ __device__ __forceinline__ void ic2d_average(const IC2D& a, int ii, int jj, cons
     prim4_to_cons(pl[0], pl[1], pl[2], pl[3], a.gamma, UL);
     prim4_to_cons(pr[0], pr[1], pr[2], pr[3], a.gamma, UR);
     const double x_left = a.x_lo + (ii - 1) * a.dx;
-    const double frac = fmin(fmax((a.x0 - x_left) / a.dx, 0.0), 1.0);
+    const double x0 = affine3(a.x0, a.dx0, xi, P);
+    const double frac = fmin(fmax((x0 - x_left) / a.dx, 0.0), 1.0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) ub[k] = frac * UL[k] + (1.0 - frac) * UR[k];
   }

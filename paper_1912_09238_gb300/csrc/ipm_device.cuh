@@ -250,6 +250,11 @@ struct StepScalars {
   int fp32_fallbacks;                      // FP32-factor mode: factorisations redone in FP64 (cumulative)
   unsigned long long cached_checks;        // cells whose convergence check came from their moment image
   unsigned long long last_cached_checks;   // ... of the last solve
+  int tc_stuck;                  // sticky: a CTA could not drain its tensor-core work after a timeout
+  unsigned long long hessian_ns;        // mixed path: tensor-core Hessian phases since the last reduction (ns, summed over CTAs)
+  unsigned long long hessian_count;     // ... and how many
+  unsigned long long last_hessian_ns;   // ... of the last solve
+  unsigned long long last_hessian_count;
 };
 
 // Mixed-precision Hessian (tensor cores): tiling of H_ab = Phi^T diag(w J_ab) Phi as MMAs with

@@ -562,6 +562,257 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
 }
 
 // ------------------------------------------------------------------------------------------------
+// (c), split variant: the right-looking factorisation of cholesky_aug with outer panels of SNB = 16
+// columns, whose trailing updates A22 -= L21 L21^T run on the tensor cores as exact integer products.
+//
+// Each row r of a finished panel (16 entries of L21; the gradient row n included) is written as
+// 2^e_r sum_{i=1..7} d_i 2^(-8i): e_r is the exponent of the row's largest entry and the integer digits
+// d_i, |d_i| <= 255, are the base-256 digits of the entries' binary expansions truncated to 56 bits
+// (the error-free splitting of Ozaki, Ogita and Oishi, 2012, with one scale per row). A digit is exact in
+// BF16 and a product of two digits exact in FP32. For every output entry the seven diagonals
+// D_t = sum_{i+j=t} sum_k d_i[r][k] d_j[c][k], t = 2..8, are accumulated by tcgen05.mma in seven FP32
+// accumulators in tensor memory; a diagonal sums at most 7 x 16 products below 2^16, so it stays below
+// 2^24 and is exact. The diagonals are combined exactly in a 64-bit integer, 2^56 S = sum_t D_t 2^(56-8t)
+// (the t = 8 term truncated), converted to FP64 and subtracted as A22 -= 2^(e_r + e_c - 56) (2^56 S).
+// The roundings are the 56-bit truncation of the digits (relative to the row's largest entry), the
+// conversion of 2^56 S and the final FMA: FP64-level accuracy, with the FP64 work of a trailing entry cut
+// from 16 FMAs per panel to one conversion and one FMA. The panel itself (two blocks of NB = 8 columns)
+// is factorised in FP64 by panel_diag / panel_trsm as in cholesky_aug.
+// Digit slices: SDIG arrays of s_rows x 16 BF16 in the K-major core-matrix layout (8-row groups SSBO
+// bytes apart), rows counted from the first trailing row s1; rows beyond the trailing block hold stale
+// data that only ever feeds output rows and columns that are not read back.
+// ------------------------------------------------------------------------------------------------
+constexpr int SNB = 16;                 // outer panel width = MMA K
+constexpr int SDIG = 7;                 // base-256 digits per entry (56 bits)
+constexpr int SBLK = 32;                // output columns per MMA (N)
+constexpr uint32_t SSBO = 256;          // tc::kmajor_sbo(16)
+constexpr int SPLIT_BUF_COLS = 256;     // tensor-memory columns of one accumulator set (7 x SBLK used)
+
+struct SplitSmem {
+  uint8_t* slices;   // SDIG x rows x 16 BF16
+  int* rexp;         // [rows] biased exponent field of each row's largest entry
+  int rows;          // rows per slice (multiple of 32, >= 128)
+  int nbuf;          // accumulator sets in tensor memory (1, or 2 to overlap MMAs with the combine)
+};
+
+// BF16 bits of the integer +-d, 0 <= d <= 255 (exact)
+__device__ __forceinline__ uint32_t digit_bf16(uint32_t d, bool neg) {
+  if (d == 0) return 0u;
+  const int p = 31 - __clz(d);
+  return ((uint32_t)(p + 127) << 7) | ((d << (7 - p)) & 0x7Fu) | (neg ? 0x8000u : 0u);
+}
+
+// Digit slices and row exponents of rows s1..n of the panel columns kb..kb+kw-1 (kw <= 16; the other
+// columns get zero digits). Two threads per row, eight columns each.
+__device__ void split_panel(const double* A, int n, int kb, int kw, int s1, const SplitSmem& sp) {
+  const int R = n + 1 - s1;
+  const uint32_t slice_bytes = (uint32_t)sp.rows * 32u;
+  for (int base = 0; base < 2 * R; base += NT) {
+    const int item = base + threadIdx.x;
+    const bool valid = item < 2 * R;
+    const int rs = item >> 1, half = item & 1;
+    long long bits[8];
+    int emax = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = half * 8 + e;
+      bits[e] = (valid && k < kw) ? __double_as_longlong(A[rowoff(s1 + rs) + kb + k]) : 0ll;
+      emax = max(emax, (int)((bits[e] >> 52) & 0x7FF));
+    }
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
+    if (valid) {
+      uint32_t w[SDIG][4];
+#pragma unroll
+      for (int i = 0; i < SDIG; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[i][q] = 0u;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int E = (int)((bits[e] >> 52) & 0x7FF);
+        unsigned long long X = 0ull;
+        if (E != 0) {
+          const unsigned long long mant = ((unsigned long long)bits[e] & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+          const int sh = E - emax + 3;                  // <= 3: X < 2^56
+          X = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
+        }
+        const bool neg = bits[e] < 0;
+#pragma unroll
+        for (int i = 0; i < SDIG; ++i) {
+          const uint32_t d = (uint32_t)(X >> (48 - 8 * i)) & 0xFFu;
+          w[i][e >> 1] |= digit_bf16(d, neg) << (16 * (e & 1));
+        }
+      }
+      const uint32_t off = (uint32_t)(rs >> 3) * SSBO + (uint32_t)half * 128u + (uint32_t)(rs & 7) * 16u;
+#pragma unroll
+      for (int i = 0; i < SDIG; ++i)
+        *reinterpret_cast<uint4*>(sp.slices + i * slice_bytes + off) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+      if (half == 0) sp.rexp[rs] = emax;
+    }
+  }
+}
+
+// Work unit u of a trailing update with R rows (row slots 0..R-1; column slots 0..R-2): a 128-row MMA
+// tile starting at slot ta that owns the output rows [lo, hi), and a block of SBLK columns from cb.
+__device__ __forceinline__ bool split_unit(int u, int R, int& ta, int& lo, int& hi, int& cb) {
+  const int R8 = (R + 7) & ~7;
+  for (int l = 0; l < R; l += 128) {
+    const int h = min(R, l + 128);
+    const int nb = (min(h, R - 1) + SBLK - 1) / SBLK;
+    if (u < nb) {
+      lo = l;
+      hi = h;
+      ta = min(l, max(0, R8 - 128));
+      cb = u * SBLK;
+      return true;
+    }
+    u -= nb;
+  }
+  return false;
+}
+
+__device__ __forceinline__ int split_units(int R) {
+  int U = 0;
+  for (int l = 0; l < R; l += 128) U += (min(min(R, l + 128), R - 1) + SBLK - 1) / SBLK;
+  return U;
+}
+
+// One thread issues the 28 digit-pair MMAs of a unit into accumulator set d (D_t at column (t-2) SBLK).
+__device__ __forceinline__ void split_mma(uint32_t d, uint32_t sl, uint32_t slice_bytes, int ta, int cb) {
+  const uint32_t idesc = tc::idesc_bf16_f32(128, SBLK);
+#pragma unroll
+  for (int t = 2; t <= SDIG + 1; ++t) {
+#pragma unroll
+    for (int i = 1; i < t; ++i) {
+      const int j = t - i;
+      const uint64_t ad = tc::smem_desc(sl + (uint32_t)(i - 1) * slice_bytes + (uint32_t)(ta >> 3) * SSBO, SSBO);
+      const uint64_t bd = tc::smem_desc(sl + (uint32_t)(j - 1) * slice_bytes + (uint32_t)(cb >> 3) * SSBO, SSBO);
+      tc::mma_bf16(d + (uint32_t)((t - 2) * SBLK), ad, bd, idesc, i > 1 ? 1u : 0u);
+    }
+  }
+}
+
+__device__ __forceinline__ long long split_digit_sum(const uint32_t (&v)[SDIG][8], int e) {
+  long long acc = 0;
+#pragma unroll
+  for (int t = 0; t < SDIG; ++t) {
+    const long long dt = (long long)__float2int_rz(__uint_as_float(v[t][e]));
+    const int sh = 40 - 8 * t;                       // D_(t+2) 2^(56 - 8 (t+2))
+    acc += sh >= 0 ? (dt << sh) : (dt >> -sh);
+  }
+  return acc;
+}
+
+// A[s1 + rs][s1 + cs] -= L21 L21^T for the unit's entries (rows [lo, hi), lower triangle, columns < n).
+// Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile rows) and half (w / 4) of the block's columns.
+__device__ void split_combine(double* A, int s1, int R, int lo, int hi, int ta, int cb, uint32_t d, const int* rexp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lq = warp & 3, half = warp >> 2;
+  const int rs = ta + lq * 32 + lane;
+  const bool row_ok = rs >= lo && rs < hi;
+  const int Er = row_ok ? rexp[rs] : 0;
+  double* Arow = A + rowoff(row_ok ? s1 + rs : 0) + s1;
+#pragma unroll
+  for (int cg = 0; cg < 2; ++cg) {
+    const int c0 = half * 16 + cg * 8;
+    uint32_t v[SDIG][8];
+#pragma unroll
+    for (int t = 0; t < SDIG; ++t)
+      tc::tmem_ld_x8(d + ((uint32_t)(lq * 32) << 16) + (uint32_t)(t * SBLK + c0), v[t]);
+    tc::tmem_wait_ld();
+    if (row_ok) {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int cs = cb + c0 + e;
+        if (cs <= rs && cs < R - 1) {
+          const long long acc = split_digit_sum(v, e);
+          const int ex = Er + rexp[cs] - 1077;        // biased exponent of 2^(e_r + e_c - 56)
+          if (acc != 0 && ex >= 1) Arow[cs] = fma(-(double)acc, __longlong_as_double((long long)ex << 52), Arow[cs]);
+        }
+      }
+    }
+  }
+}
+
+// Factorise the 16-column panel kb..kb+kw-1 (rows kb..n, already updated by every earlier panel) in FP64:
+// two blocks of NB columns, the second updated by the first within the panel. Returns false on a bad pivot.
+__device__ bool panel16(double* A, int n, int kb, int kw, double* P, double* s_dinv, int* s_flag) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int k0 = min(NB, kw);
+  if (warp == 0) panel_diag(A, kb, k0, P, s_dinv, s_flag);
+  __syncthreads();
+  if (*s_flag) return false;
+  panel_trsm(A, n, kb, k0, P, s_dinv, tid, NT);
+  __syncthreads();
+  if (kw > NB) {
+    const int s0 = kb + NB, k1 = kw - NB, rows = n + 1 - s0;
+    for (int item = tid; item < rows * k1; item += NT) {
+      const int r = s0 + item / k1, c = s0 + item % k1;
+      if (c > r) continue;
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < NB; ++k) acc = fma(P[r * PSTR + k], P[c * PSTR + k], acc);
+      A[rowoff(r) + c] -= acc;
+    }
+    __syncthreads();
+    if (warp == 0) panel_diag(A, s0, k1, P, s_dinv, s_flag);
+    __syncthreads();
+    if (*s_flag) return false;
+    panel_trsm(A, n, s0, k1, P, s_dinv, tid, NT);
+    __syncthreads();
+  }
+  return true;
+}
+
+// Split factorisation of the packed (n+1) x (n+1) augmented matrix (rows 0..n-1: H, row n: g), with
+// the forward substitution folded in as in cholesky_aug. Returns false on a bad pivot (*s_flag set) or
+// when a bounded tensor-core wait ran out (*s_abort set).
+__device__ bool cholesky_split(double* A, int n, double* s_P, double* s_dinv, int* s_flag, const SplitSmem& sp,
+                               TcState& t, int* s_abort) {
+  const int tid = threadIdx.x;
+  const uint32_t sl = tc::smem_u32(sp.slices);
+  const uint32_t slice_bytes = (uint32_t)sp.rows * 32u;
+  if (tid == 0) *s_flag = 0;
+  __syncthreads();
+  for (int kb = 0; kb < n; kb += SNB) {
+    const int kw = min(SNB, n - kb);
+    if (!panel16(A, n, kb, kw, s_P, s_dinv, s_flag)) return false;
+    const int s1 = kb + kw;
+    if (s1 >= n) break;                              // only the gradient row is below: nothing to update
+    const int R = n + 1 - s1;
+    split_panel(A, n, kb, kw, s1, sp);
+    tc::fence_proxy_async();
+    __syncthreads();
+    const int U = split_units(R);
+    auto issue = [&](int u) {
+      const int b = u % sp.nbuf;
+      if (tid == 0) {
+        int ta, lo, hi, cb;
+        split_unit(u, R, ta, lo, hi, cb);
+        tc::fence_after_sync();
+        split_mma(t.tmem + (uint32_t)(b * SPLIT_BUF_COLS), sl, slice_bytes, ta, cb);
+        tc::mma_commit(&t.bars[3 + b]);
+      }
+      t.pend[3 + b] = true;
+    };
+    issue(0);
+    for (int u = 0; u < U; ++u) {
+      const int b = u % sp.nbuf;
+      if (sp.nbuf == 2 && u + 1 < U) issue(u + 1);
+      if (!tc_wait(t, 3 + b)) *s_abort = 1;
+      tc::fence_after_sync();
+      int ta, lo, hi, cb;
+      split_unit(u, R, ta, lo, hi, cb);
+      split_combine(A, s1, R, lo, hi, ta, cb, t.tmem + (uint32_t)(b * SPLIT_BUF_COLS), sp.rexp);
+      tc::fence_before_sync();
+      __syncthreads();
+      if (*s_abort) return false;
+      if (sp.nbuf == 1 && u + 1 < U) issue(u + 1);
+    }
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------------------------------------
 // 1-D Lax-Friedrichs update folded into the Newton launch (Algorithm 1, the moment update; App. A).
 // With nu = dx / (2 dt) the update of cell j,
 //   u_hat_j = sum_k w_k [u_j - dt/dx (g(u_j, u_r) - g(u_l, u_j))] phi(xi_k),
@@ -651,6 +902,14 @@ __device__ void lf_fold(const NewtonArgs& a, int k, double* s_ia, double* s_ib, 
     }
     __syncthreads();
   }
+}
+
+// Duration of one tensor-core Hessian phase (entry of hessian_tc to its final block barrier, as seen by
+// thread 0), added to the step counters: the in-phase tensor-pipe rate of row (b) is its tensor flops
+// over this time.
+__device__ __forceinline__ void hessian_timed(StepScalars* sc, uint64_t t0) {
+  atomicAdd(&sc->hessian_ns, (unsigned long long)(tc::globaltimer() - t0));
+  atomicAdd(&sc->hessian_count, 1ULL);
 }
 
 template <int ENT, int PHYS, int M, bool H_SMEM, bool MIXED, bool F32F>
@@ -869,6 +1128,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
         float* Hf = reinterpret_cast<float*>(s_H);
         float* Pf = reinterpret_cast<float*>(s_P);
         float* dinvf = reinterpret_cast<float*>(s_dinv);
+        const uint64_t th0 = tid == 0 ? tc::globaltimer() : 0;
         if (!hessian_tc<M, float>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), Hf, sA, sB, tcs, &s_abort)) {
           if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
           st = ST_TIMEOUT;
@@ -876,6 +1136,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
           break;
         }
         __syncthreads();
+        if (tid == 0) hessian_timed(a.sc, th0);
         for (int r = tid; r < NM; r += NT) Hf[rowoff(NM) + r] = (float)s_g[r];
         __syncthreads();
         if (cholesky_aug<float>(Hf, NM, Pf, dinvf, &s_flag)) {
@@ -903,12 +1164,14 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       } else {
       // (b) Hessian, packed lower triangle, row index r = i*M + a
       if (MIXED) {
+        const uint64_t th0 = tid == 0 ? tc::globaltimer() : 0;
         if (!hessian_tc<M, double>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, tcs, &s_abort)) {
           if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
           st = ST_TIMEOUT;
           stop = true;
           break;
         }
+        if (tid == 0) hessian_timed(a.sc, th0);
       } else {
         hessian_fp64<M>(a, N, Qc, s_wJ, s_H);
       }
@@ -1050,13 +1313,21 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
   }
 
   if (MIXED) {
-    // drain whatever is still outstanding (only after a timeout), then free tensor memory
+    // drain whatever is still outstanding (only after a timeout), then free tensor memory. If a drain
+    // wait runs out too, an MMA or bulk copy may still write to this CTA's tensor or shared memory:
+    // the tensor memory is then left allocated and the context is marked unusable (sticky flag read
+    // by the host, which launches nothing more into it).
+    bool drained = true;
     for (int k = 0; k < 3; ++k)
-      if (tcs.pend[k]) tc_wait(tcs, k);
+      if (tcs.pend[k]) drained = tc_wait(tcs, k) && drained;
     tc::fence_before_sync();
-    __syncthreads();
+    drained = __syncthreads_and(drained);
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tcs.tmem, (uint32_t)a.mx.tmem_cols);
+    if (!drained) {
+      if (tid == 0) atomicExch(&a.sc->tc_stuck, 1);
+    } else if (warp == 0) {
+      tc::tmem_dealloc(tcs.tmem, (uint32_t)a.mx.tmem_cols);
+    }
   }
 }
 

@@ -13,11 +13,12 @@
 // holds it until the process exits. All calls share it and it keeps the last call's contents;
 // the counters that must start at zero are cleared at the start of every call. Calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on the scratch and must
-// not be issued concurrently. The first call on a device looks up the array's device address with
-// cudaGetSymbolAddress; that first call should come before any stream capture.
+// not be issued concurrently. Every call looks up the array's device address on the current device
+// with cudaGetSymbolAddress (cheap next to the table upload), so the address is never stale, also
+// after a cudaDeviceReset; the first call on a device also loads the library's kernels there, so it
+// should come before any stream capture.
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -26,9 +27,6 @@
 static __device__ __align__(256) unsigned char g_noalloc_scratch[IPM_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-
-std::mutex g_mu;
-void* g_scratch_dev[256] = {nullptr};   // device address of g_noalloc_scratch, per device ordinal
 
 ipm_status noalloc_fail(ipm_status s, const std::string& msg) {
   ipm::set_global_error(msg);
@@ -64,8 +62,11 @@ extern "C" ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, con
   } else {
     return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: problem kind must be Burgers 1-D or Euler 1-D");
   }
-  const int entk = entropy->kind == IPM_ENTROPY_QUADRATIC ? ENT_QUADRATIC
-                   : (entropy->kind == IPM_ENTROPY_BOUNDED_BARRIER ? ENT_BARRIER : ENT_EULER);
+  int entk;
+  if (entropy->kind == IPM_ENTROPY_QUADRATIC) entk = ENT_QUADRATIC;
+  else if (entropy->kind == IPM_ENTROPY_BOUNDED_BARRIER) entk = ENT_BARRIER;
+  else if (entropy->kind == IPM_ENTROPY_EULER) entk = ENT_EULER;
+  else return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: unknown entropy kind");
   if (!(entk == ENT_QUADRATIC || (entk == ENT_BARRIER && phys == PHYS_BURGERS) ||
         (entk == ENT_EULER && phys != PHYS_BURGERS)))
     return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: entropy does not match the problem");
@@ -82,30 +83,21 @@ extern "C" ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, con
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(IPM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= 256) return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: device ordinal out of range");
+  // The array's name is a host-side stand-in in host code; the kernels get its device address on the
+  // current device, looked up on every call.
   void* base = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_dev[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        ipm::set_global_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        return IPM_ECUDA;
-      }
-      g_scratch_dev[dev] = p;
-    }
-    base = g_scratch_dev[dev];
-  }
+  e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+  if (e != cudaSuccess) return noalloc_fail(IPM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
 
-  cudaDeviceProp prop;
-  e = cudaGetDeviceProperties(&prop, dev);
-  if (e != cudaSuccess) return noalloc_fail(IPM_ECUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
+  int smem_optin = 0, n_sm = 0;
+  e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return noalloc_fail(IPM_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
   const NewtonSmem sm_full = newton_smem(N, m, Q, true, nullptr);
   const NewtonSmem sm_lean = newton_smem(N, m, Q, false, nullptr);
-  if (sm_lean.bytes > (size_t)prop.sharedMemPerBlockOptin)
+  if (sm_lean.bytes > (size_t)smem_optin)
     return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: N*m and Q too large for one CTA");
-  const bool h_in_smem = sm_full.bytes <= (size_t)prop.sharedMemPerBlockOptin;
+  const bool h_in_smem = sm_full.bytes <= (size_t)smem_optin;
   const NewtonSmem sm = h_in_smem ? sm_full : sm_lean;
   const size_t smem = sm.bytes;
   int bps = 0;
@@ -128,7 +120,7 @@ extern "C" ipm_status ipm_dual_solve_noalloc(int problem_kind, double gamma, con
   const size_t o_cells = take((size_t)n_cells * sizeof(int));
   if (off > IPM_NOALLOC_SCRATCH_BYTES)
     return noalloc_fail(IPM_EINVAL, "ipm_dual_solve_noalloc: tables and cell list exceed the scratch size");
-  int grid = std::max(1, std::min(n_cells, bps * prop.multiProcessorCount));
+  int grid = std::max(1, std::min(n_cells, bps * n_sm));
   const size_t hslot = h_in_smem ? 0 : packed_aug_count(NM) * sizeof(double);
   size_t o_h = off;
   if (!h_in_smem) {

@@ -338,6 +338,10 @@ __global__ void __launch_bounds__(256) k_finalize(StepScalars* sc, const int* it
     sc->factorizations = 0;
     sc->last_cached_checks = sc->cached_checks;
     sc->cached_checks = 0;
+    sc->last_hessian_ns = sc->hessian_ns;
+    sc->hessian_ns = 0;
+    sc->last_hessian_count = sc->hessian_count;
+    sc->hessian_count = 0;
     sc->work_counter = 0;
     sc->update_counter = 0;
     sc->smax_bits = sc->fixed_smax_bits;

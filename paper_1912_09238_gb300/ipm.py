@@ -80,7 +80,8 @@ class ipm_stats(ctypes.Structure):
                 ("first_failed_cell", ctypes.c_int32), ("first_status", ctypes.c_int32),
                 ("dt", ctypes.c_double), ("t", ctypes.c_double), ("residual", ctypes.c_double),
                 ("steps", ctypes.c_int64), ("tc_timeouts", ctypes.c_int32), ("factorizations", ctypes.c_int64),
-                ("fp32_fallbacks", ctypes.c_int32), ("cached_checks", ctypes.c_int64)]
+                ("fp32_fallbacks", ctypes.c_int32), ("cached_checks", ctypes.c_int64),
+                ("hessian_ns", ctypes.c_int64), ("hessian_count", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -282,9 +283,9 @@ def make_problem(kind, nx, x_lo, x_hi, bc=("outflow", "outflow"), cfl=0.5, t_end
 
 def make_problem_2d(nx, ny, x_lo, x_hi, y_lo, y_hi, sides=("periodic",) * 4, mesh="cartesian", ramp_x0=0.0,
                     ramp_deg=0.0, cfl=0.4, t_end=0.0, gamma=1.4, ic="freestream", param=(0, 0, 0, 0), dparam=None,
-                    x0=0.5, left=(0, 0, 0, 0), dleft=None, right=(0, 0, 0, 0), dright=None):
+                    x0=0.5, left=(0, 0, 0, 0), dleft=None, right=(0, 0, 0, 0), dright=None, dx0=(0, 0, 0)):
     """2-D Euler problem; sides = (left, right, bottom, top)."""
-    pr = make_problem("euler2d", nx, x_lo, x_hi, bc=sides[:2], cfl=cfl, t_end=t_end, gamma=gamma, x0=x0,
+    pr = make_problem("euler2d", nx, x_lo, x_hi, bc=sides[:2], cfl=cfl, t_end=t_end, gamma=gamma, x0=x0, dx0=dx0,
                       left=left, dleft=dleft, right=right, dright=dright)
     pr.ny = ny
     pr.y_lo, pr.y_hi = y_lo, y_hi

@@ -58,6 +58,19 @@ XRIEMANN_2D = dict(
     dright=((0.0, 0.0, 0.0),) * 4, param=(0.0, 0.0, 0.0, 0.0), dparam=None, newton_tol=1e-10,
 )
 
+# The Sod tube of SOD_1D under the literal reading of "56 moments x 4": the four-variable 2-D Euler system
+# (rho, rho v_1, rho v_2, E) with v_2 = 0 on a 2000 x 1 Cartesian mesh (square cells, periodic in y, outflow
+# in x), the same uncertain data (rho_L, p_L, interface), total degree 5 in 3 dims (N = 56 x 4 variables),
+# 6^3 Gauss nodes, local Lax-Friedrichs faces, CFL 0.5, to t_end = 0.14.
+SOD_1D_AS_2D = dict(
+    name="sod1d_as_2d", kind="euler2d", nx=2000, ny=1, x_lo=0.0, x_hi=1.0, y_lo=0.0, y_hi=1.0 / 2000,
+    mesh="cartesian", ramp_x0=0.0, ramp_deg=0.0, sides=("outflow", "outflow", "periodic", "periodic"), cfl=0.5,
+    t_end=0.14, gamma=1.4, p=3, M=5, nq=6, entropy="euler", ic="riemann", x0=0.5, dx0=(0.0, 0.0, 0.05),
+    left=(1.0, 0.0, 0.0, 1.0), dleft=((0.1, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.1, 0.0)),
+    right=(0.125, 0.0, 0.0, 0.1), dright=((0.0, 0.0, 0.0),) * 4, param=(0.0, 0.0, 0.0, 0.0), dparam=None,
+    newton_tol=1e-10,
+)
+
 
 def variant(base: dict, **changes) -> dict:
     """Copy of a workload with some parameters changed (smaller meshes for parity cases)."""
@@ -111,3 +124,53 @@ def serving_requests(n: int, seed: int = 1234, rate_hz: float = 0.0, steps: int 
         w["steps"] = steps
         out.append((t, w))
     return out
+
+
+# ------------------------------------------------------------------------------------------------
+# Library objects for a workload dictionary (the CUDA path only; these import nothing but the binding).
+
+def problem(w: dict):
+    """The ipm_problem of a workload dictionary (1-D or 2-D)."""
+    from . import ipm
+    if w["kind"] == "euler2d":
+        return ipm.make_problem_2d(w["nx"], w["ny"], w["x_lo"], w["x_hi"], w["y_lo"], w["y_hi"], sides=w["sides"],
+                                   mesh=w["mesh"], ramp_x0=w["ramp_x0"], ramp_deg=w["ramp_deg"], cfl=w["cfl"],
+                                   t_end=w["t_end"], gamma=w["gamma"], ic=w["ic"], param=w["param"],
+                                   dparam=w.get("dparam"), x0=w.get("x0", 0.5), left=w.get("left", (0, 0, 0, 0)),
+                                   dleft=w.get("dleft"), right=w.get("right", (0, 0, 0, 0)), dright=w.get("dright"),
+                                   dx0=w.get("dx0", (0.0, 0.0, 0.0)))
+    return ipm.make_problem(w["kind"], w["nx"], w["x_lo"], w["x_hi"], bc=w["bc"], cfl=w["cfl"], t_end=w["t_end"],
+                            gamma=w["gamma"], x0=w["x0"], dx0=w["dx0"], left=w["left"], dleft=w.get("dleft"),
+                            right=w["right"], dright=w.get("dright"))
+
+
+def quadrature(w: dict):
+    """The workload's rule: tensor Gauss with nq nodes per dimension, or nested Clenshaw-Curtis rules
+    when the workload names cc_levels."""
+    from . import ipm
+    return ipm.quadrature(w["nq"], cc_levels=w.get("cc_levels"))
+
+
+def context(w: dict, precision: str = "fp64", tau=None, **opt):
+    """An ipm.Context holding the workload's initial state on the current device."""
+    from . import ipm
+    o = ipm.default_options(precision, newton_tol=tau if tau is not None else w.get("newton_tol", 1e-10), **opt)
+    if w["kind"] == "euler2d":
+        return ipm.Context(problem(w), w["p"], w["M"], quadrature(w), w["entropy"], 0.0, 0.0, o)
+    return ipm.Context(problem(w), w["p"], w["M"], quadrature(w), w["entropy"], w.get("u_minus", 0.0),
+                       w.get("u_plus", 0.0), o)
+
+
+def collocation(w: dict, steady_tol: float = 0.0):
+    """Stochastic Collocation of a workload on the GPU (ipm_sc_*), on the workload's quadrature."""
+    from . import ipm
+    return ipm.Collocation(problem(w), w["p"], w["M"], quadrature(w), steady_tol)
+
+
+def request(w: dict, precision: str = "mixed", max_steps=None):
+    """An ipm_request for the serving API (1-D workloads); max_steps defaults to w["steps"] when present."""
+    from . import ipm
+    o = ipm.default_options(precision, newton_tol=w.get("newton_tol", 1e-10))
+    steps = max_steps if max_steps is not None else w.get("steps", 2 ** 62)
+    return ipm.make_request(problem(w), w["p"], w["M"], w["nq"], w["entropy"], w.get("u_minus", 0.0),
+                            w.get("u_plus", 0.0), o, max_steps=steps)

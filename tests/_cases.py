@@ -6,6 +6,11 @@ import numpy as np
 
 from oracle import basis, dual, entropy, physics
 from oracle import scheme1d as s1
+# the CUDA side of a workload: the library's own helpers (they import nothing from oracle/)
+from paper_1912_09238_gb300.workloads import collocation as gpu_collocation  # noqa: F401
+from paper_1912_09238_gb300.workloads import context as gpu_context  # noqa: F401
+from paper_1912_09238_gb300.workloads import problem as gpu_problem  # noqa: F401
+from paper_1912_09238_gb300.workloads import quadrature as gpu_quadrature  # noqa: F401
 
 
 def _affine(vals, dvals, nvar):
@@ -67,54 +72,10 @@ def oracle_problem_2d(w, tau=None):
                         y_mid=0.5 * (w["y_lo"] + w["y_hi"]), damp=dp[0], dphase=dp[1], dhalf_width=dp[2])
     else:
         ic = s2.RiemannXIC(left=tuple(w["left"]), right=tuple(w["right"]), x0=w["x0"],
-                           dleft=w.get("dleft") or ((0.0, 0.0, 0.0),) * 4, dright=w.get("dright") or ((0.0, 0.0, 0.0),) * 4)
+                           dleft=w.get("dleft") or ((0.0, 0.0, 0.0),) * 4, dright=w.get("dright") or ((0.0, 0.0, 0.0),) * 4,
+                           dx0=tuple(w.get("dx0", (0.0, 0.0, 0.0))))
     return s2.Problem2D(phys=phys, ent=ent, space=sp, mesh=mesh, ic=ic, sides=tuple(w["sides"]), cfl=w["cfl"],
                         t_end=w["t_end"], newton=dual.NewtonOptions(tau=tau if tau is not None else w.get("newton_tol", 1e-10)))
-
-
-def gpu_problem(w):
-    """The ipm_problem of a workload dictionary."""
-    from paper_1912_09238_gb300 import ipm
-    if w["kind"] == "euler2d":
-        return ipm.make_problem_2d(w["nx"], w["ny"], w["x_lo"], w["x_hi"], w["y_lo"], w["y_hi"], sides=w["sides"],
-                                   mesh=w["mesh"], ramp_x0=w["ramp_x0"], ramp_deg=w["ramp_deg"], cfl=w["cfl"],
-                                   t_end=w["t_end"], gamma=w["gamma"], ic=w["ic"], param=w["param"],
-                                   dparam=w.get("dparam"), x0=w.get("x0", 0.5), left=w.get("left", (0, 0, 0, 0)),
-                                   dleft=w.get("dleft"), right=w.get("right", (0, 0, 0, 0)), dright=w.get("dright"))
-    return ipm.make_problem(w["kind"], w["nx"], w["x_lo"], w["x_hi"], bc=w["bc"], cfl=w["cfl"], t_end=w["t_end"],
-                            gamma=w["gamma"], x0=w["x0"], dx0=w["dx0"], left=w["left"], dleft=w.get("dleft"),
-                            right=w["right"], dright=w.get("dright"))
-
-
-def gpu_quadrature(w):
-    """The workload's rule: tensor Gauss with nq nodes per dimension, or nested Clenshaw-Curtis rules
-    when the workload names cc_levels."""
-    from paper_1912_09238_gb300 import ipm
-    return ipm.quadrature(w["nq"], cc_levels=w.get("cc_levels"))
-
-
-def gpu_collocation(w, steady_tol=0.0):
-    """Stochastic Collocation of a workload on the GPU (ipm_sc_*), on the workload's quadrature."""
-    from paper_1912_09238_gb300 import ipm
-    return ipm.Collocation(gpu_problem(w), w["p"], w["M"], gpu_quadrature(w), steady_tol)
-
-
-def gpu_context(w, precision="fp64", tau=None, **opt):
-    from paper_1912_09238_gb300 import ipm
-    if w["kind"] == "euler2d":
-        pr = ipm.make_problem_2d(w["nx"], w["ny"], w["x_lo"], w["x_hi"], w["y_lo"], w["y_hi"], sides=w["sides"],
-                                 mesh=w["mesh"], ramp_x0=w["ramp_x0"], ramp_deg=w["ramp_deg"], cfl=w["cfl"],
-                                 t_end=w["t_end"], gamma=w["gamma"], ic=w["ic"], param=w["param"],
-                                 dparam=w.get("dparam"), x0=w.get("x0", 0.5), left=w.get("left", (0, 0, 0, 0)),
-                                 dleft=w.get("dleft"), right=w.get("right", (0, 0, 0, 0)), dright=w.get("dright"))
-        o = ipm.default_options(precision, newton_tol=tau if tau is not None else w.get("newton_tol", 1e-10), **opt)
-        return ipm.Context(pr, w["p"], w["M"], gpu_quadrature(w), w["entropy"], 0.0, 0.0, o)
-    pr = ipm.make_problem(w["kind"], w["nx"], w["x_lo"], w["x_hi"], bc=w["bc"], cfl=w["cfl"], t_end=w["t_end"],
-                          gamma=w["gamma"], x0=w["x0"], dx0=w["dx0"], left=w["left"], dleft=w.get("dleft"),
-                          right=w["right"], dright=w.get("dright"))
-    o = ipm.default_options(precision, newton_tol=tau if tau is not None else w.get("newton_tol", 1e-10), **opt)
-    return ipm.Context(pr, w["p"], w["M"], gpu_quadrature(w), w["entropy"], w.get("u_minus", 0.0), w.get("u_plus", 0.0),
-                       o)
 
 
 def rel_err(a, b):

@@ -103,3 +103,22 @@ def test_option_defaults_and_validation_without_a_gpu(libipm):
         st = libipm.ipm_footprint(ctypes.byref(pr), ctypes.byref(basis), ctypes.byref(quad), ctypes.byref(ent),
                                   ctypes.byref(ob), ctypes.byref(b))
         assert st == 1, (bad, st)
+
+
+def test_noalloc_rejects_unknown_kinds_before_device_work(libipm):
+    """ipm_dual_solve_noalloc validates the problem and entropy kinds before touching the device: an
+    unknown entropy kind on an Euler problem, or an unknown problem kind, is IPM_EINVAL (the buffer
+    arguments are never dereferenced on this path)."""
+    import ctypes
+    from paper_1912_09238_gb300 import ipm
+    b = ipm.ipm_basis(3, 2)
+    q = ipm.ipm_quadrature(n_per_dim=3)
+    o = ipm.default_options("fp64")
+    s = ipm.ipm_stats()
+    fake = ctypes.c_void_p(256)          # never dereferenced: the call returns during validation
+    for kind, ent in ((ipm.PROBLEM["euler1d"], 7), (ipm.PROBLEM["euler1d"], -1), (ipm.PROBLEM["euler2d"], 2), (9, 2)):
+        e = ipm.ipm_entropy(ent, 0.0, 0.0)
+        st = libipm.ipm_dual_solve_noalloc(kind, 1.4, ctypes.byref(b), ctypes.byref(q), ctypes.byref(e),
+                                           ctypes.byref(o), 4, fake, fake, fake, fake, fake, None, ctypes.byref(s))
+        assert st == 1, (kind, ent, st)
+        assert b"kind" in libipm.ipm_last_error(None)

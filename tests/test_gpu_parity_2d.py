@@ -19,6 +19,10 @@ TOL_MIXED = 1e-6
 RAMP = workloads.variant(workloads.RAMP_2D, nx=16, ny=8, M=2, nq=3)
 KH = workloads.variant(workloads.KH_2D, nx=12, ny=12, M=2, nq=3)
 XR = workloads.XRIEMANN_2D
+# the Sod tube under the 4-variable reading (one row of cells, uncertain interface), reduced and at the
+# workload's own degree (N m = 224: the Hessian lives in the global workspace)
+SOD4 = workloads.variant(workloads.SOD_1D_AS_2D, nx=40, y_hi=1.0 / 40, M=2, nq=3)
+SOD4_FULL_DEGREE = workloads.variant(workloads.SOD_1D_AS_2D, nx=8, y_hi=1.0 / 8)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -39,7 +43,7 @@ def _interior(a, w):
     return a.reshape(w["ny"] + 2, w["nx"] + 2, *a.shape[1:])[1:-1, 1:-1]
 
 
-@pytest.mark.parametrize("w", [RAMP, KH, XR], ids=["ramp", "shear", "xriemann"])
+@pytest.mark.parametrize("w", [RAMP, KH, XR, SOD4], ids=["ramp", "shear", "xriemann", "sod_m4"])
 def test_initial_projection_and_ghost_duals(w):
     prob = oracle_problem_2d(w)
     st = s2.initial_state(prob)
@@ -53,7 +57,8 @@ def test_initial_projection_and_ghost_duals(w):
         assert rel_err(lam[-1, 1:-1], st.lam[-1, 1:-1]) < TOL
 
 
-@pytest.mark.parametrize("w", [RAMP, KH, XR], ids=["ramp", "shear", "xriemann"])
+@pytest.mark.parametrize("w", [RAMP, KH, XR, SOD4, SOD4_FULL_DEGREE],
+                         ids=["ramp", "shear", "xriemann", "sod_m4", "sod_m4_degree5"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_algorithm1_steps(w, precision):
     prob = oracle_problem_2d(w)

@@ -185,6 +185,44 @@ def test_x_riemann_problem_reduces_to_the_1d_scheme():
         assert np.abs(st2.lam[row, 1:-1, :, 2]).max() < 1e-10
 
 
+def test_x_riemann_with_uncertain_interface_reduces_to_the_1d_scheme():
+    """The Sod data of the 1-D workload in 3 uncertain dims (rho_L, p_L and the interface x0 = 0.5 +
+    0.05 xi_3) on a one-row mesh, periodic in y, as the 4-variable 2-D system: it equals the 1-D scheme with
+    the same data and flux (the per-node cell averages take the node's interface position on both sides),
+    and the y-momentum stays zero. A dropped interface term would leave the xi_3-moments zero."""
+    nx = 24
+    mesh = s2.cartesian_mesh(nx, 1, 0.0, 1.0, 0.0, 1.0 / nx)
+    left, right = (1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1)
+    dleft = ((0.1, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), (0.0, 0.1, 0.0))
+    ic = s2.RiemannXIC(left=left, right=right, x0=0.5, dleft=dleft, dx0=(0.0, 0.0, 0.05))
+    prob2 = _problem(mesh, ic, ("outflow", "outflow", "periodic", "periodic"), p=3, M=2, nq=3, cfl=0.5)
+    sp = prob2.space
+    E1 = entropy.Euler(GAMMA, 1)
+
+    def state(prim, d):
+        def f(xi):
+            pr = [prim[k] + xi @ np.asarray(d[k])[:xi.shape[1]] for k in (0, 1, 3)]
+            return E1.conserved(pr[0], pr[1][:, None], pr[2])
+        return f
+    prob1 = s1.Problem1D(phys=physics.Euler(GAMMA, 1), ent=E1, space=sp, nx=nx, x_lo=0.0, x_hi=1.0,
+                         ic=s1.RiemannIC(state(left, dleft), state(right, ((0, 0, 0),) * 4),
+                                         lambda xi: 0.5 + 0.05 * xi[:, 2]),
+                         bc="outflow", cfl=0.5, flux="rusanov")
+    prob1.newton = dual.NewtonOptions(tau=1e-10)
+    st2 = s2.initial_state(prob2)
+    st1 = s1.initial_state(prob1)
+    # the interface moves with xi_3: the first-order xi_3 moment of the density is nonzero at the jump
+    i3 = [k for k, a in enumerate(sp.indices) if tuple(a) == (0, 0, 1)][0]
+    assert np.abs(st2.uhat[1, 1:-1, i3, 0]).max() > 1e-3
+    for _ in range(4):
+        st2 = s2.ipm_step(prob2, st2)
+        st1 = s1.ipm_step(prob1, st1)
+        assert abs(st2.last_dt - st1.last_dt) <= 1e-12 * st1.last_dt
+    u2 = st2.uhat[1, 1:-1]
+    assert np.abs(u2[..., [0, 1, 3]] - st1.uhat[1:-1]).max() < 1e-9 * np.abs(st1.uhat).max()
+    assert np.abs(u2[..., 2]).max() < 1e-12
+
+
 def test_oneshot_2d_residual_decreases_to_the_steady_ramp_flow():
     """Algorithm 2 on a coarse ramp mesh: the steady residual falls by orders of magnitude."""
     mesh = s2.ramp_mesh(8, 4, 0.0, 2.0, 1.0, 0.5, 15.0)
