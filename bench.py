@@ -382,6 +382,7 @@ def run_gpu(args):
     if precision == "mixed" and not args.no_fp64_compare:
         comp = {}
         for name, prec, opt in (("fp64_gpu", "fp64", {}), ("mixed_f32_factor", "mixed_f32f", {}),
+                                ("mixed_fma_factor", "mixed", {"factorization": 1}),
                                 ("without_moment_images", "mixed", {"check_cache": 0})):
             r = SodRuns(w, prec, stream, **opt)
             r.ctx.run(20)                                   # warm-up: first time steps, then restored
@@ -415,6 +416,13 @@ def run_gpu(args):
                      "stopping test, line search and update in FP64. Not the headline: the headline keeps the "
                      "factorisation in FP64.")
         line["mixed_f32_factor"] = e
+        e, fin = comp["mixed_fma_factor"]
+        e["max_rel_diff_final_moments_vs_fp64"] = rel_diff(fin, fp64_final)
+        e["speedup_over_fp64"] = e["value"] / fp64_entry["value"]
+        e["what"] = ("the headline's mixed precision with ipm_options.factorization = 1: the Cholesky factorisation "
+                     "with FP64 FMAs on the CUDA cores instead of the split factorisation (16-column FP64 panels, "
+                     "trailing updates as exact digit products on the tensor cores)")
+        line["mixed_fma_factor"] = e
         e, fin = comp["without_moment_images"]
         e["bit_identical_final_moments"] = bool(np.array_equal(fin, head_final))
         e["what"] = ("the headline path with ipm_options.check_cache = 0: every cell evaluates its first "
@@ -924,7 +932,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=1000)
     ap.add_argument("--serving-steps", type=int, default=10)
     ap.add_argument("--serving-slots", type=int, default=32)
-    ap.add_argument("--sequential-requests", type=int, default=200)
+    ap.add_argument("--sequential-requests", type=int, default=300)
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-procs", type=int, default=1, help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -204,6 +204,14 @@ typedef struct {
    * arithmetic, and a cell that meets Eq. tauCrit there skips the reconstruction and the closures.
    * Results are identical to 0 (always evaluate); device memory 2 n_cells N m doubles. */
   int check_cache;
+  /* Cholesky factorisation of the Newton step (row (c), Sec. 3.1), CTA-per-cell kernel: 1 = blocked
+   * right-looking factorisation with FP64 FMAs on the CUDA cores; 2 = split factorisation: the same
+   * factorisation with 16-column panels factorised in FP64 and every trailing update L21 L21^T computed
+   * exactly on the tensor cores from base-256 digit slices of L21 (seven BF16 digits per entry, one
+   * scale per row, FP32 accumulators that hold every diagonal of digit products exactly), combined in
+   * 64-bit integers and applied with one FP64 FMA: FP64-level accuracy; 0 (default) = 2 on
+   * IPM_PREC_MIXED for N*m >= 128, else 1. Not with IPM_PREC_MIXED_F32_FACTOR (IPM_EINVAL). */
+  int factorization;
 } ipm_options;
 
 /* Sizes of a context's arrays. */
@@ -337,6 +345,15 @@ ipm_status ipm_dual_solve(ipm_ctx* ctx, ipm_stats* stats);
  * flat index r = i*m + a; count = n_interior * N*m*(N*m+1)/2. Does not change the state (the nodal
  * states are refreshed at the current duals). Allocates a temporary device buffer; synchronous. */
 ipm_status ipm_assemble_hessian(ipm_ctx* ctx, double* host, size_t count);
+
+/* The Cholesky factor L (H = L L^T, row (c) of Sec. 3.1, Eq. dualIterationFunction's linear solve) of
+ * the Hessian that ipm_assemble_hessian returns at the current duals of every interior cell, computed
+ * by the context's factorisation (ipm_options.factorization; IPM_PREC_MIXED_F32_FACTOR contexts report
+ * their FP64 fallback factorisation). Same layout and count as ipm_assemble_hessian (packed lower
+ * triangles, L's diagonal included); a cell whose Hessian is not numerically SPD leaves its slice
+ * unspecified and is reported by the next ipm_sync_stats. Does not change the state. Allocates a
+ * temporary device buffer; synchronous. */
+ipm_status ipm_factor_hessian(ipm_ctx* ctx, double* host, size_t count);
 
 /* Only the moment update c of every interior cell from the current duals (Eq. momentUpQuadrature)
  * with the given dt > 0 (dt is not computed and t is not advanced); then the boundary condition.

@@ -15,8 +15,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libipm.so")
-SOURCES = ["tables.cpp", "newton.cu", "update.cu", "abi.cu", "noalloc.cu", "server.cpp", "update2d.cu", "newton_warp.cu",
-           "collocation.cu", "newton_warpq.cu"]
+SOURCES = ["tables.cpp", "newton.cu", "newton_m0.cu", "newton_m1.cu", "newton_m2.cu", "newton_m3.cu", "newton_m4.cu",
+           "update.cu", "abi.cu", "noalloc.cu", "server.cpp", "update2d.cu", "newton_warp.cu", "collocation.cu",
+           "newton_warpq.cu"]
 HEADERS = [os.path.join(ROOT, "include", "ipm.h")] + [
     os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))
 ]

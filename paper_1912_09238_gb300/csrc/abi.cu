@@ -66,7 +66,9 @@ struct ipm_ctx {
   int n_fixed_ghosts = 0;
   // launch configuration
   bool mixed = false;          // precision IPM_PREC_MIXED or _MIXED_F32_FACTOR: tensor-core Hessian
-  int newton_mode = 0;         // 0 FP64, 1 mixed, 2 mixed with an FP32 factorisation
+  int newton_mode = 0;         // 0 FP64, 1 mixed, 2 mixed with an FP32 factorisation, 3 mixed + split, 4 FP64 + split
+  bool split = false;          // split factorisation (tensor-core trailing updates) on the CTA-per-cell kernel
+  int s_rows = 0, s_nbuf = 0;  // its digit-slice rows and tensor-memory accumulator sets
   MixedLayout mx;
   NewtonSmem sm;
   float* d_phiT32 = nullptr;
@@ -211,6 +213,10 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.off_h = c->sm.off_h;
   a.off_a = c->sm.off_a;
   a.off_b = c->sm.off_b;
+  a.off_s = c->sm.off_s;
+  a.s_rows = c->s_rows;
+  a.s_nbuf = c->s_nbuf;
+  a.f_dump = nullptr;
   return a;
 }
 
@@ -354,6 +360,47 @@ struct TuneKey {
     return std::tie(kind, entk, N, m, Q, mixed, size_bucket) < std::tie(o.kind, o.entk, o.N, o.m, o.Q, o.mixed, o.size_bucket);
   }
 };
+// Device memory of a context comes from one stream-ordered memory pool per device
+// (cudaMallocFromPoolAsync / cudaFreeAsync on the context's stream). Creating or destroying a context
+// therefore neither calls cudaMalloc nor cudaFree, whose implicit synchronisation would stall the work
+// of every other context on the device (the serving layer creates and destroys contexts while others
+// run). Freed blocks stay in the pool (no release threshold) and serve the next context.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static cudaError_t device_pool(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&p, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = ~0ull;
+    e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return e;
+    }
+    g_pool[dev] = p;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
+// bytes of device memory for the context, ordered on stream s (default: the context's own stream)
+template <typename T>
+static cudaError_t dalloc(const ipm_ctx* c, T** p, size_t bytes, cudaStream_t s = nullptr) {
+  if (!s) s = c->own_stream;
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = device_pool(c->device, &pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), std::max<size_t>(bytes, 1), pool, s);
+}
+
 struct TuneVal {
   int kind;
   float ms[2];
@@ -381,7 +428,7 @@ static ipm_status autotune_newton(ipm_ctx* c) {
   const size_t bytes = (size_t)c->n_cells * c->NM * sizeof(double);
   double* saved = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  IPM_CK(c, cudaMalloc(&saved, bytes));
+  IPM_CK(c, dalloc(c, &saved, bytes, c->stream));
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaMemcpyAsync(saved, c->d_lam, bytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -423,7 +470,7 @@ static ipm_status autotune_newton(ipm_ctx* c) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune.emplace(key, TuneVal{best_kind, {c->tune_ms[0], c->tune_ms[1]}});
   }
-  cudaFree(saved);
+  cudaFreeAsync(saved, c->stream);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   IPM_CK(c, e);
@@ -457,18 +504,21 @@ static void free_ctx(ipm_ctx* c) {
                   c->d_phiT32, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf, c->d_level,
                   c->d_factors, c->d_factor_valid, c->d_level_next, c->d_lev_w, c->d_q_eval,
                   c->d_img, c->d_img_lam, c->d_img_smax, c->d_img_valid, c->d_lf_a, c->d_lf_b, c->d_lf_cnt};
+  cudaStream_t fs = c->stream ? c->stream : c->own_stream;
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, fs);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }
 
+// a device copy of a host vector on the context's own stream (the pageable source is staged before the
+// call returns)
 template <typename T>
-static cudaError_t upload(T** dst, const std::vector<T>& src) {
-  cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(1, src.size()) * sizeof(T));
+static cudaError_t upload(const ipm_ctx* c, T** dst, const std::vector<T>& src) {
+  cudaError_t e = dalloc(c, dst, src.size() * sizeof(T), c->own_stream);
   if (e != cudaSuccess) return e;
   if (src.empty()) return cudaSuccess;
-  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, c->own_stream);
 }
 
 namespace ipm {
@@ -520,6 +570,9 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   if (opt.hessian_reuse < 0 || opt.hessian_reuse > 2 || !(opt.reuse_ratio > 0.0 && opt.reuse_ratio < 1.0))
     return fail(nullptr, IPM_EINVAL, "ipm_init: hessian_reuse must be 0..2 with 0 < reuse_ratio < 1");
   if (opt.check_cache != 0 && opt.check_cache != 1) return fail(nullptr, IPM_EINVAL, "ipm_init: check_cache must be 0 or 1");
+  if (opt.factorization < 0 || opt.factorization > 2) return fail(nullptr, IPM_EINVAL, "ipm_init: factorization must be 0..2");
+  if (opt.factorization == 2 && opt.precision == IPM_PREC_MIXED_F32_FACTOR)
+    return fail(nullptr, IPM_EINVAL, "ipm_init: the split factorisation is an FP64 factorisation; not with IPM_PREC_MIXED_F32_FACTOR");
   c->prob = *problem;
   c->basis = *basis;
   c->quad = *quad;
@@ -611,26 +664,44 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   // launch configuration of the Newton kernel: packed H in shared memory when it fits
   const size_t budget = (size_t)prop.sharedMemPerBlockOptin;
   c->mixed = opt.precision != IPM_PREC_FP64;
-  c->newton_mode = opt.precision == IPM_PREC_MIXED_F32_FACTOR ? 2 : (c->mixed ? 1 : 0);
+  // factorisation: 1 blocked FP64 FMAs; 2 split (FP64-accurate, trailing updates on the tensor cores);
+  // 0 picks the split one on the mixed path for systems of at least SPLIT_AUTO_NM unknowns
+  c->split = opt.factorization == 2 ||
+             (opt.factorization == 0 && opt.precision == IPM_PREC_MIXED && c->NM >= SPLIT_AUTO_NM);
+  c->s_rows = c->split ? split_rows(c->NM) : 0;
+  c->newton_mode = opt.precision == IPM_PREC_MIXED_F32_FACTOR ? 2 : (c->mixed ? (c->split ? 3 : 1) : (c->split ? 4 : 0));
   if (c->mixed) {
     c->h_in_smem = true;
-    c->mx = mixed_layout(c->N, c->m, c->Q, budget, true);
+    c->mx = mixed_layout(c->N, c->m, c->Q, budget, true, c->s_rows);
     if (!c->mx.ok) {
       c->h_in_smem = false;
-      c->mx = mixed_layout(c->N, c->m, c->Q, budget, false);
+      c->mx = mixed_layout(c->N, c->m, c->Q, budget, false, c->s_rows);
+    }
+    if (!c->mx.ok && c->split && opt.factorization == 0) {
+      // the digit slices do not fit next to the tensor-core Hessian: the automatic choice falls back
+      c->split = false;
+      c->s_rows = 0;
+      c->newton_mode = 1;
+      c->h_in_smem = true;
+      c->mx = mixed_layout(c->N, c->m, c->Q, budget, true, 0);
+      if (!c->mx.ok) {
+        c->h_in_smem = false;
+        c->mx = mixed_layout(c->N, c->m, c->Q, budget, false, 0);
+      }
     }
     if (!c->mx.ok) {
         return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for the mixed-precision Newton kernel");
     }
-    c->sm = newton_smem(c->N, c->m, c->Q, c->h_in_smem, &c->mx);
+    c->sm = newton_smem(c->N, c->m, c->Q, c->h_in_smem, &c->mx, c->s_rows);
   } else {
-    const NewtonSmem full = newton_smem(c->N, c->m, c->Q, true, nullptr);
-    const NewtonSmem lean = newton_smem(c->N, c->m, c->Q, false, nullptr);
+    const NewtonSmem full = newton_smem(c->N, c->m, c->Q, true, nullptr, c->s_rows);
+    const NewtonSmem lean = newton_smem(c->N, c->m, c->Q, false, nullptr, c->s_rows);
     if (lean.bytes > budget) {
         return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for one CTA");
     }
     c->h_in_smem = full.bytes <= budget;
     c->sm = c->h_in_smem ? full : lean;
+    if (c->split) c->mx.tmem_cols = SPLIT_TMEM_COLS_ONE;
   }
   c->newton_smem = c->sm.bytes;
   {
@@ -642,7 +713,13 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     if (e != cudaSuccess || bps < 1) {
         return fail(nullptr, IPM_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(e));
     }
-    if (c->mixed) bps = std::min(bps, 512 / c->mx.tmem_cols);
+    if (c->split) {
+      // two accumulator sets (MMAs of the next unit overlap the combine of this one) when one CTA per
+      // SM is resident anyway, or when the Hessian already holds all 512 columns
+      if (bps == 1) c->mx.tmem_cols = 512;
+      c->s_nbuf = c->mx.tmem_cols >= 2 * SPLIT_TMEM_COLS_ONE ? 2 : 1;
+    }
+    if (c->mixed || c->split) bps = std::min(bps, 512 / c->mx.tmem_cols);
     c->newton_grid = std::max(1, std::min(c->n_interior, bps * prop.multiProcessorCount));
   }
   // warp-per-cell variant for small cells: as many warps (cells) per CTA as shared memory allows
@@ -724,6 +801,7 @@ void ipm_default_options(ipm_options* o) {
   o->reuse_ratio = 0.5;
   o->newton_kernel = 0;
   o->check_cache = 1;
+  o->factorization = 0;
 }
 
 const char* ipm_last_error(const ipm_ctx* c) {
@@ -808,43 +886,43 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking), "cudaStreamCreate");
   for (cudaEvent_t& ev : c->ev) CK(cudaEventCreate(&ev), "cudaEventCreate");
   c->stream = c->own_stream;
-  CK(upload(&c->d_Phi, c->tab.Phi), "upload Phi");
-  CK(upload(&c->d_PhiT, c->tab.PhiT), "upload PhiT");
-  CK(upload(&c->d_w, c->tab.w), "upload w");
-  CK(upload(&c->d_nodes, c->tab.nodes), "upload nodes");
-  CK(upload(&c->d_pairs, c->tab.pairs), "upload pairs");
+  CK(upload(c, &c->d_Phi, c->tab.Phi), "upload Phi");
+  CK(upload(c, &c->d_PhiT, c->tab.PhiT), "upload PhiT");
+  CK(upload(c, &c->d_w, c->tab.w), "upload w");
+  CK(upload(c, &c->d_nodes, c->tab.nodes), "upload nodes");
+  CK(upload(c, &c->d_pairs, c->tab.pairs), "upload pairs");
   if (c->mixed) {
-    CK(cudaMalloc(&c->d_phiT32, (size_t)c->N * c->Q * sizeof(float)), "cudaMalloc phiT32");
-    CK(cudaMalloc(&c->d_phi_img, (size_t)c->mx.chunks * c->mx.b_chunk_bytes), "cudaMalloc phi image");
+    CK(dalloc(c, &c->d_phiT32, (size_t)c->N * c->Q * sizeof(float)), "allocate phiT32");
+    CK(dalloc(c, &c->d_phi_img, (size_t)c->mx.chunks * c->mx.b_chunk_bytes), "allocate phi image");
     if (st == IPM_OK)
       CK(launch_phi_images(c->d_PhiT, c->N, c->Q, c->mx, c->d_phiT32, c->d_phi_img, c->stream), "phi images");
   }
   const size_t nstate = (size_t)c->n_cells * c->NM;
-  CK(cudaMalloc(&c->d_uhat, nstate * sizeof(double)), "cudaMalloc uhat");
-  CK(cudaMalloc(&c->d_lam, nstate * sizeof(double)), "cudaMalloc lam");
-  CK(cudaMalloc(&c->d_unode, (size_t)c->n_cells * c->m * c->Q * sizeof(double)), "cudaMalloc unode");
-  CK(cudaMalloc(&c->d_cell_resid, (size_t)c->n_cells * sizeof(double)), "cudaMalloc resid");
-  CK(cudaMalloc(&c->d_iters, (size_t)c->n_cells * sizeof(int)), "cudaMalloc iters");
-  CK(cudaMalloc(&c->d_status, (size_t)c->n_cells * sizeof(int)), "cudaMalloc status");
-  CK(cudaMalloc(&c->d_order, (size_t)c->n_interior * sizeof(int)), "cudaMalloc order");
-  CK(cudaMalloc(&c->d_sc, sizeof(StepScalars)), "cudaMalloc scalars");
-  if (!c->h_in_smem) CK(cudaMalloc(&c->d_hwork, (size_t)c->newton_grid * c->hwork_stride * sizeof(double)), "cudaMalloc hwork");
+  CK(dalloc(c, &c->d_uhat, nstate * sizeof(double)), "allocate uhat");
+  CK(dalloc(c, &c->d_lam, nstate * sizeof(double)), "allocate lam");
+  CK(dalloc(c, &c->d_unode, (size_t)c->n_cells * c->m * c->Q * sizeof(double)), "allocate unode");
+  CK(dalloc(c, &c->d_cell_resid, (size_t)c->n_cells * sizeof(double)), "allocate resid");
+  CK(dalloc(c, &c->d_iters, (size_t)c->n_cells * sizeof(int)), "allocate iters");
+  CK(dalloc(c, &c->d_status, (size_t)c->n_cells * sizeof(int)), "allocate status");
+  CK(dalloc(c, &c->d_order, (size_t)c->n_interior * sizeof(int)), "allocate order");
+  CK(dalloc(c, &c->d_sc, sizeof(StepScalars)), "allocate scalars");
+  if (!c->h_in_smem) CK(dalloc(c, &c->d_hwork, (size_t)c->newton_grid * c->hwork_stride * sizeof(double)), "allocate hwork");
   if (c->factor_stride) {
-    CK(cudaMalloc(&c->d_factors, (size_t)c->n_cells * c->factor_stride * sizeof(double)), "cudaMalloc factors");
-    CK(cudaMalloc(&c->d_factor_valid, (size_t)c->n_cells * sizeof(int)), "cudaMalloc factor flags");
+    CK(dalloc(c, &c->d_factors, (size_t)c->n_cells * c->factor_stride * sizeof(double)), "allocate factors");
+    CK(dalloc(c, &c->d_factor_valid, (size_t)c->n_cells * sizeof(int)), "allocate factor flags");
     if (st == IPM_OK) CK(cudaMemsetAsync(c->d_factor_valid, 0, (size_t)c->n_cells * sizeof(int), c->stream), "memset factor flags");
   }
   if (c->img) {
-    CK(cudaMalloc(&c->d_img, nstate * sizeof(double)), "cudaMalloc moment images");
-    CK(cudaMalloc(&c->d_img_lam, nstate * sizeof(double)), "cudaMalloc image duals");
-    CK(cudaMalloc(&c->d_img_smax, (size_t)c->n_cells * sizeof(double)), "cudaMalloc image speeds");
-    CK(cudaMalloc(&c->d_img_valid, (size_t)c->n_cells * sizeof(int)), "cudaMalloc image flags");
+    CK(dalloc(c, &c->d_img, nstate * sizeof(double)), "allocate moment images");
+    CK(dalloc(c, &c->d_img_lam, nstate * sizeof(double)), "allocate image duals");
+    CK(dalloc(c, &c->d_img_smax, (size_t)c->n_cells * sizeof(double)), "allocate image speeds");
+    CK(dalloc(c, &c->d_img_valid, (size_t)c->n_cells * sizeof(int)), "allocate image flags");
     if (st == IPM_OK) CK(cudaMemsetAsync(c->d_img_valid, 0, (size_t)c->n_cells * sizeof(int), c->stream), "memset image flags");
   }
   if (!c->is2d) {
-    CK(cudaMalloc(&c->d_lf_a, nstate * sizeof(double)), "cudaMalloc folded update terms");
-    CK(cudaMalloc(&c->d_lf_b, nstate * sizeof(double)), "cudaMalloc folded update terms");
-    CK(cudaMalloc(&c->d_lf_cnt, (size_t)c->n_cells * sizeof(int)), "cudaMalloc folded update counts");
+    CK(dalloc(c, &c->d_lf_a, nstate * sizeof(double)), "allocate folded update terms");
+    CK(dalloc(c, &c->d_lf_b, nstate * sizeof(double)), "allocate folded update terms");
+    CK(dalloc(c, &c->d_lf_cnt, (size_t)c->n_cells * sizeof(int)), "allocate folded update counts");
   }
   if (st != IPM_OK) {
     free_ctx(c);
@@ -857,17 +935,17 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   CK(cudaMemsetAsync(c->d_unode, 0, (size_t)c->n_cells * c->m * c->Q * sizeof(double), c->stream), "memset unode");
   // initial data on every cell, then the boundary copies (1-D) or the mesh tables (2-D)
   if (c->is2d) {
-    CK(upload(&c->d_area, c->mesh2d.area), "upload areas");
-    CK(upload(&c->d_xf, c->mesh2d.xf), "upload x faces");
-    CK(upload(&c->d_yf, c->mesh2d.yf), "upload y faces");
+    CK(upload(c, &c->d_area, c->mesh2d.area), "upload areas");
+    CK(upload(c, &c->d_xf, c->mesh2d.xf), "upload x faces");
+    CK(upload(c, &c->d_yf, c->mesh2d.yf), "upload y faces");
     if (st == IPM_OK)
       CK(launch_init2d(c->entk, dev_tables(c), ent_params(c), c->prob, c->d_uhat, c->d_lam, c->stream), "init kernel");
     if (c->n_levels) {
-      CK(cudaMalloc(&c->d_level, (size_t)c->n_cells * sizeof(int)), "cudaMalloc levels");
-      CK(cudaMalloc(&c->d_level_next, (size_t)c->n_cells * sizeof(int)), "cudaMalloc next levels");
+      CK(dalloc(c, &c->d_level, (size_t)c->n_cells * sizeof(int)), "allocate levels");
+      CK(dalloc(c, &c->d_level_next, (size_t)c->n_cells * sizeof(int)), "allocate next levels");
       if (c->level_rules) {
-        CK(upload(&c->d_lev_w, c->lev_w), "upload level weights");
-        CK(upload(&c->d_q_eval, std::vector<int>((size_t)c->n_cells, c->Q)), "upload evaluation nodes");
+        CK(upload(c, &c->d_lev_w, c->lev_w), "upload level weights");
+        CK(upload(c, &c->d_q_eval, std::vector<int>((size_t)c->n_cells, c->Q)), "upload evaluation nodes");
       }
       if (st == IPM_OK)
         CK(launch_init_levels(update2d_args(c, 0.0, false, false), c->n_cells, c->stream), "initial levels");
@@ -906,7 +984,7 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   }
   c->n_fixed_ghosts = (int)ghosts.size();
   if (!ghosts.empty()) {
-    CK(upload(&c->d_ghost_list, ghosts), "upload ghosts");
+    CK(upload(c, &c->d_ghost_list, ghosts), "upload ghosts");
     if (st == IPM_OK) {
       NewtonArgs a = newton_args(c, 0);
       a.cell_list = c->d_ghost_list;
@@ -932,9 +1010,9 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
       h.t = 0.0;
       h.dt = 0.0;
       h.steps = 0;
-      CK(cudaMemcpy(c->d_sc, &h, sizeof(StepScalars), cudaMemcpyHostToDevice), "write scalars");
+      CK(cudaMemcpyAsync(c->d_sc, &h, sizeof(StepScalars), cudaMemcpyHostToDevice, c->own_stream), "write scalars");
       // per-cell counters start from zero (the step reductions of 2-D meshes include the ghosts)
-      CK(cudaMemset(c->d_iters, 0, (size_t)c->n_cells * sizeof(int)), "reset iters");
+      CK(cudaMemsetAsync(c->d_iters, 0, (size_t)c->n_cells * sizeof(int), c->own_stream), "reset iters");
     }
   }
   if (st == IPM_OK && c->warp_warps > 0) {
@@ -1169,7 +1247,7 @@ ipm_status ipm_assemble_hessian(ipm_ctx* c, double* h, size_t count) {
   const size_t nph = (size_t)c->NM * (c->NM + 1) / 2;
   if (count != (size_t)c->n_interior * nph) return fail(c, IPM_EINVAL, "ipm_assemble_hessian: count must be n_interior*NM(NM+1)/2");
   double* d = nullptr;
-  IPM_CK(c, cudaMalloc(&d, count * sizeof(double)));
+  IPM_CK(c, dalloc(c, &d, count * sizeof(double), c->stream));
   NewtonArgs a = newton_args(c, 0);
   a.h_dump = d;
   a.track_speed = 0;
@@ -1180,7 +1258,30 @@ ipm_status ipm_assemble_hessian(ipm_ctx* c, double* h, size_t count) {
   if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  cudaFree(d);
+  cudaFreeAsync(d, c->stream);
+  IPM_CK(c, e);
+  return IPM_OK;
+}
+
+ipm_status ipm_factor_hessian(ipm_ctx* c, double* h, size_t count) {
+  NvtxRange nvtx_("ipm_factor_hessian");
+  if (!c || (!h && count)) return IPM_EINVAL;
+  if (c->unusable) return fail(c, IPM_ETIMEOUT, "context unusable after an undrained tensor-core timeout");
+  const size_t nph = (size_t)c->NM * (c->NM + 1) / 2;
+  if (count != (size_t)c->n_interior * nph) return fail(c, IPM_EINVAL, "ipm_factor_hessian: count must be n_interior*NM(NM+1)/2");
+  double* d = nullptr;
+  IPM_CK(c, dalloc(c, &d, count * sizeof(double), c->stream));
+  NewtonArgs a = newton_args(c, 0);
+  a.f_dump = d;
+  a.track_speed = 0;
+  cudaError_t e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess)
+    e = launch_newton_phys(c->entk, c->phys, c->m, a, c->newton_grid, c->newton_smem, c->h_in_smem, c->newton_mode,
+                           c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&c->d_sc->work_counter, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFreeAsync(d, c->stream);
   IPM_CK(c, e);
   return IPM_OK;
 }

@@ -329,6 +329,12 @@ struct NewtonArgs {
   int bc_left, bc_right;
   MixedTiles mx;         // mixed path only
   uint32_t off_h, off_a, off_b;  // shared-memory byte offsets: packed H, A staging, Phi chunks
+  // split factorisation (tensor-core trailing updates): shared-memory offset of the digit slices and
+  // row exponents, rows per slice, tensor-memory accumulator sets (1 or 2)
+  uint32_t off_s;
+  int s_rows, s_nbuf;
+  double* f_dump;        // non-null: factorise the augmented Hessian at the current duals, store L packed
+                         // [work item][NM(NM+1)/2] and stop (no Newton update)
 };
 
 struct Update1DArgs {

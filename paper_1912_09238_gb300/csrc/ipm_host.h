@@ -61,6 +61,7 @@ struct MixedLayout {
 // the two Phi-chunk buffers, and the total.
 struct NewtonSmem {
   uint32_t off_h = 0, off_a = 0, off_b = 0;
+  uint32_t off_s = 0;       // digit slices and row exponents of the split factorisation
   size_t bytes = 0;
 };
 
@@ -83,10 +84,17 @@ cudaError_t raise_smem_limit(K k, size_t need) {
 }
 
 // kernel launchers (newton.cu, update.cu)
-NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* mx);
-MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem);
+// s_rows > 0: room for the split factorisation's digit slices (rows per slice from split_rows)
+NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* mx, int s_rows = 0);
+MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem, int s_rows = 0);
+// rows per digit slice of the split factorisation of an N*m system, and the bytes of the slices
+int split_rows(int NM);
+size_t split_bytes(int rows);
+constexpr int SPLIT_AUTO_NM = 128;         // factorization = 0: the split factorisation from this N*m (mixed)
+constexpr int SPLIT_TMEM_COLS_ONE = 256;   // tensor-memory columns of one accumulator set
 int newton_threads();
-// mode: 0 FP64, 1 mixed (tensor-core Hessian, FP64 factorisation), 2 mixed with an FP32 factorisation
+// mode: 0 FP64, 1 mixed (tensor-core Hessian, FP64 factorisation), 2 mixed with an FP32 factorisation,
+// 3 mixed with the split factorisation (tensor-core trailing updates), 4 FP64 Hessian with the split one
 cudaError_t launch_newton_phys(int ent, int phys, int m, const NewtonArgs& a, int grid, size_t smem, bool h_in_smem,
                                int mode, cudaStream_t s);
 cudaError_t prepare_newton(int ent, int phys, int m, size_t smem, bool h_in_smem, int mode, int* blocks_per_sm);

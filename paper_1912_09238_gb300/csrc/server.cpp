@@ -1,14 +1,19 @@
 // server.cpp -- continuous-batching request server (ipm_server_*, declared in include/ipm.h).
 //
-// One worker thread per server drives the device. Each loop iteration:
-//   1. admission: waiting requests, in arrival order, become active while a slot is free and the sum
-//      of the active requests' ipm_footprint stays within the memory cap (the oldest request is never
-//      passed over, so admission is FIFO);
+// Two host threads per server drive the device:
+//   admission thread: waiting requests, in arrival order, are taken while a slot is free and the sum
+//      of the admitted requests' ipm_footprint stays within the memory cap (the oldest request is never
+//      passed over, so admission is FIFO); each gets its context (ipm_init: stream-ordered allocations
+//      from the library's memory pool, initial data, dual solve, graph capture) and its own stream, and
+//      is handed to the worker. Set-up thus runs beside the worker's launches instead of between them.
+//   worker thread, each loop iteration:
+//   1. it takes the contexts the admission thread has readied;
 //   2. launch: every active request without work in flight gets its next batch of time steps
 //      (ipm_step graph launches on the request's own stream) and an event after the batch;
 //   3. completion: requests whose event has fired are checked (t >= t_end, max_steps, or a per-cell
-//      failure); finished requests copy their moments to the host, free their context and slot, and
-//      wake ipm_poll / ipm_server_drain callers.
+//      failure); finished requests copy their moments to the host, free their context (stream-ordered
+//      frees, no device-wide synchronisation) and slot, and wake the admission thread and ipm_poll /
+//      ipm_server_drain callers.
 // Batches are sized from the last time step so that a request stops within a few steps of t_end.
 // The kernels of all active requests overlap on the GPU through their separate streams; no request
 // reads another's memory, and every kernel's result is independent of the order in which CTAs run,
@@ -63,17 +68,23 @@ struct ipm_server {
   std::mutex mu;
   std::condition_variable cv_work;   // worker waits for submissions
   std::condition_variable cv_done;   // drain waits for completions
+  std::condition_variable cv_admit; // admission thread waits for submissions and freed capacity
   std::deque<std::shared_ptr<Job>> waiting;
+  std::deque<std::shared_ptr<Job>> ready;   // contexts set up by the admission thread, not yet active
   std::map<uint64_t, std::shared_ptr<Job>> jobs;
   uint64_t next_ticket = 1;
   size_t outstanding = 0;            // submitted and not yet done
+  int admitted = 0;                  // requests holding a slot (being set up, ready or active)
+  size_t in_use = 0;                 // their footprints
+  bool admitting = false;            // the admission thread is setting up a request
   bool stop = false;
-  std::thread worker;
+  std::thread worker, admitter;
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   void run();
+  void admit();
 };
 
 static void finish(ipm_server* s, const std::shared_ptr<Job>& j, int32_t status, const std::string& why = "") {
@@ -101,62 +112,83 @@ static void finish(ipm_server* s, const std::shared_ptr<Job>& j, int32_t status,
   std::lock_guard<std::mutex> lk(s->mu);
   j->done = true;
   --s->outstanding;
+  --s->admitted;
+  s->in_use -= j->footprint;
   s->cv_done.notify_all();
+  s->cv_admit.notify_all();
+}
+
+// Admission thread: FIFO by slots and memory; sets up each admitted request's context.
+void ipm_server::admit() {
+  cudaSetDevice(device);
+  for (;;) {
+    std::shared_ptr<Job> j;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_admit.wait(lk, [&] {
+        return stop || (!waiting.empty() && admitted < max_active && in_use + waiting.front()->footprint <= mem_cap);
+      });
+      if (stop) {
+        // drop the waiting requests; the running ones finish
+        for (auto& w : waiting) {
+          w->status = IPM_EAGAIN;
+          w->done = true;
+          --outstanding;
+        }
+        waiting.clear();
+        cv_done.notify_all();
+        return;
+      }
+      j = waiting.front();
+      waiting.pop_front();
+      ++admitted;
+      in_use += j->footprint;
+      admitting = true;
+    }
+    j->t_start = now();
+    std::string why;
+    ipm_status st = ipm_init(&j->req.problem, &j->req.basis, &j->req.quad, &j->req.entropy, &j->req.options, &j->ctx);
+    if (st != IPM_OK) why = std::string("ipm_init: ") + ipm_last_error(nullptr);
+    cudaError_t ce = cudaSuccess;
+    if (st == IPM_OK && (ce = cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+      st = IPM_ECUDA;
+      why = std::string("cudaStreamCreate: ") + cudaGetErrorString(ce);
+    }
+    if (st == IPM_OK && (ce = cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming)) != cudaSuccess) {
+      st = IPM_ECUDA;
+      why = std::string("cudaEventCreate: ") + cudaGetErrorString(ce);
+    }
+    if (st == IPM_OK && (st = ipm_set_stream(j->ctx, j->stream)) != IPM_OK)
+      why = std::string("ipm_set_stream: ") + ipm_last_error(j->ctx);
+    if (st != IPM_OK) {
+      finish(this, j, st, why);
+      std::lock_guard<std::mutex> lk(mu);
+      admitting = false;
+      continue;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    ready.push_back(j);
+    admitting = false;
+    cv_work.notify_one();
+  }
 }
 
 void ipm_server::run() {
   cudaSetDevice(device);
   std::vector<std::shared_ptr<Job>> active;
-  size_t in_use = 0;
   for (;;) {
-    // 1. admission (FIFO, by slots and memory)
-    std::vector<std::shared_ptr<Job>> admitted;
+    // 1. contexts the admission thread has set up
     {
       std::unique_lock<std::mutex> lk(mu);
-      if (active.empty() && waiting.empty()) {
-        if (stop) break;
-        cv_work.wait(lk, [&] { return stop || !waiting.empty(); });
-        if (stop && waiting.empty()) break;
+      if (active.empty() && ready.empty()) {
+        // idle: wait for a readied request, or for the end (nothing waiting, admitted or being set up)
+        cv_work.wait(lk, [&] { return !ready.empty() || (stop && admitted == 0 && !admitting); });
+        if (ready.empty()) break;
       }
-      if (stop) {
-        // drop the waiting requests; the running ones finish
-        for (auto& j : waiting) {
-          j->status = IPM_EAGAIN;
-          j->done = true;
-          --outstanding;
-        }
-        waiting.clear();
-        cv_done.notify_all();
+      while (!ready.empty()) {
+        active.push_back(ready.front());
+        ready.pop_front();
       }
-      while (!waiting.empty() && (int)(active.size() + admitted.size()) < max_active &&
-             in_use + waiting.front()->footprint <= mem_cap) {
-        admitted.push_back(waiting.front());
-        in_use += waiting.front()->footprint;
-        waiting.pop_front();
-      }
-    }
-    for (auto& j : admitted) {
-      j->t_start = now();
-      std::string why;
-      ipm_status st = ipm_init(&j->req.problem, &j->req.basis, &j->req.quad, &j->req.entropy, &j->req.options, &j->ctx);
-      if (st != IPM_OK) why = std::string("ipm_init: ") + ipm_last_error(nullptr);
-      cudaError_t ce = cudaSuccess;
-      if (st == IPM_OK && (ce = cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking)) != cudaSuccess) {
-        st = IPM_ECUDA;
-        why = std::string("cudaStreamCreate: ") + cudaGetErrorString(ce);
-      }
-      if (st == IPM_OK && (ce = cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming)) != cudaSuccess) {
-        st = IPM_ECUDA;
-        why = std::string("cudaEventCreate: ") + cudaGetErrorString(ce);
-      }
-      if (st == IPM_OK && (st = ipm_set_stream(j->ctx, j->stream)) != IPM_OK)
-        why = std::string("ipm_set_stream: ") + ipm_last_error(j->ctx);
-      if (st != IPM_OK) {
-        in_use -= j->footprint;
-        finish(this, j, st, why);
-        continue;
-      }
-      active.push_back(j);
     }
     // 2. launch the next batch of every idle active request
     for (auto& j : active) {
@@ -215,7 +247,6 @@ void ipm_server::run() {
         }
       }
       if (done) {
-        in_use -= j->footprint;
         finish(this, j, status);
         active.erase(active.begin() + k);
         progressed = true;
@@ -249,6 +280,7 @@ ipm_status ipm_server_create(size_t mem_cap_bytes, int max_active, ipm_server** 
   }
   s->mem_cap = mem_cap_bytes;
   s->worker = std::thread([s] { s->run(); });
+  s->admitter = std::thread([s] { s->admit(); });
   *out = s;
   return IPM_OK;
 }
@@ -269,7 +301,7 @@ ipm_status ipm_submit(ipm_server* s, const ipm_request* req, uint64_t* ticket) {
   s->waiting.push_back(j);
   ++s->outstanding;
   *ticket = j->ticket;
-  s->cv_work.notify_one();
+  s->cv_admit.notify_one();
   return IPM_OK;
 }
 
@@ -311,6 +343,12 @@ void ipm_server_destroy(ipm_server* s) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
+    s->cv_work.notify_all();
+    s->cv_admit.notify_all();
+  }
+  if (s->admitter.joinable()) s->admitter.join();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
     s->cv_work.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();

@@ -67,7 +67,7 @@ class ipm_options(ctypes.Structure):
                 ("armijo_c", ctypes.c_double), ("max_halvings", ctypes.c_int), ("slack_rel", ctypes.c_double),
                 ("adapt_min_degree", ctypes.c_int), ("delta_lo", ctypes.c_double), ("delta_hi", ctypes.c_double),
                 ("hessian_reuse", ctypes.c_int), ("reuse_ratio", ctypes.c_double), ("newton_kernel", ctypes.c_int),
-                ("check_cache", ctypes.c_int)]
+                ("check_cache", ctypes.c_int), ("factorization", ctypes.c_int)]
 
 
 class ipm_dims(ctypes.Structure):
@@ -148,6 +148,7 @@ SIGNATURES = [
     ("ipm_dual_solve", ctypes.c_int, [_vp, _P(ipm_stats)]),
     ("ipm_update", ctypes.c_int, [_vp, ctypes.c_double]),
     ("ipm_assemble_hessian", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
+    ("ipm_factor_hessian", ctypes.c_int, [_vp, _dp, ctypes.c_size_t]),
     ("ipm_step", ctypes.c_int, [_vp, _P(ipm_stats)]),
     ("ipm_run", ctypes.c_int, [_vp, ctypes.c_int64, _P(ipm_stats)]),
     ("ipm_oneshot_step", ctypes.c_int, [_vp, _P(ipm_stats)]),
@@ -435,6 +436,12 @@ class Context:
         d = self.dims
         nm = d.N * d.m
         return self._get("ipm_assemble_hessian", (d.n_interior, nm * (nm + 1) // 2))
+
+    def factor_hessian(self):
+        """Packed lower-triangular Cholesky factors of those Hessians, (n_interior, NM(NM+1)/2)."""
+        d = self.dims
+        nm = d.N * d.m
+        return self._get("ipm_factor_hessian", (d.n_interior, nm * (nm + 1) // 2))
 
     def update(self, dt):
         _check("ipm_update", lib().ipm_update(self.h, dt), self.h)

@@ -51,9 +51,13 @@ def _grid(a, w):
     return a.reshape(w["ny"] + 2, w["nx"] + 2, *a.shape[1:])
 
 
-@pytest.mark.parametrize("precision,steps", [("fp64", 3), ("mixed", 3), ("mixed_f32f", 1)])
-def test_degree_six_cells_match_the_oracle(oracle_run, precision, steps):
-    ctx = gpu_context(STRIP, precision=precision, adapt_min_degree=2, delta_lo=2e-5, delta_hi=2e-4)
+@pytest.mark.parametrize("precision,steps,factorization", [("fp64", 3, 1), ("mixed", 3, 1), ("mixed_f32f", 1, 0),
+                                                           ("fp64", 2, 2), ("mixed", 3, 2)],
+                         ids=["fp64", "mixed", "mixed_f32f", "fp64_split", "mixed_split"])
+def test_degree_six_cells_match_the_oracle(oracle_run, precision, steps, factorization):
+    """factorization 1: blocked FP64 FMAs; 2: the split factorisation (tensor-core trailing updates)."""
+    ctx = gpu_context(STRIP, precision=precision, adapt_min_degree=2, delta_lo=2e-5, delta_hi=2e-4,
+                      factorization=factorization)
     d = ctx.dims
     assert (d.N, d.m, d.Q) == (84, 4, 343)
     st = oracle_run[0]

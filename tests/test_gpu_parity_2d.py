@@ -78,6 +78,21 @@ def test_algorithm1_steps(w, precision):
     assert s.newton_iters == int(st.newton_iters.sum()) or precision == "mixed"
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("mixed", TOL_MIXED)])
+def test_sod_m4_with_the_split_factorisation(precision, tol):
+    """The 4-variable Sod reading at its own degree (N m = 224, workspace Hessian) with the split
+    factorisation (tensor-core trailing updates), against the 2-D oracle."""
+    w = SOD4_FULL_DEGREE
+    prob = oracle_problem_2d(w)
+    st = s2.initial_state(prob)
+    ctx = gpu_context(w, precision=precision, factorization=2)
+    for n in range(3):
+        st = s2.ipm_step(prob, st)
+        s = ctx.step()
+        assert s.failed_cells == 0 and s.tc_timeouts == 0
+        assert rel_err(_interior(ctx.get_moments(), w), st.uhat[1:-1, 1:-1]) < tol, n
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_oneshot_on_the_ramp(precision):
     prob = oracle_problem_2d(RAMP)
