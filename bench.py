@@ -678,10 +678,13 @@ def collocation_bench(args):
 
 def frozen_hessian_bench(args):
     """The Sod workload with frozen Hessians (ipm_options.hessian_reuse 2: Cholesky factors kept per
-    cell across solves, reused while they converge): both precision paths, the full run."""
+    cell across solves, reused while they converge): both precision paths, the full run (--full) or its
+    first 300 time steps."""
     from paper_1912_09238_gb300 import workloads
     import torch
-    out = {"workload": "Sod (as the headline) with hessian_reuse = 2, reuse_ratio 0.5, one full run to t_end",
+    limit = None if args.full else 300
+    out = {"workload": "Sod (as the headline) with hessian_reuse = 2, reuse_ratio 0.5, " +
+                       ("one full run to t_end" if limit is None else f"the first {limit} time steps of a run"),
            "unit": UNIT}
     stream = torch.cuda.current_stream()
     for prec in ("mixed", "fp64"):
@@ -701,7 +704,7 @@ def frozen_hessian_bench(args):
             n += 1
             if s.failed_cells:
                 raise RuntimeError(f"failed cells: {s.as_dict()}")
-            if s.t >= workloads.SOD_1D["t_end"] * (1 - 1e-12):
+            if s.t >= workloads.SOD_1D["t_end"] * (1 - 1e-12) or (limit and n >= limit):
                 break
         out[prec] = {"value": workloads.SOD_1D["nx"] * n / secs, "time_steps": n, "ms_per_time_step": 1e3 * secs / n,
                      "newton_updates_per_time_step": it / n, "factorizations_per_time_step": fa / n}
