@@ -693,25 +693,6 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
         return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for the mixed-precision Newton kernel");
     }
     c->sm = newton_smem(c->N, c->m, c->Q, c->h_in_smem, &c->mx, c->s_rows);
-    if (c->split) {
-      // The split factorisation touches the trailing matrix once per 16-column panel, so the packed H can
-      // live in the (L2-resident) workspace at little cost; without it in shared memory two CTAs may share
-      // an SM, and one cell's serial diagonal-block chains overlap another's throughput work. Taken when
-      // the occupancy API confirms two CTAs per SM (tensor memory: 256 columns each).
-      const size_t half = (size_t)prop.sharedMemPerMultiprocessor / 2 - 2048;
-      MixedLayout two = mixed_layout(c->N, c->m, c->Q, std::min(budget, half), false, c->s_rows, 256);
-      if (two.ok) {
-        const NewtonSmem sm2 = newton_smem(c->N, c->m, c->Q, false, &two, c->s_rows);
-        int b2 = 0;
-        if (prepare_newton(c->entk, c->phys, c->m, sm2.bytes, false, c->newton_mode, &b2) == cudaSuccess && b2 >= 2) {
-          c->mx = two;
-          c->mx.tmem_cols = 256;
-          c->sm = sm2;
-          c->h_in_smem = false;
-        }
-        cudaGetLastError();
-      }
-    }
   } else {
     const NewtonSmem full = newton_smem(c->N, c->m, c->Q, true, nullptr, c->s_rows);
     const NewtonSmem lean = newton_smem(c->N, c->m, c->Q, false, nullptr, c->s_rows);
@@ -720,17 +701,7 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     }
     c->h_in_smem = full.bytes <= budget;
     c->sm = c->h_in_smem ? full : lean;
-    if (c->split) {
-      c->mx.tmem_cols = SPLIT_TMEM_COLS_ONE;
-      // as on the mixed path: the workspace H when that lets two CTAs share an SM
-      int b2 = 0;
-      if (c->h_in_smem && lean.bytes <= (size_t)prop.sharedMemPerMultiprocessor / 2 - 2048 &&
-          prepare_newton(c->entk, c->phys, c->m, lean.bytes, false, c->newton_mode, &b2) == cudaSuccess && b2 >= 2) {
-        c->h_in_smem = false;
-        c->sm = lean;
-      }
-      cudaGetLastError();
-    }
+    if (c->split) c->mx.tmem_cols = SPLIT_TMEM_COLS_ONE;
   }
   c->newton_smem = c->sm.bytes;
   {

@@ -86,8 +86,7 @@ cudaError_t raise_smem_limit(K k, size_t need) {
 // kernel launchers (newton.cu, update.cu)
 // s_rows > 0: room for the split factorisation's digit slices (rows per slice from split_rows)
 NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* mx, int s_rows = 0);
-// tmem_max: tensor-memory columns one CTA may take (512, or 256 when two CTAs share an SM)
-MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem, int s_rows = 0, int tmem_max = 512);
+MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem, int s_rows = 0);
 // rows per digit slice of the split factorisation of an N*m system, and the bytes of the slices
 int split_rows(int NM);
 size_t split_bytes(int rows);

@@ -28,13 +28,11 @@ NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* m
   const size_t NM = (size_t)N * m;
   const size_t B = (size_t)m * (m + 1) / 2;
   const size_t wj = mx ? (B * Q + 1) / 2 : B * Q;     // w J: float on the mixed path
-  // the split factorisation needs no panel buffers (the folded update's scratch then uses its slices)
-  const size_t panels = s_rows > 0 ? 0 : 2 * (NM + 1) * PSTR;
-  const size_t fixed = (4 * NM + 4 * (size_t)m * Q + wj + NWARPS * 8 + NM + panels) * sizeof(double);
+  const size_t fixed =
+      (4 * NM + 4 * (size_t)m * Q + wj + NWARPS * 8 + NM + 2 * (NM + 1) * PSTR) * sizeof(double);
   const size_t h_bytes = h_in_smem ? packed_aug_count((int)NM) * sizeof(double) : 0;
   s.off_h = (uint32_t)align128(fixed);
-  // digit slices; also the folded update's scratch (2 x NWARPS x NM doubles) in split mode
-  const size_t sp_bytes = s_rows > 0 ? std::max(split_bytes(s_rows), align128(2 * NWARPS * NM * sizeof(double))) : 0;
+  const size_t sp_bytes = s_rows > 0 ? split_bytes(s_rows) : 0;
   if (!mx) {
     s.bytes = s.off_h + h_bytes;
     if (sp_bytes) {
@@ -64,7 +62,7 @@ NewtonSmem newton_smem(int N, int m, int Q, bool h_in_smem, const MixedLayout* m
   return s;
 }
 
-MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem, int s_rows, int tmem_max) {
+MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem, int s_rows) {
   MixedLayout L;
   const int B = m * (m + 1) / 2;
   L.n_pad = (N + 15) / 16 * 16;
@@ -74,7 +72,7 @@ MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem
   L.b_chunk_bytes = (size_t)2 * L.n_pad * L.kc * 2;
   if (L.n_pad > 256) return L;
   // row tiles per pass: bounded by tensor memory (512 columns) and by the shared-memory budget
-  for (int tpp = std::min(L.tiles, tmem_max / L.n_pad); tpp >= 1; --tpp) {
+  for (int tpp = std::min(L.tiles, 512 / L.n_pad); tpp >= 1; --tpp) {
     L.tpp = tpp;
     L.a_bytes = (size_t)2 * tpp * 128 * L.kc * 2;
     if (newton_smem(N, m, Q, h_in_smem, &L, s_rows).bytes <= smem_budget) {

@@ -581,8 +581,7 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
 // The roundings are the 56-bit truncation of the digits (relative to the row's largest entry), the
 // conversion of 2^56 S and the final FMA: FP64-level accuracy, with the FP64 work of a trailing entry cut
 // from 16 FMAs per panel to one conversion and one FMA. The panel itself (two blocks of NB = 8 columns)
-// is factorised in FP64: its 16 x 16 diagonal block by one warp (diag16), the rows below by a triangular
-// solve with one thread per row (trsm16).
+// is factorised in FP64 by panel_diag / panel_trsm as in cholesky_aug.
 // Digit slices: SDIG arrays of s_rows x 16 BF16 in the K-major core-matrix layout (8-row groups SSBO
 // bytes apart), rows counted from the first trailing row s1; rows beyond the trailing block hold stale
 // data that only ever feeds output rows and columns that are not read back.
@@ -739,72 +738,41 @@ static __device__ void split_combine(double* A, int s1, int R, int lo, int hi, i
   }
 }
 
-// Factorise the kw x kw diagonal block (kw <= SNB) at rows and columns kb.. of A (already updated by every
-// earlier panel) in FP64: one warp, lane i owning row kb + i in registers. Writes L into A and the
-// reciprocal pivots into s_dinv; sets *s_flag on a pivot that is not positive and finite.
-static __device__ void diag16(double* A, int kb, int kw, double* s_dinv, int* s_flag) {
-  const int lane = threadIdx.x & 31;
-  double row[SNB];
-  const bool mine = lane < kw;
+// Factorise the 16-column panel kb..kb+kw-1 (rows kb..n, already updated by every earlier panel) in FP64:
+// two blocks of NB columns, the second updated by the first within the panel. Returns false on a bad pivot.
+static __device__ bool panel16(double* A, int n, int kb, int kw, double* P, double* s_dinv, int* s_flag) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int k0 = min(NB, kw);
+  if (warp == 0) panel_diag(A, kb, k0, P, s_dinv, s_flag);
+  __syncthreads();
+  if (*s_flag) return false;
+  panel_trsm(A, n, kb, k0, P, s_dinv, tid, NT);
+  __syncthreads();
+  if (kw > NB) {
+    const int s0 = kb + NB, k1 = kw - NB, rows = n + 1 - s0;
+    for (int item = tid; item < rows * k1; item += NT) {
+      const int r = s0 + item / k1, c = s0 + item % k1;
+      if (c > r) continue;
+      double acc = 0.0;
 #pragma unroll
-  for (int j = 0; j < SNB; ++j) row[j] = (mine && j <= lane) ? A[rowoff(kb + lane) + kb + j] : 0.0;
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < SNB; ++k) {
-    if (k < kw) {
-      const double dkk = __shfl_sync(0xffffffffu, row[k], k);
-      ok = ok && dkk > 0.0 && isfinite(dkk);
-      const double id = rsqrt(dkk > 0.0 ? dkk : 1.0);
-      if (lane == k) row[k] = dkk * id;
-      if (lane > k) row[k] *= id;
-#pragma unroll
-      for (int j = k + 1; j < SNB; ++j) {
-        if (j < kw) {
-          const double ljk = __shfl_sync(0xffffffffu, row[k], j);
-          if (lane >= j) row[j] = fma(-row[k], ljk, row[j]);
-        }
-      }
-      if (lane == 0) s_dinv[kb + k] = id;
+      for (int k = 0; k < NB; ++k) acc = fma(P[r * PSTR + k], P[c * PSTR + k], acc);
+      A[rowoff(r) + c] -= acc;
     }
+    __syncthreads();
+    if (warp == 0) panel_diag(A, s0, k1, P, s_dinv, s_flag);
+    __syncthreads();
+    if (*s_flag) return false;
+    panel_trsm(A, n, s0, k1, P, s_dinv, tid, NT);
+    __syncthreads();
   }
-  if (mine) {
-#pragma unroll
-    for (int j = 0; j < SNB; ++j)
-      if (j <= lane) A[rowoff(kb + lane) + kb + j] = row[j];
-  }
-  if (lane == 0 && !ok) *s_flag = 1;
-}
-
-// Rows r = kb+kw .. n of the panel: L[r][kb..kb+kw) = A[r][kb..kb+kw) L11^-T (L11 from diag16), one row per
-// thread (t0, t0 + stride, ...). Column by column: x_k = v_k / L_kk, then v_j -= x_k L_jk for the later
-// columns, so the dependent chain is two operations per column (the same operations on each v_j, in the
-// same order, as the row-by-row substitution).
-static __device__ void trsm16(double* A, int n, int kb, int kw, const double* s_dinv, int t0, int stride) {
-  for (int r = kb + kw + t0; r <= n; r += stride) {
-    double* Ar = A + rowoff(r) + kb;
-    double v[SNB];
-#pragma unroll
-    for (int k = 0; k < SNB; ++k) v[k] = k < kw ? Ar[k] : 0.0;
-#pragma unroll
-    for (int k = 0; k < SNB; ++k) {
-      if (k < kw) {
-        v[k] *= s_dinv[kb + k];
-#pragma unroll
-        for (int j = k + 1; j < SNB; ++j)
-          if (j < kw) v[j] = fma(-v[k], A[rowoff(kb + j) + kb + k], v[j]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < SNB; ++k)
-      if (k < kw) Ar[k] = v[k];
-  }
+  return true;
 }
 
 // Split factorisation of the packed (n+1) x (n+1) augmented matrix (rows 0..n-1: H, row n: g), with
 // the forward substitution folded in as in cholesky_aug. Returns false on a bad pivot (*s_flag set) or
 // when a bounded tensor-core wait ran out (*s_abort set).
-static __device__ bool cholesky_split(double* A, int n, double* s_dinv, int* s_flag, const SplitSmem& sp, TcState& t,
-                                      int* s_abort) {
+static __device__ bool cholesky_split(double* A, int n, double* s_P, double* s_dinv, int* s_flag, const SplitSmem& sp,
+                               TcState& t, int* s_abort) {
   const int tid = threadIdx.x;
   const uint32_t sl = tc::smem_u32(sp.slices);
   const uint32_t slice_bytes = (uint32_t)sp.rows * 32u;
@@ -812,11 +780,7 @@ static __device__ bool cholesky_split(double* A, int n, double* s_dinv, int* s_f
   __syncthreads();
   for (int kb = 0; kb < n; kb += SNB) {
     const int kw = min(SNB, n - kb);
-    if (threadIdx.x < 32) diag16(A, kb, kw, s_dinv, s_flag);
-    __syncthreads();
-    if (*s_flag) return false;
-    trsm16(A, n, kb, kw, s_dinv, tid, NT);
-    __syncthreads();
+    if (!panel16(A, n, kb, kw, s_P, s_dinv, s_flag)) return false;
     const int s1 = kb + kw;
     if (s1 >= n) break;                              // only the gradient row is below: nothing to update
     const int R = n + 1 - s1;
@@ -955,7 +919,7 @@ __device__ __forceinline__ void hessian_timed(StepScalars* sc, uint64_t t0) {
 
 // The split variants run one CTA per SM (their systems fill the shared memory) and get its registers.
 template <int ENT, int PHYS, int M, bool H_SMEM, bool MIXED, bool F32F, bool SPLIT>
-__global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
+__global__ void __launch_bounds__(NT, SPLIT ? 1 : 2) k_newton(NewtonArgs a) {
   constexpr bool TC = MIXED || SPLIT;   // tensor memory and barriers in use
   constexpr int B = packed_count(M);
   extern __shared__ __align__(128) double smem[];
@@ -979,7 +943,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
   double* s_red = s_wJ + (MIXED ? (B * Q + 1) / 2 : B * Q);   // NWARPS * 8
   double* s_wu = s_red + NWARPS * 8;  // [M][Q] w_k u_k
   double* s_dinv = s_wu + M * Q;      // [NM] reciprocal pivots
-  double* s_P = s_dinv + NMX;         // [2][(NM + 1) * PSTR] Cholesky panels (current, next); not in split mode
+  double* s_P = s_dinv + NMX;         // [2][(NM + 1) * PSTR] Cholesky panels (current, next)
   uint8_t* sbytes = reinterpret_cast<uint8_t*>(smem);
   double* s_H = H_SMEM ? reinterpret_cast<double*>(sbytes + a.off_h) : (a.hwork + (size_t)blockIdx.x * a.hwork_stride);
   uint8_t* sA = sbytes + a.off_a;
@@ -995,9 +959,6 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
     tcs.ph[k] = 0u;
     tcs.pend[k] = false;
   }
-  // scratch of the folded update: the panel buffers, or in split mode (no panel buffers) the digit slices,
-  // which are free once a cell's Newton iterations are over
-  double* s_lfs = SPLIT ? reinterpret_cast<double*>(sbytes + a.off_s) : s_P;
   SplitSmem ssp;
   ssp.slices = sbytes + a.off_s;
   ssp.rexp = reinterpret_cast<int*>(sbytes + a.off_s + (size_t)SDIG * a.s_rows * 32);
@@ -1070,7 +1031,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
           }
           __syncthreads();
           if constexpr (PHYS != PHYS_EULER2D)
-            if (a.lf_a) lf_fold<PHYS, M>(a, cell, s_Lam, s_dLam, s_lfs, s_lf_ready);
+            if (a.lf_a) lf_fold<PHYS, M>(a, cell, s_Lam, s_dLam, s_P, s_lf_ready);
           continue;
         }
       }
@@ -1241,7 +1202,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       for (int r = tid; r < NM; r += NT) s_H[rowoff(NM) + r] = s_g[r];
       __syncthreads();
       if constexpr (SPLIT) {
-        if (!cholesky_split(s_H, NM, s_dinv, &s_flag, ssp, tcs, &s_abort)) {
+        if (!cholesky_split(s_H, NM, s_P, s_dinv, &s_flag, ssp, tcs, &s_abort)) {
           if (s_abort) {
             if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
             st = ST_TIMEOUT;
@@ -1381,7 +1342,7 @@ __global__ void __launch_bounds__(NT, 2) k_newton(NewtonArgs a) {
       }
     }
     if constexpr (PHYS != PHYS_EULER2D)
-      if (a.lf_a) lf_fold<PHYS, M>(a, cell, s_Lam, s_dLam, s_lfs, s_lf_ready);
+      if (a.lf_a) lf_fold<PHYS, M>(a, cell, s_Lam, s_dLam, s_P, s_lf_ready);
     __syncthreads();
   }
 
