@@ -210,6 +210,7 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.mx.tiles = c->mx.tiles;
   a.mx.tpp = c->mx.tpp;
   a.mx.tmem_cols = c->mx.tmem_cols;
+  a.mx.abuf = c->mx.abuf;
   a.off_h = c->sm.off_h;
   a.off_a = c->sm.off_a;
   a.off_b = c->sm.off_b;

@@ -268,6 +268,7 @@ struct MixedTiles {
   int tiles;               // ceil(B N / 128) row tiles of 128 (MMA M)
   int tpp;                 // row tiles per pass (accumulators resident in tensor memory at once)
   int tmem_cols;           // allocated tensor-memory columns (power of two >= 32)
+  int abuf;                // A staging buffers (2: the next chunk is built while the MMAs of this one run)
 };
 
 struct NewtonArgs {

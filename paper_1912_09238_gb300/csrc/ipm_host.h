@@ -54,7 +54,8 @@ const char* cc_levels(const ipm_quadrature* quad, int M0, int n, int* out);
 struct MixedLayout {
   bool ok = false;          // the problem fits the tensor-core path
   int n_pad = 0, kc = 0, chunks = 0, tiles = 0, tpp = 0, tmem_cols = 0;
-  size_t a_bytes = 0;       // A staging of one pass and one K-chunk (both BF16 terms)
+  int abuf = 1;             // A staging buffers (2: build of the next K-chunk overlaps the MMAs)
+  size_t a_bytes = 0;       // A staging of one pass: abuf K-chunks (both BF16 terms each)
   size_t b_chunk_bytes = 0; // one K-chunk of the Phi image (both BF16 terms)
 };
 // Dynamic shared memory of the Newton kernel: byte offsets of the packed H, the A staging and

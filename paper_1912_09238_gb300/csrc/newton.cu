@@ -72,9 +72,12 @@ MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem
   L.b_chunk_bytes = (size_t)2 * L.n_pad * L.kc * 2;
   if (L.n_pad > 256) return L;
   // row tiles per pass: bounded by tensor memory (512 columns) and by the shared-memory budget
+  // (two A buffers when they fit at that tile count, else one)
   for (int tpp = std::min(L.tiles, 512 / L.n_pad); tpp >= 1; --tpp) {
+   for (int abuf = L.chunks > 1 ? 2 : 1; abuf >= 1; --abuf) {
     L.tpp = tpp;
-    L.a_bytes = (size_t)2 * tpp * 128 * L.kc * 2;
+    L.abuf = abuf;
+    L.a_bytes = (size_t)abuf * 2 * tpp * 128 * L.kc * 2;
     if (newton_smem(N, m, Q, h_in_smem, &L, s_rows).bytes <= smem_budget) {
       int cols = 32;
       while (cols < tpp * L.n_pad) cols *= 2;
@@ -83,6 +86,7 @@ MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem
       L.ok = true;
       return L;
     }
+   }
   }
   L.tpp = 0;
   return L;

@@ -453,6 +453,8 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
   const uint32_t a_img = (uint32_t)mx.tpp * 128u * (uint32_t)mx.kc * 2u;   // one BF16 term of A
   const uint32_t b_img = (uint32_t)mx.n_pad * (uint32_t)mx.kc * 2u;         // one BF16 term of B (table size)
   const uint32_t b_chunk = 2u * b_img;
+  const uint32_t a_buf = 2u * a_img;                                         // both terms of one chunk
+  const bool two_a = mx.abuf == 2;
   // this cell's tiling (N may be below the table's on adaptive meshes: the Phi image rows beyond N
   // only feed accumulator columns that are never read back)
   const int n_pad = (N + 15) / 16 * 16;
@@ -471,18 +473,8 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
       tc::bulk_g2s(sB, mx.phi_img, b_chunk, &t.bars[1]);
     }
     t.pend[1] = true;
-    for (int c = 0; c < chunks; ++c) {
-      const int buf = c & 1;
-      if (c + 1 < chunks) {
-        // the other buffer was last read by the MMAs of chunk c-1, which have completed
-        if (tid == 0) {
-          tc::mbar_arrive_expect_tx(&t.bars[1 + (buf ^ 1)], b_chunk);
-          tc::bulk_g2s(sB + (buf ^ 1) * b_chunk, mx.phi_img + (size_t)(c + 1) * b_chunk, b_chunk,
-                       &t.bars[1 + (buf ^ 1)]);
-        }
-        t.pend[1 + (buf ^ 1)] = true;
-      }
-      // A operand of this chunk: rows (ab, i) of this pass, nodes q0 .. q0 + kc - 1
+    // A operand of chunk c: rows (ab, i) of this pass, nodes c kc .. c kc + kc - 1, both BF16 terms, into dst
+    auto build = [&](int c, uint8_t* dst) {
       const int q0 = c * mx.kc;
       for (int item = tid; item < rows * groups; item += NT) {
         const int rl = item / groups, g = item - rl * groups;
@@ -505,16 +497,31 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
           }
         }
         const uint32_t off = tc::kmajor_offset(rl, g * 8, sbo);
-        *reinterpret_cast<uint4*>(sA + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(sA + a_img + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        *reinterpret_cast<uint4*>(dst + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(dst + a_img + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
-      tc::fence_proxy_async();
-      __syncthreads();
+    };
+    // With two A buffers the threads build chunk c + 1 while the MMAs of chunk c run; with one, after them.
+    build(0, sA);
+    tc::fence_proxy_async();
+    __syncthreads();
+    for (int c = 0; c < chunks; ++c) {
+      const int buf = c & 1;
+      uint8_t* a_cur = sA + (two_a ? buf : 0) * a_buf;
+      if (c + 1 < chunks) {
+        // the other B buffer was last read by the MMAs of chunk c-1, which have completed
+        if (tid == 0) {
+          tc::mbar_arrive_expect_tx(&t.bars[1 + (buf ^ 1)], b_chunk);
+          tc::bulk_g2s(sB + (buf ^ 1) * b_chunk, mx.phi_img + (size_t)(c + 1) * b_chunk, b_chunk,
+                       &t.bars[1 + (buf ^ 1)]);
+        }
+        t.pend[1 + (buf ^ 1)] = true;
+      }
       const bool got_b = tc_wait(t, 1 + buf);
       if (!got_b) *s_abort = 1;
       if (tid == 0 && got_b) {
         tc::fence_after_sync();
-        const uint32_t sa = tc::smem_u32(sA), sb = tc::smem_u32(sB + buf * b_chunk);
+        const uint32_t sa = tc::smem_u32(a_cur), sb = tc::smem_u32(sB + buf * b_chunk);
         for (int tl = 0; tl < nt; ++tl) {
           const uint32_t d = t.tmem + (uint32_t)(tl * n_pad);
           const uint32_t ta = sa + (uint32_t)tl * 16u * sbo;   // 128 rows = 16 row groups
@@ -530,7 +537,11 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
         tc::mma_commit(&t.bars[0]);
       }
       if (got_b) t.pend[0] = true;
+      // the other A buffer was last read by the MMAs of chunk c-1, which have completed
+      if (two_a && c + 1 < chunks) build(c + 1, sA + (buf ^ 1) * a_buf);
       if (!tc_wait(t, 0)) *s_abort = 1;
+      if (!two_a && c + 1 < chunks) build(c + 1, sA);
+      tc::fence_proxy_async();
       tc::fence_after_sync();
       __syncthreads();
       if (*s_abort) return false;
@@ -581,7 +592,7 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
 // The roundings are the 56-bit truncation of the digits (relative to the row's largest entry), the
 // conversion of 2^56 S and the final FMA: FP64-level accuracy, with the FP64 work of a trailing entry cut
 // from 16 FMAs per panel to one conversion and one FMA. The panel itself (two blocks of NB = 8 columns)
-// is factorised in FP64 by panel_diag / panel_trsm as in cholesky_aug.
+// is factorised in FP64 by panel_diag / panel_trsm as in cholesky_aug, one panel ahead of the trailing update.
 // Digit slices: SDIG arrays of s_rows x 16 BF16 in the K-major core-matrix layout (8-row groups SSBO
 // bytes apart), rows counted from the first trailing row s1; rows beyond the trailing block hold stale
 // data that only ever feeds output rows and columns that are not read back.
@@ -658,21 +669,31 @@ static __device__ void split_panel(const double* A, int n, int kb, int kw, int s
 
 // Work unit u of a trailing update with R rows (row slots 0..R-1; column slots 0..R-2): a 128-row MMA
 // tile starting at slot ta that owns the output rows [lo, hi), and a block of SBLK columns from cb.
+// Units are ordered with the first column block of every tile first (they hold the next panel's columns).
 __device__ __forceinline__ bool split_unit(int u, int R, int& ta, int& lo, int& hi, int& cb) {
   const int R8 = (R + 7) & ~7;
-  for (int l = 0; l < R; l += 128) {
-    const int h = min(R, l + 128);
-    const int nb = (min(h, R - 1) + SBLK - 1) / SBLK;
-    if (u < nb) {
-      lo = l;
-      hi = h;
-      ta = min(l, max(0, R8 - 128));
-      cb = u * SBLK;
-      return true;
+  const int ntl = (R + 127) / 128;
+  int k = -1;
+  if (u < ntl) {
+    k = u;
+    cb = 0;
+  } else {
+    u -= ntl;
+    for (int l = 0; l < R && k < 0; l += 128) {
+      const int nb = (min(min(R, l + 128), R - 1) + SBLK - 1) / SBLK - 1;   // blocks after the first
+      if (u < nb) {
+        k = l / 128;
+        cb = (u + 1) * SBLK;
+      } else {
+        u -= nb;
+      }
     }
-    u -= nb;
+    if (k < 0) return false;
   }
-  return false;
+  lo = 128 * k;
+  hi = min(R, lo + 128);
+  ta = min(lo, max(0, R8 - 128));
+  return true;
 }
 
 __device__ __forceinline__ int split_units(int R) {
@@ -708,17 +729,18 @@ __device__ __forceinline__ long long split_digit_sum(const uint32_t (&v)[SDIG][8
 }
 
 // A[s1 + rs][s1 + cs] -= L21 L21^T for the unit's entries (rows [lo, hi), lower triangle, columns < n).
-// Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile rows) and half (w / 4) of the block's columns.
-static __device__ void split_combine(double* A, int s1, int R, int lo, int hi, int ta, int cb, uint32_t d, const int* rexp) {
+// The calling warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile rows) and the block's columns
+// [8 g0, 8 g1).
+static __device__ void split_combine(double* A, int s1, int R, int lo, int hi, int ta, int cb, uint32_t d, const int* rexp,
+                                     int g0, int g1) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int lq = warp & 3, half = warp >> 2;
+  const int lq = warp & 3;
   const int rs = ta + lq * 32 + lane;
   const bool row_ok = rs >= lo && rs < hi;
   const int Er = row_ok ? rexp[rs] : 0;
   double* Arow = A + rowoff(row_ok ? s1 + rs : 0) + s1;
-#pragma unroll
-  for (int cg = 0; cg < 2; ++cg) {
-    const int c0 = half * 16 + cg * 8;
+  for (int cg = g0; cg < g1; ++cg) {
+    const int c0 = cg * 8;
     uint32_t v[SDIG][8];
 #pragma unroll
     for (int t = 0; t < SDIG; ++t)
@@ -738,19 +760,24 @@ static __device__ void split_combine(double* A, int s1, int R, int lo, int hi, i
   }
 }
 
-// Factorise the 16-column panel kb..kb+kw-1 (rows kb..n, already updated by every earlier panel) in FP64:
-// two blocks of NB columns, the second updated by the first within the panel. Returns false on a bad pivot.
-static __device__ bool panel16(double* A, int n, int kb, int kw, double* P, double* s_dinv, int* s_flag) {
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int k0 = min(NB, kw);
-  if (warp == 0) panel_diag(A, kb, k0, P, s_dinv, s_flag);
-  __syncthreads();
-  if (*s_flag) return false;
-  panel_trsm(A, n, kb, k0, P, s_dinv, tid, NT);
-  __syncthreads();
-  if (kw > NB) {
-    const int s0 = kb + NB, k1 = kw - NB, rows = n + 1 - s0;
-    for (int item = tid; item < rows * k1; item += NT) {
+// The 16-column panel kb..kb+kw-1 (rows kb..n, already updated by every earlier panel) is factorised in
+// FP64 in up to five phases, each a block-wide step between two barriers: 0 the diagonal block of its
+// first NB columns (one warp, panel_diag), 1 their rows below (panel_trsm), 2 the second block's columns
+// updated by the first, 3 the second diagonal block, 4 its rows below. Threads t0, t0 + stride, ...
+// share the row work.
+__device__ __forceinline__ int panel_phases(int kw) { return kw > NB ? 5 : 2; }
+
+static __device__ void panel_phase(int ph, double* A, int n, int kb, int kw, double* P, double* s_dinv, int* s_flag,
+                                   int t0, int stride) {
+  const int warp = threadIdx.x >> 5;
+  const int k0 = min(NB, kw), s0 = kb + NB, k1 = kw - NB;
+  if (ph == 0) {
+    if (warp == 0) panel_diag(A, kb, k0, P, s_dinv, s_flag);
+  } else if (ph == 1) {
+    panel_trsm(A, n, kb, k0, P, s_dinv, t0, stride);
+  } else if (ph == 2) {
+    const int rows = n + 1 - s0;
+    for (int item = t0; item < rows * k1; item += stride) {
       const int r = s0 + item / k1, c = s0 + item % k1;
       if (c > r) continue;
       double acc = 0.0;
@@ -758,32 +785,49 @@ static __device__ bool panel16(double* A, int n, int kb, int kw, double* P, doub
       for (int k = 0; k < NB; ++k) acc = fma(P[r * PSTR + k], P[c * PSTR + k], acc);
       A[rowoff(r) + c] -= acc;
     }
-    __syncthreads();
+  } else if (ph == 3) {
     if (warp == 0) panel_diag(A, s0, k1, P, s_dinv, s_flag);
-    __syncthreads();
-    if (*s_flag) return false;
-    panel_trsm(A, n, s0, k1, P, s_dinv, tid, NT);
-    __syncthreads();
+  } else {
+    panel_trsm(A, n, s0, k1, P, s_dinv, t0, stride);
   }
-  return true;
 }
 
 // Split factorisation of the packed (n+1) x (n+1) augmented matrix (rows 0..n-1: H, row n: g), with
 // the forward substitution folded in as in cholesky_aug. Returns false on a bad pivot (*s_flag set) or
 // when a bounded tensor-core wait ran out (*s_abort set).
+// One panel of look-ahead: the trailing units of a panel start with the first column block of every row
+// tile, which holds the next panel's columns. Once the unit with the next diagonal block (and for the
+// later phases, every first column block) is combined, each unit iteration also advances one phase of
+// the next panel on warps 0..3, while warps 4..7 (one per tensor-memory lane quadrant) combine that unit
+// alone; the other units are combined by all eight warps (two per quadrant, half of the columns each).
+// The phases touch only the next panel's 16 columns, the panel buffer and the pivots; the units combined
+// beside them only columns 32 and more to the right, so the two never meet. Phases left over when the
+// units run out follow on all warps.
 static __device__ bool cholesky_split(double* A, int n, double* s_P, double* s_dinv, int* s_flag, const SplitSmem& sp,
-                               TcState& t, int* s_abort) {
-  const int tid = threadIdx.x;
+                                      TcState& t, int* s_abort) {
+  const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t sl = tc::smem_u32(sp.slices);
   const uint32_t slice_bytes = (uint32_t)sp.rows * 32u;
   if (tid == 0) *s_flag = 0;
   __syncthreads();
+  {
+    const int kw0 = min(SNB, n);
+    for (int ph = 0; ph < panel_phases(kw0); ++ph) {
+      panel_phase(ph, A, n, 0, kw0, s_P, s_dinv, s_flag, tid, NT);
+      __syncthreads();
+      if (*s_flag) return false;
+    }
+  }
   for (int kb = 0; kb < n; kb += SNB) {
+    // this panel is factorised (above, or by the look-ahead of the previous panel)
     const int kw = min(SNB, n - kb);
-    if (!panel16(A, n, kb, kw, s_P, s_dinv, s_flag)) return false;
     const int s1 = kb + kw;
     if (s1 >= n) break;                              // only the gradient row is below: nothing to update
     const int R = n + 1 - s1;
+    const int kw1 = min(SNB, n - s1);                // the next panel
+    const int nph = panel_phases(kw1);
+    const int ntl = (R + 127) / 128;                 // units 0 .. ntl-1: the first column block of each tile
+    int ph = 0;
     split_panel(A, n, kb, kw, s1, sp);
     tc::fence_proxy_async();
     __syncthreads();
@@ -807,12 +851,25 @@ static __device__ bool cholesky_split(double* A, int n, double* s_P, double* s_d
       tc::fence_after_sync();
       int ta, lo, hi, cb;
       split_unit(u, R, ta, lo, hi, cb);
-      split_combine(A, s1, R, lo, hi, ta, cb, t.tmem + (uint32_t)(b * SPLIT_BUF_COLS), sp.rexp);
+      const uint32_t d = t.tmem + (uint32_t)(b * SPLIT_BUF_COLS);
+      const bool ahead = ph < nph && !*s_flag && u >= (ph == 0 ? 1 : ntl);
+      if (ahead) {
+        if (warp >= 4) split_combine(A, s1, R, lo, hi, ta, cb, d, sp.rexp, 0, 4);
+        else panel_phase(ph, A, n, s1, kw1, s_P, s_dinv, s_flag, tid, 128);
+        ++ph;
+      } else {
+        split_combine(A, s1, R, lo, hi, ta, cb, d, sp.rexp, 2 * (warp >> 2), 2 * (warp >> 2) + 2);
+      }
       tc::fence_before_sync();
       __syncthreads();
       if (*s_abort) return false;
       if (sp.nbuf == 1 && u + 1 < U) issue(u + 1);
     }
+    for (; ph < nph && !*s_flag; ++ph) {
+      panel_phase(ph, A, n, s1, kw1, s_P, s_dinv, s_flag, tid, NT);
+      __syncthreads();
+    }
+    if (*s_flag) return false;
   }
   return true;
 }
