@@ -13,8 +13,8 @@ beside it, with the difference of their final moments. Prints one JSON line (ran
 --impl reference times the CPU oracle on the host cores instead (each step a bounded sample).
 With torchrun (N > 1) every rank runs an independent replica of the workload on its own GPU
 (the method needs no data exchange between replicas), value = all cells updated / max time.
---full adds the long forms of the other workloads (shear layer to 200 steps, the 10,000-request
-serving stream at three arrival rates, the ramp on the FP64 path to its residual).
+--full adds the long forms of the other workloads (shear layer to 200 steps, the ramp on the FP64 path
+to its residual).
 """
 import argparse
 import json
@@ -32,9 +32,10 @@ if ROOT not in sys.path:
 METRIC = "IPM cell-steps/s (mixed+batched vs FP64 GPU at equal error); p50/p99 latency"
 UNIT = "cell-steps/s"
 KERNELS_PER_TIME_STEP = 4    # k_order, k_newton, k_lf_combine, k_finalize (one CUDA graph per time step)
-# dram__bytes_read.sum + dram__bytes_write.sum of one mixed-path k_newton launch on this workload,
-# from an ncu capture of the current kernel; None when no capture of the current kernel exists
-NEWTON_TRAFFIC_BYTES = {"mixed": None, "fp64": None, "mixed_f32f": None}
+# dram__bytes_read.sum + dram__bytes_write.sum of one mixed-path k_newton launch on this workload (the
+# launch of time step 691 of a whole run: 17.72 MB read, 0 written), from an ncu capture of the current
+# kernel; None when no capture of the current kernel exists
+NEWTON_TRAFFIC_BYTES = {"mixed": 17.72e6, "fp64": None, "mixed_f32f": None}
 L2_FLUSH_BYTES = 512 << 20   # > 4x the 126 MiB L2
 FP64_PROBE_N = 6144          # cuBLAS DGEMM size of the FP64 ceiling measurement
 CPU_SAMPLE_STEPS = 20        # Algorithm-1 steps of the oracle in the cpu_baseline sample
@@ -748,7 +749,7 @@ def serving_bench(args):
     import numpy as np
     import torch
     from paper_1912_09238_gb300 import workloads
-    n = 10000 if args.full else args.serving_requests
+    n = args.serving_requests
     steps = args.serving_steps
     stream = [w for _, w in workloads.serving_requests(n, seed=1234, steps=steps)]
     reqs = [(workloads.request(w, "mixed"), w) for w in stream]
@@ -937,7 +938,7 @@ def main():
     ap.add_argument("--sod-m4-fp64-steps", type=int, default=200)
     ap.add_argument("--only", choices=["burgers", "ramp", "kh", "sod_m4", "collocation", "serving"], default=None,
                     help="run only this workload's timing (no headline; for profiling)")
-    ap.add_argument("--serving-requests", type=int, default=1000)
+    ap.add_argument("--serving-requests", type=int, default=10000)
     ap.add_argument("--serving-steps", type=int, default=10)
     ap.add_argument("--serving-slots", type=int, default=32)
     ap.add_argument("--sequential-requests", type=int, default=300)
