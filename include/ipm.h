@@ -275,7 +275,10 @@ ipm_status ipm_get_dims(const ipm_ctx* ctx, ipm_dims* out);
 
 /* Order all later work of ctx on the given cudaStream_t, used verbatim: NULL is the CUDA legacy
  * default stream (the stream PyTorch reports as 0). Until the first call the context uses a
- * non-blocking stream of its own. Waits for the work already queued on the previous stream. */
+ * non-blocking stream of its own. Waits for the work already queued on the previous stream. The
+ * context's device memory comes from a stream-ordered pool and is released on its current stream by
+ * ipm_destroy, so a stream given here must stay valid until the context is destroyed (or another
+ * stream is set). */
 ipm_status ipm_set_stream(ipm_ctx* ctx, void* cuda_stream);
 
 /* Copy moments / duals in or out; count must equal n_cells*N*m doubles. Synchronous. */
