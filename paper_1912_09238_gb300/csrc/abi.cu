@@ -69,9 +69,11 @@ struct ipm_ctx {
   int newton_mode = 0;         // 0 FP64, 1 mixed, 2 mixed with an FP32 factorisation, 3 mixed + split, 4 FP64 + split
   bool split = false;          // split factorisation (tensor-core trailing updates) on the CTA-per-cell kernel
   int s_rows = 0, s_nbuf = 0;  // its digit-slice rows and tensor-memory accumulator sets
+  uint32_t ph_stage_off = 0;    // shared-memory offset of the staged Phi^T chunks of the mixed Hessian (0: none)
   MixedLayout mx;
   NewtonSmem sm;
   float* d_phiT32 = nullptr;
+  float* d_phi32c = nullptr;     // [chunk][N][kc + 4] Phi^T by K-chunk (staged by bulk copy)
   uint8_t* d_phi_img = nullptr;
   size_t newton_smem = 0;
   bool h_in_smem = true;
@@ -204,6 +206,10 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.bc_right = c->prob.bc_right;
   a.mx.phi_img = c->d_phi_img;
   a.mx.phiT32 = c->d_phiT32;
+  a.mx.phi32c = c->d_phi32c;
+  a.mx.n_rows = c->N;
+  a.mx.kcp = c->mx.kc + 4;
+  a.mx.off_ph = c->ph_stage_off;
   a.mx.n_pad = c->mx.n_pad;
   a.mx.kc = c->mx.kc;
   a.mx.chunks = c->mx.chunks;
@@ -211,6 +217,7 @@ static NewtonArgs newton_args(const ipm_ctx* c, int one_step) {
   a.mx.tpp = c->mx.tpp;
   a.mx.tmem_cols = c->mx.tmem_cols;
   a.mx.abuf = c->mx.abuf;
+  a.mx.stack = c->mx.stack ? 1 : 0;
   a.off_h = c->sm.off_h;
   a.off_a = c->sm.off_a;
   a.off_b = c->sm.off_b;
@@ -392,6 +399,25 @@ static cudaError_t device_pool(int dev, cudaMemPool_t* out) {
   return cudaSuccess;
 }
 
+// Device memory a new context can still obtain: what the device reports free plus what the pool holds
+// for reuse (blocks freed by earlier contexts count as used in the device's report).
+static cudaError_t available_device_bytes(size_t* out) {
+  int dev = 0;
+  size_t free_b = 0, total_b = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool = nullptr;
+  e = device_pool(dev, &pool);
+  if (e != cudaSuccess) return e;
+  uint64_t reserved = 0, used = 0;
+  e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+  if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+  if (e != cudaSuccess) return e;
+  *out = free_b + (size_t)(reserved > used ? reserved - used : 0);
+  return cudaSuccess;
+}
+
 // bytes of device memory for the context, ordered on stream s (default: the context's own stream)
 template <typename T>
 static cudaError_t dalloc(const ipm_ctx* c, T** p, size_t bytes, cudaStream_t s = nullptr) {
@@ -502,7 +528,7 @@ static void free_ctx(ipm_ctx* c) {
   if (c->oneshot_exec) cudaGraphExecDestroy(c->oneshot_exec);
   void* ptrs[] = {c->d_Phi, c->d_PhiT, c->d_w, c->d_nodes, c->d_pairs, c->d_uhat, c->d_lam, c->d_unode,
                   c->d_cell_resid, c->d_hwork, c->d_iters, c->d_status, c->d_ghost_list, c->d_sc,
-                  c->d_phiT32, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf, c->d_level,
+                  c->d_phiT32, c->d_phi32c, c->d_phi_img, c->d_order, c->d_area, c->d_xf, c->d_yf, c->d_level,
                   c->d_factors, c->d_factor_valid, c->d_level_next, c->d_lev_w, c->d_q_eval,
                   c->d_img, c->d_img_lam, c->d_img_smax, c->d_img_valid, c->d_lf_a, c->d_lf_b, c->d_lf_cnt};
   cudaStream_t fs = c->stream ? c->stream : c->own_stream;
@@ -626,8 +652,8 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
   if (c->is2d) build_mesh2d(*problem, c->mesh2d);
   if (opt.hessian_reuse == 2) {
     c->factor_stride = (size_t)c->NM * (c->NM + 1) / 2 + c->NM;
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess ||
+    size_t free_b = 0;
+    if (available_device_bytes(&free_b) != cudaSuccess ||
         (size_t)c->n_cells * c->factor_stride * sizeof(double) > free_b / 4)
       return fail(nullptr, IPM_EINVAL, "ipm_init: kept factors (hessian_reuse 2) need more than a quarter of the free memory");
   }
@@ -694,6 +720,11 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
         return fail(nullptr, IPM_EINVAL, "ipm_init: N*m and Q too large for the mixed-precision Newton kernel");
     }
     c->sm = newton_smem(c->N, c->m, c->Q, c->h_in_smem, &c->mx, c->s_rows);
+    // the digit-slice region of the split factorisation is idle while the Hessian is assembled: when it
+    // has a region of its own (not the A staging) it holds two staged Phi^T chunks for the A builds
+    if (c->split && c->sm.off_s != c->sm.off_a &&
+        split_bytes(c->s_rows) >= 2 * (size_t)c->N * (c->mx.kc + 4) * sizeof(float))
+      c->ph_stage_off = c->sm.off_s;
   } else {
     const NewtonSmem full = newton_smem(c->N, c->m, c->Q, true, nullptr, c->s_rows);
     const NewtonSmem lean = newton_smem(c->N, c->m, c->Q, false, nullptr, c->s_rows);
@@ -776,7 +807,7 @@ static size_t ctx_footprint(const ipm_ctx* c) {
   size_t b = 2 * Q * N * 8 + Q * 8 + Q * c->tab.p * 8 + (N * (N + 1) / 2) * 4;   // tables
   b += 2 * nc * NM * 8 + nc * c->m * Q * 8 + nc * 8 + 3 * nc * 4 + sizeof(StepScalars);
   if (!c->h_in_smem) b += (size_t)c->newton_grid * c->hwork_stride * 8;
-  if (c->mixed) b += N * Q * 4 + (size_t)c->mx.chunks * c->mx.b_chunk_bytes;
+  if (c->mixed) b += N * Q * 4 + (size_t)c->mx.chunks * (c->mx.b_chunk_bytes + N * (c->mx.kc + 4) * 4);
   if (c->is2d) b += (c->mesh2d.area.size() + c->mesh2d.xf.size() + c->mesh2d.yf.size()) * 8;
   if (c->n_levels) b += 2 * nc * 4;
   if (c->level_rules) b += nc * 4 + c->lev_w.size() * 8;
@@ -895,9 +926,11 @@ ipm_status ipm_init(const ipm_problem* problem, const ipm_basis* basis, const ip
   CK(upload(c, &c->d_pairs, c->tab.pairs), "upload pairs");
   if (c->mixed) {
     CK(dalloc(c, &c->d_phiT32, (size_t)c->N * c->Q * sizeof(float)), "allocate phiT32");
+    CK(dalloc(c, &c->d_phi32c, (size_t)c->mx.chunks * c->N * (c->mx.kc + 4) * sizeof(float)), "allocate phi32c");
     CK(dalloc(c, &c->d_phi_img, (size_t)c->mx.chunks * c->mx.b_chunk_bytes), "allocate phi image");
     if (st == IPM_OK)
-      CK(launch_phi_images(c->d_PhiT, c->N, c->Q, c->mx, c->d_phiT32, c->d_phi_img, c->stream), "phi images");
+      CK(launch_phi_images(c->d_PhiT, c->N, c->Q, c->mx, c->d_phiT32, c->d_phi32c, c->d_phi_img, c->stream),
+         "phi images");
   }
   const size_t nstate = (size_t)c->n_cells * c->NM;
   CK(dalloc(c, &c->d_uhat, nstate * sizeof(double)), "allocate uhat");

@@ -262,6 +262,10 @@ struct StepScalars {
 struct MixedTiles {
   const uint8_t* phi_img;  // [chunk][hi, lo][n_pad x kc] BF16 K-major images of Phi (B operand)
   const float* phiT32;     // [N][Q] Phi^T in FP32 (builds the A operand)
+  const float* phi32c;     // [chunk][n_rows][kcp] the same by K-chunk, rows padded to kcp (bulk-copy source)
+  int n_rows;              // rows of phi32c (the table's N)
+  int kcp;                 // kc + 4: row stride of phi32c (shifts consecutive rows by four banks)
+  uint32_t off_ph;         // shared-memory offset of two staged phi32c chunks, 0: no staging
   int n_pad;               // N rounded up to a multiple of 16 (MMA N)
   int kc;                  // nodes per K-chunk (multiple of 16)
   int chunks;              // ceil(Q / kc)
@@ -269,6 +273,7 @@ struct MixedTiles {
   int tpp;                 // row tiles per pass (accumulators resident in tensor memory at once)
   int tmem_cols;           // allocated tensor-memory columns (power of two >= 32)
   int abuf;                // A staging buffers (2: the next chunk is built while the MMAs of this one run)
+  int stack;               // 1: B = [B_hi; B_lo] as one operand, two accumulators of n_pad columns per row tile
 };
 
 struct NewtonArgs {

@@ -55,6 +55,7 @@ struct MixedLayout {
   bool ok = false;          // the problem fits the tensor-core path
   int n_pad = 0, kc = 0, chunks = 0, tiles = 0, tpp = 0, tmem_cols = 0;
   int abuf = 1;             // A staging buffers (2: build of the next K-chunk overlaps the MMAs)
+  bool stack = false;       // B = [B_hi; B_lo] in one MMA operand (two accumulators of n_pad columns per row tile)
   size_t a_bytes = 0;       // A staging of one pass: abuf K-chunks (both BF16 terms each)
   size_t b_chunk_bytes = 0; // one K-chunk of the Phi image (both BF16 terms)
 };
@@ -113,8 +114,8 @@ size_t newton_warpq_slice(int nm, int m);
 cudaError_t prepare_newton_warpq(int ent, int phys, int m, bool mixed, int warps, int slice, int* blocks_per_sm);
 cudaError_t launch_newton_warpq(int ent, int phys, int m, bool mixed, const NewtonArgs& a, int grid, int warps,
                                 int slice, int nm_slice, cudaStream_t s);
-cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayout& L, float* phiT32, uint8_t* img,
-                              cudaStream_t s);
+cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayout& L, float* phiT32, float* phi32c,
+                              uint8_t* img, cudaStream_t s);
 cudaError_t prepare_update1d(int phys, int m, int N, int Q);
 cudaError_t launch_update1d(int phys, int m, const Update1DArgs& a, int grid, cudaStream_t s);
 // u_hat_j = lf_a[j] - (dt/dx) lf_b[j] on the interior cells (the Lax-Friedrichs update folded into the

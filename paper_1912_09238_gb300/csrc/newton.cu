@@ -71,16 +71,23 @@ MixedLayout mixed_layout(int N, int m, int Q, size_t smem_budget, bool h_in_smem
   L.tiles = (B * N + 127) / 128;
   L.b_chunk_bytes = (size_t)2 * L.n_pad * L.kc * 2;
   if (L.n_pad > 256) return L;
+  // B = [B_hi; B_lo] as one operand of 2 n_pad rows (two accumulators per row tile) when that needs no
+  // more passes over the row tiles than one accumulator per tile does
+  {
+    auto passes = [&](int cols) { return (L.tiles + std::min(L.tiles, 512 / cols) - 1) / std::min(L.tiles, 512 / cols); };
+    L.stack = 2 * L.n_pad <= 256 && passes(2 * L.n_pad) == passes(L.n_pad);
+  }
+  const int acc_cols = L.stack ? 2 * L.n_pad : L.n_pad;
   // row tiles per pass: bounded by tensor memory (512 columns) and by the shared-memory budget
   // (two A buffers when they fit at that tile count, else one)
-  for (int tpp = std::min(L.tiles, 512 / L.n_pad); tpp >= 1; --tpp) {
+  for (int tpp = std::min(L.tiles, 512 / acc_cols); tpp >= 1; --tpp) {
    for (int abuf = L.chunks > 1 ? 2 : 1; abuf >= 1; --abuf) {
     L.tpp = tpp;
     L.abuf = abuf;
     L.a_bytes = (size_t)abuf * 2 * tpp * 128 * L.kc * 2;
     if (newton_smem(N, m, Q, h_in_smem, &L, s_rows).bytes <= smem_budget) {
       int cols = 32;
-      while (cols < tpp * L.n_pad) cols *= 2;
+      while (cols < tpp * acc_cols) cols *= 2;
       if (s_rows > 0) cols = std::max(cols, SPLIT_BUF_COLS);   // one accumulator set of the split factorisation
       L.tmem_cols = cols;
       L.ok = true;
@@ -173,10 +180,11 @@ cudaError_t launch_order(const int* iters, int n_work, int nx, int gy, int* orde
   return cudaGetLastError();
 }
 
-// Phi in the forms the mixed path reads: FP32 Phi^T [N][Q], and per K-chunk the two BF16 terms
-// (hi, lo) of B[j][k] = phi_j(xi_k) in the K-major tile layout (zero beyond N and Q).
+// Phi in the forms the mixed path reads: FP32 Phi^T [N][Q], the same by K-chunk with rows padded to
+// kc + 4 floats ([chunk][N][kc + 4], zero beyond Q), and per K-chunk the two BF16 terms (hi, lo) of
+// B[j][k] = phi_j(xi_k) in the K-major tile layout (zero beyond N and Q).
 __global__ void k_phi_images(const double* __restrict__ PhiT, int N, int Q, int n_pad, int kc, int chunks,
-                             float* __restrict__ phiT32, uint8_t* __restrict__ img) {
+                             float* __restrict__ phiT32, float* __restrict__ phi32c, uint8_t* __restrict__ img) {
   const uint32_t sbo = tc::kmajor_sbo(kc);
   const size_t b_img = (size_t)n_pad * kc * 2;
   const int total = chunks * n_pad * kc;
@@ -187,6 +195,11 @@ __global__ void k_phi_images(const double* __restrict__ PhiT, int N, int Q, int 
     const int q = c * kc + k;
     const float x = (j < N && q < Q) ? (float)PhiT[(size_t)j * Q + q] : 0.f;
     if (j < N && q < Q) phiT32[(size_t)j * Q + q] = x;
+    if (j < N) {
+      float* row = phi32c + ((size_t)c * N + j) * (kc + 4);
+      row[k] = x;
+      if (k < 4) row[kc + k] = 0.f;
+    }
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
     uint8_t* base = img + (size_t)c * 2 * b_img;
@@ -196,11 +209,11 @@ __global__ void k_phi_images(const double* __restrict__ PhiT, int N, int Q, int 
   }
 }
 
-cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayout& L, float* phiT32, uint8_t* img,
-                              cudaStream_t s) {
+cudaError_t launch_phi_images(const double* PhiT, int N, int Q, const MixedLayout& L, float* phiT32, float* phi32c,
+                              uint8_t* img, cudaStream_t s) {
   const int total = L.chunks * L.n_pad * L.kc;
   k_phi_images<<<std::max(1, std::min(1024, (total + 255) / 256)), 256, 0, s>>>(PhiT, N, Q, L.n_pad, L.kc, L.chunks,
-                                                                                 phiT32, img);
+                                                                                 phiT32, phi32c, img);
   return cudaGetLastError();
 }
 

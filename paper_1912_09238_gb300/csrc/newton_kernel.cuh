@@ -423,12 +423,13 @@ __device__ void back_substitute(const T* A, int n, const T* s_dinv, T* x) {
 
 // Tensor-core pipeline state of one CTA (uniform across its threads).
 struct TcState {
-  uint64_t* bars;     // [0] Hessian MMA completion, [1], [2] Phi chunk buffers, [3], [4] split-factor MMA sets
+  uint64_t* bars;     // [0] Hessian MMA completion, [1], [2] Phi chunk buffers, [3], [4] split-factor MMA sets,
+                      // [5], [6] staged Phi^T chunk buffers
   uint32_t tmem;      // tensor-memory base address
-  uint32_t ph[5];     // parity of the next phase to wait for, per barrier
-  bool pend[5];       // a phase is outstanding on the barrier
+  uint32_t ph[7];     // parity of the next phase to wait for, per barrier
+  bool pend[7];       // a phase is outstanding on the barrier
 };
-constexpr int TC_BARS = 5;
+constexpr int TC_BARS = 7;
 
 __device__ __forceinline__ bool tc_wait(TcState& t, int k) {
   const bool ok = tc::mbar_wait(&t.bars[k], t.ph[k]);
@@ -439,12 +440,36 @@ __device__ __forceinline__ bool tc_wait(TcState& t, int k) {
   return ok;
 }
 
+// FP32 -> T. For T = double the conversion is exact and done on the integer pipes from the IEEE formats
+// (a subnormal FP32 value, below 1.2e-38 in magnitude, becomes zero): the FP64 pipe is the scarce one.
+template <typename T>
+__device__ __forceinline__ T widen(float f);
+template <>
+__device__ __forceinline__ float widen<float>(float f) { return f; }
+template <>
+__device__ __forceinline__ double widen<double>(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long ex = e == 0xFFu ? 0x7FFull : (unsigned long long)(e + 896u);   // e - 127 + 1023
+  return __longlong_as_double((long long)(sign | (ex << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
 // (b), mixed: split-BF16 products on the tensor cores, FP32 accumulate in tensor memory, then
 // widened into the packed FP64 H. s_wJf holds w_k J_k,ab as float [B][Q]. Returns false when a
 // bounded wait ran out (the CTA must stop).
+// s_ph: room for two staged chunks of Phi^T (FP32, n_rows x kcp each) or nullptr. When given, every
+// K-chunk's Phi^T columns arrive by bulk copy one chunk ahead of the build that reads them; otherwise
+// the build reads Phi^T from global memory (L2).
+// Warp 0 issues the MMAs (lane 0) and the bulk copies; warps 1..7 build the A operand, so the MMA issue
+// of chunk c overlaps the build of chunk c + 1. With mx.stack (chosen once per layout) and the cell's N
+// the table's, B = [B_hi; B_lo] is one operand of 2 n_pad rows: A_hi B_hi and A_hi B_lo come from one MMA
+// into adjacent accumulators and A_lo B_hi is added to the first, two MMAs per K-step instead of three;
+// the two accumulators are added in the epilogue.
 template <int M, typename T>
 __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJf, T* s_H, uint8_t* sA, uint8_t* sB,
-                           TcState& t, int* s_abort) {
+                           float* s_ph, TcState& t, int* s_abort) {
   constexpr int B = packed_count(M);
   const MixedTiles& mx = a.mx;
   const int Q = a.tab.Q, BN = B * N;
@@ -460,10 +485,24 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
   const int n_pad = (N + 15) / 16 * 16;
   const int tiles = (BN + 127) / 128;
   const int tpp = min(mx.tpp, tiles);
+  const bool stack = mx.stack && n_pad == mx.n_pad;                       // the cell's N is the table's
+  const int acc_cols = stack ? 2 * n_pad : n_pad;                            // tensor-memory columns per row tile
   const uint32_t idesc = tc::idesc_bf16_f32(128, n_pad);
+  const uint32_t idesc2 = tc::idesc_bf16_f32(128, 2 * n_pad);
   const int groups = mx.kc / 8;
   // K chunks of this cell's rule (a prefix of the table's nodes; the rest of the last chunk is zero in A)
   const int chunks = (Qc + mx.kc - 1) / mx.kc;
+  const bool staged = s_ph != nullptr;
+  const int kcp = mx.kcp;
+  // item -> (row, group of 8 nodes) by shifts (kc is 16 or 32), row -> (ab, i) by a multiply-high:
+  // floor(R / N) = umulhi(R, ceil(2^32 / N)) exactly for R N < 2^32
+  const int gshift = groups == 4 ? 2 : 1;
+  const uint32_t inv_n = 0xFFFFFFFFu / (uint32_t)N + 1u;
+  // w J rows read as float4 when they are 16-byte aligned (the last group of a row may read up to seven
+  // floats past Qc: entries of the next row or of the shared-memory region after it, all masked below)
+  const bool wj_vec = (Q & 3) == 0 && (reinterpret_cast<uintptr_t>(s_wJf) & 15u) == 0;
+  const uint32_t ph_floats = (uint32_t)mx.n_rows * (uint32_t)kcp;
+  const uint32_t ph_bytes = ph_floats * 4u;
 
   for (int t0 = 0; t0 < tiles; t0 += tpp) {
     const int nt = min(tpp, tiles - t0);
@@ -471,24 +510,58 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
     if (tid == 0) {
       tc::mbar_arrive_expect_tx(&t.bars[1], b_chunk);
       tc::bulk_g2s(sB, mx.phi_img, b_chunk, &t.bars[1]);
+      if (staged) {
+        for (int c = 0; c < 2 && c < chunks; ++c) {
+          tc::mbar_arrive_expect_tx(&t.bars[5 + c], ph_bytes);
+          tc::bulk_g2s(s_ph + c * ph_floats, mx.phi32c + (size_t)c * ph_floats, ph_bytes, &t.bars[5 + c]);
+        }
+      }
     }
     t.pend[1] = true;
-    // A operand of chunk c: rows (ab, i) of this pass, nodes c kc .. c kc + kc - 1, both BF16 terms, into dst
+    if (staged) {
+      t.pend[5] = true;
+      if (chunks > 1) t.pend[6] = true;
+    }
+    // A operand of chunk c: rows (ab, i) of this pass, nodes c kc .. c kc + kc - 1, both BF16 terms, into dst;
+    // warps 1..7 (every thread waits for the staged chunk, so that the barrier phases stay uniform)
     auto build = [&](int c, uint8_t* dst) {
       const int q0 = c * mx.kc;
-      for (int item = tid; item < rows * groups; item += NT) {
-        const int rl = item / groups, g = item - rl * groups;
+      if (staged && !tc_wait(t, 5 + (c & 1))) *s_abort = 1;
+      const float* phc = staged ? s_ph + (c & 1) * ph_floats : nullptr;
+      if (warp == 0) return;
+#pragma unroll 2
+      for (int item = tid - 32; item < rows * groups; item += NT - 32) {
+        const int rl = item >> gshift, g = item & (groups - 1);
         const int R = t0 * 128 + rl;
         uint32_t hw[4] = {0u, 0u, 0u, 0u}, lw[4] = {0u, 0u, 0u, 0u};
         if (R < BN) {
-          const int ab = R / N, i = R - ab * N;
-          const float* wj = s_wJf + ab * Q;
-          const float* ph = mx.phiT32 + (size_t)i * Q;
+          const int ab = (int)__umulhi((uint32_t)R, inv_n), i = R - ab * N;   // R / N, R mod N
+          const float* wj = s_wJf + ab * Q + q0 + g * 8;
+          const int qe = Qc - q0 - g * 8;                 // entries of this group inside the rule
+          float pv[8], wv[8];
+          if (wj_vec) {
+            const float4 v0 = reinterpret_cast<const float4*>(wj)[0], v1 = reinterpret_cast<const float4*>(wj)[1];
+            wv[0] = v0.x; wv[1] = v0.y; wv[2] = v0.z; wv[3] = v0.w;
+            wv[4] = v1.x; wv[5] = v1.y; wv[6] = v1.z; wv[7] = v1.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) wv[e] = e < qe ? wj[e] : 0.f;
+          }
+          if (staged) {
+            // rows of kcp = kc + 4 floats: the two 16-byte loads of a quarter warp hit 32 distinct banks
+            const float4* p4 = reinterpret_cast<const float4*>(phc + i * kcp + g * 8);
+            const float4 u0 = p4[0], u1 = p4[1];
+            pv[0] = u0.x; pv[1] = u0.y; pv[2] = u0.z; pv[3] = u0.w;
+            pv[4] = u1.x; pv[5] = u1.y; pv[6] = u1.z; pv[7] = u1.w;
+          } else {
+            const float* ph = mx.phiT32 + (size_t)i * Q + q0 + g * 8;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) pv[e] = e < qe ? ph[e] : 0.f;
+          }
 #pragma unroll
           for (int e = 0; e < 8; e += 2) {
-            const int q = q0 + g * 8 + e;
-            const float x0 = q < Qc ? wj[q] * ph[q] : 0.f;
-            const float x1 = q + 1 < Qc ? wj[q + 1] * ph[q + 1] : 0.f;
+            const float x0 = e < qe ? wv[e] * pv[e] : 0.f;
+            const float x1 = e + 1 < qe ? wv[e + 1] * pv[e + 1] : 0.f;
             const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
             const float2 hf = __bfloat1622float2(h);
             const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
@@ -501,7 +574,7 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
         *reinterpret_cast<uint4*>(dst + a_img + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
     };
-    // With two A buffers the threads build chunk c + 1 while the MMAs of chunk c run; with one, after them.
+    // With two A buffers warps 1..7 build chunk c + 1 while the MMAs of chunk c run; with one, after them.
     build(0, sA);
     tc::fence_proxy_async();
     __syncthreads();
@@ -517,21 +590,36 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
         }
         t.pend[1 + (buf ^ 1)] = true;
       }
+      if (staged && c + 2 < chunks) {
+        // staged buffer c & 1 was last read by the build of chunk c, which has completed
+        if (tid == 0) {
+          tc::mbar_arrive_expect_tx(&t.bars[5 + buf], ph_bytes);
+          tc::bulk_g2s(s_ph + buf * ph_floats, mx.phi32c + (size_t)(c + 2) * ph_floats, ph_bytes, &t.bars[5 + buf]);
+        }
+        t.pend[5 + buf] = true;
+      }
       const bool got_b = tc_wait(t, 1 + buf);
       if (!got_b) *s_abort = 1;
       if (tid == 0 && got_b) {
         tc::fence_after_sync();
         const uint32_t sa = tc::smem_u32(a_cur), sb = tc::smem_u32(sB + buf * b_chunk);
         for (int tl = 0; tl < nt; ++tl) {
-          const uint32_t d = t.tmem + (uint32_t)(tl * n_pad);
+          const uint32_t d = t.tmem + (uint32_t)(tl * acc_cols);
           const uint32_t ta = sa + (uint32_t)tl * 16u * sbo;   // 128 rows = 16 row groups
           for (int ks = 0; ks < mx.kc / 16; ++ks) {
             const uint32_t kofs = (uint32_t)ks * 256u;
             const uint64_t ah = tc::smem_desc(ta + kofs, sbo), al = tc::smem_desc(ta + a_img + kofs, sbo);
-            const uint64_t bh = tc::smem_desc(sb + kofs, sbo), bl = tc::smem_desc(sb + b_img + kofs, sbo);
-            tc::mma_bf16(d, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-            tc::mma_bf16(d, ah, bl, idesc, 1u);
-            tc::mma_bf16(d, al, bh, idesc, 1u);
+            const uint64_t bh = tc::smem_desc(sb + kofs, sbo);
+            const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+            if (stack) {
+              tc::mma_bf16(d, ah, bh, idesc2, acc);          // [A_hi B_hi | A_hi B_lo]
+              tc::mma_bf16(d, al, bh, idesc, 1u);            // + A_lo B_hi into the first half
+            } else {
+              const uint64_t bl = tc::smem_desc(sb + b_img + kofs, sbo);
+              tc::mma_bf16(d, ah, bh, idesc, acc);
+              tc::mma_bf16(d, ah, bl, idesc, 1u);
+              tc::mma_bf16(d, al, bh, idesc, 1u);
+            }
           }
         }
         tc::mma_commit(&t.bars[0]);
@@ -547,7 +635,7 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
       if (*s_abort) return false;
     }
     // accumulators -> packed FP64 H. Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 and one
-    // half of the columns.
+    // half of the columns, eight at a time (with the stacked operand both accumulators before one wait).
     const int lq = warp & 3, half = warp >> 2;
     const int hcols = n_pad / 2;
     for (int tl = 0; tl < nt; ++tl) {
@@ -556,16 +644,27 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
       const int ab = valid ? R / N : 0, i = valid ? R - ab * N : 0;
       int aa, bb;
       unpack_ab<M>(ab, aa, bb);
+      // the value H_ab[i][j] goes to packed row i M + a, column j M + b (j < i, or j <= i when a = b) and,
+      // for a < b, also to row i M + b, column j M + a (j <= i)
+      const size_t o1 = rowoff(i * M + aa) + bb, o2 = rowoff(i * M + bb) + aa;
+      const int jmax1 = aa == bb ? i : i - 1;
+      const uint32_t tbase = t.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(tl * acc_cols);
       for (int cg = 0; cg < hcols; cg += 8) {
         const int col0 = half * hcols + cg;
-        uint32_t r[8];
-        tc::tmem_ld_x8(t.tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(tl * n_pad + col0), r);
+        uint32_t r[8], r2[8];
+        tc::tmem_ld_x8(tbase + (uint32_t)col0, r);
+        if (stack) tc::tmem_ld_x8(tbase + (uint32_t)(n_pad + col0), r2);
         tc::tmem_wait_ld();
         if (valid) {
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int j = col0 + e;
-            if (j < N) store_block_entry<M, T>(s_H, aa, bb, i, j, (T)__uint_as_float(r[e]));
+            if (j <= i) {
+              const float f = stack ? __uint_as_float(r[e]) + __uint_as_float(r2[e]) : __uint_as_float(r[e]);
+              const T v = widen<T>(f);
+              if (j <= jmax1) s_H[o1 + (size_t)j * M] = v;
+              if (aa != bb) s_H[o2 + (size_t)j * M] = v;
+            }
           }
         }
       }
@@ -1005,6 +1104,7 @@ __global__ void __launch_bounds__(NT, SPLIT ? 1 : 2) k_newton(NewtonArgs a) {
   double* s_H = H_SMEM ? reinterpret_cast<double*>(sbytes + a.off_h) : (a.hwork + (size_t)blockIdx.x * a.hwork_stride);
   uint8_t* sA = sbytes + a.off_a;
   uint8_t* sB = sbytes + a.off_b;
+  float* s_ph = (MIXED && SPLIT && a.mx.off_ph) ? reinterpret_cast<float*>(sbytes + a.mx.off_ph) : nullptr;
   const double* __restrict__ PhiT = a.tab.PhiT;
   const double* __restrict__ Phi = a.tab.Phi;
   const double* __restrict__ w = a.tab.w;
@@ -1201,7 +1301,7 @@ __global__ void __launch_bounds__(NT, SPLIT ? 1 : 2) k_newton(NewtonArgs a) {
         float* Pf = reinterpret_cast<float*>(s_P);
         float* dinvf = reinterpret_cast<float*>(s_dinv);
         const uint64_t th0 = tid == 0 ? tc::globaltimer() : 0;
-        if (!hessian_tc<M, float>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), Hf, sA, sB, tcs, &s_abort)) {
+        if (!hessian_tc<M, float>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), Hf, sA, sB, s_ph, tcs, &s_abort)) {
           if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
           st = ST_TIMEOUT;
           stop = true;
@@ -1237,7 +1337,7 @@ __global__ void __launch_bounds__(NT, SPLIT ? 1 : 2) k_newton(NewtonArgs a) {
       // (b) Hessian, packed lower triangle, row index r = i*M + a
       if (MIXED) {
         const uint64_t th0 = tid == 0 ? tc::globaltimer() : 0;
-        if (!hessian_tc<M, double>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, tcs, &s_abort)) {
+        if (!hessian_tc<M, double>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, s_ph, tcs, &s_abort)) {
           if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
           st = ST_TIMEOUT;
           stop = true;
