@@ -461,13 +461,14 @@ __device__ __forceinline__ double widen<double>(float f) {
 // bounded wait ran out (the CTA must stop).
 // s_ph: room for two staged chunks of Phi^T (FP32, n_rows x kcp each) or nullptr. When given, every
 // K-chunk's Phi^T columns arrive by bulk copy one chunk ahead of the build that reads them; otherwise
-// the build reads Phi^T from global memory (L2).
+// the build reads Phi^T from global memory (L2). UNROLL: items per thread in flight in the build (2 on
+// the one-CTA-per-SM split kernels, 1 where the register budget is halved for two CTAs per SM).
 // Warp 0 issues the MMAs (lane 0) and the bulk copies; warps 1..7 build the A operand, so the MMA issue
 // of chunk c overlaps the build of chunk c + 1. With mx.stack (chosen once per layout) and the cell's N
 // the table's, B = [B_hi; B_lo] is one operand of 2 n_pad rows: A_hi B_hi and A_hi B_lo come from one MMA
 // into adjacent accumulators and A_lo B_hi is added to the first, two MMAs per K-step instead of three;
 // the two accumulators are added in the epilogue.
-template <int M, typename T>
+template <int M, typename T, int UNROLL>
 __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJf, T* s_H, uint8_t* sA, uint8_t* sB,
                            float* s_ph, TcState& t, int* s_abort) {
   constexpr int B = packed_count(M);
@@ -529,7 +530,7 @@ __device__ bool hessian_tc(const NewtonArgs& a, int N, int Qc, const float* s_wJ
       if (staged && !tc_wait(t, 5 + (c & 1))) *s_abort = 1;
       const float* phc = staged ? s_ph + (c & 1) * ph_floats : nullptr;
       if (warp == 0) return;
-#pragma unroll 2
+#pragma unroll UNROLL
       for (int item = tid - 32; item < rows * groups; item += NT - 32) {
         const int rl = item >> gshift, g = item & (groups - 1);
         const int R = t0 * 128 + rl;
@@ -710,13 +711,6 @@ struct SplitSmem {
   int nbuf;          // accumulator sets in tensor memory (1, or 2 to overlap MMAs with the combine)
 };
 
-// BF16 bits of the integer +-d, 0 <= d <= 255 (exact)
-__device__ __forceinline__ uint32_t digit_bf16(uint32_t d, bool neg) {
-  if (d == 0) return 0u;
-  const int p = 31 - __clz(d);
-  return ((uint32_t)(p + 127) << 7) | ((d << (7 - p)) & 0x7Fu) | (neg ? 0x8000u : 0u);
-}
-
 // Digit slices and row exponents of rows s1..n of the panel columns kb..kb+kw-1 (kw <= 16; the other
 // columns get zero digits). Two threads per row, eight columns each.
 static __device__ void split_panel(const double* A, int n, int kb, int kw, int s1, const SplitSmem& sp) {
@@ -736,25 +730,40 @@ static __device__ void split_panel(const double* A, int n, int kb, int kw, int s
     }
     emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 1));
     if (valid) {
+      // Digits as BF16 from 32-bit words: the 56-bit X is split into its high 24 and low 32 bits, a digit
+      // 0 <= d <= 255 is made exact in FP32 as (2^23 + d) - 2^23 and its BF16 is the float's high half
+      // (d has at most 8 significant bits); two columns' halves are packed with one byte permute.
       uint32_t w[SDIG][4];
 #pragma unroll
-      for (int i = 0; i < SDIG; ++i)
+      for (int pr = 0; pr < 4; ++pr) {
+        uint32_t xh[2], xl[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) w[i][q] = 0u;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int E = (int)((bits[e] >> 52) & 0x7FF);
-        unsigned long long X = 0ull;
-        if (E != 0) {
-          const unsigned long long mant = ((unsigned long long)bits[e] & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-          const int sh = E - emax + 3;                  // <= 3: X < 2^56
-          X = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
+        for (int h = 0; h < 2; ++h) {
+          const long long b = bits[2 * pr + h];
+          const int E = (int)((b >> 52) & 0x7FF);
+          unsigned long long X = 0ull;
+          if (E != 0) {
+            const unsigned long long mant = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+            const int sh = E - emax + 3;                  // <= 3: X < 2^56
+            X = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
+          }
+          xh[h] = (uint32_t)(X >> 32);
+          xl[h] = (uint32_t)X;
         }
-        const bool neg = bits[e] < 0;
+        const uint32_t sgn = (bits[2 * pr] < 0 ? 0x8000u : 0u) | (bits[2 * pr + 1] < 0 ? 0x80000000u : 0u);
 #pragma unroll
         for (int i = 0; i < SDIG; ++i) {
-          const uint32_t d = (uint32_t)(X >> (48 - 8 * i)) & 0xFFu;
-          w[i][e >> 1] |= digit_bf16(d, neg) << (16 * (e & 1));
+          uint32_t d0, d1;                                // digit i: bits 48 - 8 i .. 55 - 8 i of X
+          if (i < 3) {
+            d0 = (xh[0] >> (16 - 8 * i)) & 0xFFu;
+            d1 = (xh[1] >> (16 - 8 * i)) & 0xFFu;
+          } else {
+            d0 = (xl[0] >> (48 - 8 * i)) & 0xFFu;
+            d1 = (xl[1] >> (48 - 8 * i)) & 0xFFu;
+          }
+          const float f0 = __uint_as_float(0x4B000000u | d0) - 8388608.0f;
+          const float f1 = __uint_as_float(0x4B000000u | d1) - 8388608.0f;
+          w[i][pr] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) | sgn;
         }
       }
       const uint32_t off = (uint32_t)(rs >> 3) * SSBO + (uint32_t)half * 128u + (uint32_t)(rs & 7) * 16u;
@@ -860,34 +869,50 @@ static __device__ void split_combine(double* A, int s1, int R, int lo, int hi, i
 }
 
 // The 16-column panel kb..kb+kw-1 (rows kb..n, already updated by every earlier panel) is factorised in
-// FP64 in up to five phases, each a block-wide step between two barriers: 0 the diagonal block of its
+// FP64 in up to four phases, each a block-wide step between two barriers: 0 the diagonal block of its
 // first NB columns (one warp, panel_diag), 1 their rows below (panel_trsm), 2 the second block's columns
-// updated by the first, 3 the second diagonal block, 4 its rows below. Threads t0, t0 + stride, ...
-// share the row work.
-__device__ __forceinline__ int panel_phases(int kw) { return kw > NB ? 5 : 2; }
+// updated by the first, with warp 0 taking the rows of the second diagonal block and factorising that
+// block right after (the other threads update the rows below it meanwhile), 3 the second block's rows
+// below. Threads t0, t0 + stride, ... share the row work (t0 < 32: warp 0). The first block's columns go
+// to the panel buffer P, the second block's to the buffer after it (P + (n + 1) PSTR), so that the rows
+// below still read the first block's values while warp 0 factorises the second diagonal block.
+__device__ __forceinline__ int panel_phases(int kw) { return kw > NB ? 4 : 2; }
 
 static __device__ void panel_phase(int ph, double* A, int n, int kb, int kw, double* P, double* s_dinv, int* s_flag,
                                    int t0, int stride) {
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int k0 = min(NB, kw), s0 = kb + NB, k1 = kw - NB;
+  double* P1 = P + (size_t)(n + 1) * PSTR;
   if (ph == 0) {
     if (warp == 0) panel_diag(A, kb, k0, P, s_dinv, s_flag);
   } else if (ph == 1) {
     panel_trsm(A, n, kb, k0, P, s_dinv, t0, stride);
   } else if (ph == 2) {
-    const int rows = n + 1 - s0;
-    for (int item = t0; item < rows * k1; item += stride) {
-      const int r = s0 + item / k1, c = s0 + item % k1;
-      if (c > r) continue;
-      double acc = 0.0;
+    if (warp == 0) {
+      // rows s0 .. s0 + k1 - 1 (lane i: row s0 + i), then their diagonal block
+      if (lane < k1) {
+        const int r = s0 + lane;
+        for (int c = s0; c <= r; ++c) {
+          double acc = 0.0;
 #pragma unroll
-      for (int k = 0; k < NB; ++k) acc = fma(P[r * PSTR + k], P[c * PSTR + k], acc);
-      A[rowoff(r) + c] -= acc;
+          for (int k = 0; k < NB; ++k) acc = fma(P[r * PSTR + k], P[c * PSTR + k], acc);
+          A[rowoff(r) + c] -= acc;
+        }
+      }
+      __syncwarp();
+      panel_diag(A, s0, k1, P1, s_dinv, s_flag);
+    } else {
+      const int r0 = s0 + k1, rows = n + 1 - r0;
+      for (int item = t0 - 32; item < rows * k1; item += stride - 32) {
+        const int r = r0 + item / k1, c = s0 + item % k1;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) acc = fma(P[r * PSTR + k], P[c * PSTR + k], acc);
+        A[rowoff(r) + c] -= acc;
+      }
     }
-  } else if (ph == 3) {
-    if (warp == 0) panel_diag(A, s0, k1, P, s_dinv, s_flag);
   } else {
-    panel_trsm(A, n, s0, k1, P, s_dinv, t0, stride);
+    panel_trsm(A, n, s0, k1, P1, s_dinv, t0, stride);
   }
 }
 
@@ -1301,7 +1326,7 @@ __global__ void __launch_bounds__(NT, SPLIT ? 1 : 2) k_newton(NewtonArgs a) {
         float* Pf = reinterpret_cast<float*>(s_P);
         float* dinvf = reinterpret_cast<float*>(s_dinv);
         const uint64_t th0 = tid == 0 ? tc::globaltimer() : 0;
-        if (!hessian_tc<M, float>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), Hf, sA, sB, s_ph, tcs, &s_abort)) {
+        if (!hessian_tc<M, float, SPLIT ? 2 : 1>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), Hf, sA, sB, s_ph, tcs, &s_abort)) {
           if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
           st = ST_TIMEOUT;
           stop = true;
@@ -1337,7 +1362,7 @@ __global__ void __launch_bounds__(NT, SPLIT ? 1 : 2) k_newton(NewtonArgs a) {
       // (b) Hessian, packed lower triangle, row index r = i*M + a
       if (MIXED) {
         const uint64_t th0 = tid == 0 ? tc::globaltimer() : 0;
-        if (!hessian_tc<M, double>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, s_ph, tcs, &s_abort)) {
+        if (!hessian_tc<M, double, SPLIT ? 2 : 1>(a, N, Qc, reinterpret_cast<const float*>(s_wJ), s_H, sA, sB, s_ph, tcs, &s_abort)) {
           if (tid == 0) atomicAdd(&a.sc->tc_timeouts, 1);
           st = ST_TIMEOUT;
           stop = true;
