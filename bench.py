@@ -33,9 +33,9 @@ METRIC = "IPM cell-steps/s (mixed+batched vs FP64 GPU at equal error); p50/p99 l
 UNIT = "cell-steps/s"
 KERNELS_PER_TIME_STEP = 4    # k_order, k_newton, k_lf_combine, k_finalize (one CUDA graph per time step)
 # dram__bytes_read.sum + dram__bytes_write.sum of one mixed-path k_newton launch on this workload (the
-# launch of time step 691 of a whole run: 17.72 MB read, 0 written), from an ncu capture of the current
+# launch of time step 691 of a whole run: 17.68 MB read, 0 written), from an ncu capture of the current
 # kernel; None when no capture of the current kernel exists
-NEWTON_TRAFFIC_BYTES = {"mixed": 17.72e6, "fp64": None, "mixed_f32f": None}
+NEWTON_TRAFFIC_BYTES = {"mixed": 17.68e6, "fp64": None, "mixed_f32f": None}
 L2_FLUSH_BYTES = 512 << 20   # > 4x the 126 MiB L2
 FP64_PROBE_N = 6144          # cuBLAS DGEMM size of the FP64 ceiling measurement
 CPU_SAMPLE_STEPS = 20        # Algorithm-1 steps of the oracle in the cpu_baseline sample
