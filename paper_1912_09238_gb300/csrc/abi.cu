@@ -722,9 +722,19 @@ static ipm_status plan_ctx(ipm_ctx* c, const ipm_problem* problem, const ipm_bas
     c->sm = newton_smem(c->N, c->m, c->Q, c->h_in_smem, &c->mx, c->s_rows);
     // the digit-slice region of the split factorisation is idle while the Hessian is assembled: when it
     // has a region of its own (not the A staging) it holds two staged Phi^T chunks for the A builds
-    if (c->split && c->sm.off_s != c->sm.off_a &&
-        split_bytes(c->s_rows) >= 2 * (size_t)c->N * (c->mx.kc + 4) * sizeof(float))
+    const size_t stage_bytes = 2 * (size_t)c->N * (c->mx.kc + 4) * sizeof(float);
+    if (c->split && c->sm.off_s != c->sm.off_a && split_bytes(c->s_rows) >= stage_bytes) {
       c->ph_stage_off = c->sm.off_s;
+    } else if (!c->split) {
+      // without a digit-slice region: a staging region of its own, when the shared memory has room and
+      // the CTAs resident per SM stay as many
+      const size_t off = (c->sm.bytes + 127) & ~(size_t)127, with = off + stage_bytes;
+      const size_t per_sm = (size_t)prop.sharedMemPerMultiprocessor, rsv = (size_t)prop.reservedSharedMemPerBlock;
+      if (with + 1024 <= budget && per_sm / (with + rsv) == per_sm / (c->sm.bytes + rsv)) {
+        c->ph_stage_off = (uint32_t)off;
+        c->sm.bytes = with;
+      }
+    }
   } else {
     const NewtonSmem full = newton_smem(c->N, c->m, c->Q, true, nullptr, c->s_rows);
     const NewtonSmem lean = newton_smem(c->N, c->m, c->Q, false, nullptr, c->s_rows);

@@ -1129,7 +1129,7 @@ __global__ void __launch_bounds__(NT, SPLIT ? 1 : 2) k_newton(NewtonArgs a) {
   double* s_H = H_SMEM ? reinterpret_cast<double*>(sbytes + a.off_h) : (a.hwork + (size_t)blockIdx.x * a.hwork_stride);
   uint8_t* sA = sbytes + a.off_a;
   uint8_t* sB = sbytes + a.off_b;
-  float* s_ph = (MIXED && SPLIT && a.mx.off_ph) ? reinterpret_cast<float*>(sbytes + a.mx.off_ph) : nullptr;
+  float* s_ph = (MIXED && a.mx.off_ph) ? reinterpret_cast<float*>(sbytes + a.mx.off_ph) : nullptr;
   const double* __restrict__ PhiT = a.tab.PhiT;
   const double* __restrict__ Phi = a.tab.Phi;
   const double* __restrict__ w = a.tab.w;
